@@ -1,0 +1,171 @@
+/*
+ * dnatok.h -- C ABI of the GB300 DNA byte -> token-ID library (libdnatok.so).
+ *
+ * The library turns raw DNA bytes into token-ID streams on one GPU, following
+ * the problem statement of Niktab & Patel, "DNATokenizer: A GPU-First
+ * Byte-to-Identifier Tokenizer" (arXiv 2601.05531): bytes go to the device
+ * and a device-resident byte -> identifier table is applied there (Sec. 2.2,
+ * "Bytes path"; Algorithm 2), producing the integer identifiers that an
+ * embed_tokens : Z^{B x T} -> R^{B x T x D} consumes (Sec. 2).  Sequences
+ * here are ragged (one flat byte array plus offsets) instead of the paper's
+ * equal-length B x T matrix, and FASTA text is accepted directly.
+ *
+ * Tokenization modes (Sec. 1.1, Table 1; Sec. 1.3 lists all three):
+ *   DNATOK_CHAR  single-nucleotide: id = lut[byte] (Algorithm 1's ascii_lut);
+ *   DNATOK_KMER  non-overlapping k-mers, id = sum_i 4^(k-1-i) * code(b_i),
+ *                A0 C1 G2 T3, UNK = 4^k (MapKmer, Algorithm 2);
+ *   DNATOK_BPE   greedy rank-ordered BPE merges of a fixed table
+ *                (segmentation identical to the table's tokenizer, Sec. 4.3).
+ *
+ * Conventions for what the paper leaves open (identical in the CPU oracle):
+ *   - case-insensitive; '\n' '\r' ' ' '\t' are dropped (they emit nothing and
+ *     do not move the k-mer frame; BPE words continue across them);
+ *   - every other non-ACGT byte is N-class: CHAR default id 4, k-mer UNK,
+ *     BPE: ends the word and emits N_ID = 4 + n_merges;
+ *   - a k-mer tail of L mod k > 0 bases emits one UNK;
+ *   - CHAR default table: A0 C1 G2 T3, N-class 4, separators -1 (dropped);
+ *   - BPE ids: bases 0..3, merge rank r -> 4 + r;
+ *   - FASTA: a line whose first byte is '>' is a header; it is dropped with
+ *     its newline and opens a record; bytes before the first header form a
+ *     record only when byte 0 is not '>'.
+ *
+ * Output layout: ids are int32, packed record after record with no padding;
+ * id_offsets (int64) has one entry per record boundary, so record r's ids are
+ * ids[id_offsets[r] .. id_offsets[r+1]).
+ *
+ * Threading: a handle may be used by one host thread at a time, and its
+ * device work must stay ordered on one CUDA stream at a time (its
+ * look-back descriptors are reused by every launch).  Handles are
+ * independent of each other.
+ *
+ * Errors: every entry point returns a dnatok_status.  Argument and table
+ * errors are reported synchronously.  Launches are asynchronous; a device-side
+ * error (a bounded wait that ran out, malformed device offsets) is recorded in
+ * the handle and reported by dnatok_sync() or by the next call that
+ * synchronizes; dnatok_last_error() gives the text of the last error.
+ */
+#ifndef DNATOK_H
+#define DNATOK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DNATOK_API __attribute__((visibility("default")))
+#else
+#define DNATOK_API
+#endif
+
+typedef enum {
+    DNATOK_OK = 0,
+    DNATOK_PENDING = 1,           /* request not finished yet (poll again) */
+    DNATOK_ERR_ARG = -1,          /* bad argument (null, negative size, k out of range ...) */
+    DNATOK_ERR_TABLE = -2,        /* invalid LUT or merge table */
+    DNATOK_ERR_CAPACITY = -3,     /* an output buffer is too small */
+    DNATOK_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+    DNATOK_ERR_BUDGET = -5,       /* request larger than the device-memory budget */
+    DNATOK_ERR_TIMEOUT = -6,      /* a bounded device-side wait ran out */
+    DNATOK_ERR_UNKNOWN_REQ = -7,  /* no such request id */
+    DNATOK_ERR_NOMEM = -8,        /* host or device allocation failed */
+    DNATOK_ERR_STATE = -9,        /* call not valid in the current state */
+    DNATOK_ERR_DEVICE_DATA = -10  /* device-side input (seq_offsets) malformed */
+} dnatok_status;
+
+typedef enum { DNATOK_CHAR = 0, DNATOK_KMER = 1, DNATOK_BPE = 2 } dnatok_mode;
+typedef enum { DNATOK_RAW = 0, DNATOK_FASTA = 1 } dnatok_format;
+
+/* Same type as cudaStream_t (NULL = the legacy default stream). */
+typedef struct CUstream_st *dnatok_cuda_stream;
+
+typedef struct dnatok_handle dnatok_handle;
+
+/* Tables, copied by dnatok_create (the caller keeps ownership of its arrays).
+ *   ascii_lut256: CHAR only; 256 host int32 ids, -1 = drop the byte; NULL =
+ *                 default table.  Ids must be >= -1.  This is the ascii_lut of
+ *                 Algorithm 1 (e.g. its fixed DNA fallback A1 C2 G3 T4 N0).
+ *   merges:       BPE only; n_merges host (left, right) int32 pairs in rank
+ *                 order.  Valid iff for every rank r both ids are < 4 + r and
+ *                 no pair repeats.  n_merges <= DNATOK_MAX_MERGES. */
+typedef struct {
+    const int32_t *ascii_lut256;
+    const int32_t *merges;
+    int32_t n_merges;
+} dnatok_tables;
+
+#define DNATOK_MAX_K 15
+#define DNATOK_MAX_MERGES 16384
+
+/* Create a tokenizer on the current CUDA device.  mode/k/tables as above (k
+ * is ignored unless mode == DNATOK_KMER; 1 <= k <= 15).  fmt selects how
+ * records are found by dnatok_encode and the stream API.  Tables are
+ * validated and copied to device memory.  On success *out owns its device
+ * tables and workspace; release it with dnatok_destroy. */
+DNATOK_API dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
+                            const dnatok_tables *tables, dnatok_format fmt);
+
+/* Free everything the handle owns.  Waits for its outstanding device work. */
+DNATOK_API void dnatok_destroy(dnatok_handle *h);
+
+/* Upper bound on the ids produced from n_bytes of input in n_seq records
+ * (RAW) -- use it to size ids_out.  FASTA: n_seq is ignored. */
+DNATOK_API dnatok_status dnatok_max_tokens(const dnatok_handle *h, int64_t n_bytes, int64_t n_seq,
+                                int64_t *cap);
+
+/* Reserve device workspace for inputs up to max_bytes / max_seq so that later
+ * dnatok_encode calls of that size allocate nothing (needed before stream
+ * capture).  Synchronizes the device if it grows. */
+DNATOK_API dnatok_status dnatok_reserve(dnatok_handle *h, int64_t max_bytes, int64_t max_seq);
+
+/*
+ * One-shot encode, asynchronous on `stream` (every pointer is DEVICE memory
+ * owned by the caller and must stay valid until the stream reaches this work).
+ *   bytes_d        n_bytes input bytes (any alignment).
+ *   seq_offsets_d  RAW: n_seq + 1 non-decreasing int64 with [0] = 0 and
+ *                  [n_seq] = n_bytes; record r = bytes[off[r] .. off[r+1]).
+ *                  Checked on the device (DNATOK_ERR_DEVICE_DATA via
+ *                  dnatok_sync).  FASTA: ignored (pass NULL, 0).
+ *   ids_out_d      capacity ids_capacity >= dnatok_max_tokens(n_bytes, n_seq),
+ *                  checked here (DNATOK_ERR_CAPACITY).
+ *   id_offsets_d   RAW: n_seq + 1 entries.  FASTA: offsets_capacity entries;
+ *                  the records found may exceed it: entries past the capacity
+ *                  are not written and totals tells how many there were.
+ *   totals_d       NULL or 2 int64: {number of ids, number of records}.
+ * Workspace (look-back descriptors) is owned by the handle; it grows with a
+ * synchronizing allocation when n_bytes exceeds what was reserved.
+ */
+DNATOK_API dnatok_status dnatok_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
+                            const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
+                            int64_t ids_capacity, int64_t *id_offsets_d,
+                            int64_t offsets_capacity, int64_t *totals_d,
+                            dnatok_cuda_stream stream);
+
+/* Wait for `stream`, then report any device-side error recorded by this
+ * handle's kernels (clearing it). */
+DNATOK_API dnatok_status dnatok_sync(dnatok_handle *h, dnatok_cuda_stream stream);
+
+/* Copy the text of the handle's last error into buf (always NUL-terminated).
+ * h may be NULL for errors of dnatok_create. */
+DNATOK_API dnatok_status dnatok_last_error(const dnatok_handle *h, char *buf, size_t len);
+
+/* -------------------------------------------------------------- launch */
+
+/* Kernel launch shape for the CHAR / KMER tile kernel: bytes per tile
+ * (4096, 8192, 16384 or 32768), threads per CTA (128, 256 or 512), and
+ * resident CTAs per SM the grid is sized for (1..8). */
+typedef struct {
+    int32_t tile_bytes;
+    int32_t threads;
+    int32_t ctas_per_sm;
+} dnatok_launch_cfg;
+
+DNATOK_API dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg);
+DNATOK_API dnatok_status dnatok_set_launch(dnatok_handle *h, const dnatok_launch_cfg *cfg);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DNATOK_H */

@@ -1,0 +1,112 @@
+"""GB300-native DNA byte -> token-ID library (arXiv 2601.05531's hot path).
+
+``binding`` mirrors the C ABI of ``libdnatok.so`` one function per entry
+point.  ``Tokenizer`` below is a convenience wrapper that takes PyTorch CUDA
+tensors (PyTorch supplies device memory and streams only; every step of the
+tokenization runs in the library's CUDA kernels).
+"""
+from __future__ import annotations
+
+from . import binding
+from .binding import (BPE, CHAR, END_OF_STREAM, FASTA, HOST_PINNED, KMER, NEW_RECORD, RAW,
+                      DnatokError)
+
+__all__ = ["binding", "Tokenizer", "CHAR", "KMER", "BPE", "RAW", "FASTA", "DnatokError",
+           "END_OF_STREAM", "NEW_RECORD", "HOST_PINNED", "build"]
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Tokenizer:
+    """One library handle.  mode: CHAR / KMER / BPE; fmt: RAW / FASTA."""
+
+    def __init__(self, mode: int, k: int = 1, lut=None, merges=None, fmt: int = RAW):
+        import torch  # noqa: F401  (initializes the CUDA context the library uses)
+        torch.cuda.init()
+        self.mode, self.k, self.fmt = mode, k, fmt
+        self.n_merges = 0 if merges is None else len(merges)
+        self.h = binding.dnatok_create(mode, k, lut=lut, merges=merges, fmt=fmt)
+
+    def close(self):
+        if getattr(self, "h", None):
+            binding.dnatok_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def max_tokens(self, n_bytes: int, n_seq: int = 1) -> int:
+        return binding.dnatok_max_tokens(self.h, n_bytes, n_seq)
+
+    def reserve(self, max_bytes: int, max_seq: int = 1):
+        binding.dnatok_reserve(self.h, max_bytes, max_seq)
+
+    def set_launch(self, tile_bytes: int, threads: int, ctas_per_sm: int):
+        binding.dnatok_set_launch(self.h, tile_bytes, threads, ctas_per_sm)
+
+    def get_launch(self):
+        return binding.dnatok_get_launch(self.h)
+
+    def alloc_outputs(self, n_bytes: int, n_seq: int, offsets_capacity: int | None = None,
+                      device=None):
+        import torch
+        dev = device or torch.device("cuda")
+        cap = self.max_tokens(n_bytes, n_seq)
+        ids = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        if offsets_capacity is None:
+            offsets_capacity = n_seq + 1 if self.fmt == RAW else n_bytes + 2
+        offs = torch.empty(max(offsets_capacity, 1), dtype=torch.int64, device=dev)
+        totals = torch.zeros(2, dtype=torch.int64, device=dev)
+        return ids, offs, totals
+
+    def encode(self, data, seq_offsets=None, ids=None, offsets=None, totals=None, stream=None):
+        """Asynchronous encode of a CUDA uint8 tensor.  RAW needs seq_offsets
+        (CUDA int64, n_seq + 1).  Returns (ids, offsets, totals) tensors; the
+        counts are in totals = [n_ids, n_records] once the stream gets there."""
+        n = int(data.numel())
+        n_seq = int(seq_offsets.numel()) - 1 if seq_offsets is not None else 0
+        if ids is None or offsets is None or totals is None:
+            ids, offsets, totals = self.alloc_outputs(n, n_seq, device=data.device)
+        binding.dnatok_encode(self.h, data.data_ptr() if n else 0, n,
+                              seq_offsets.data_ptr() if seq_offsets is not None else 0, n_seq,
+                              ids.data_ptr(), ids.numel(), offsets.data_ptr(), offsets.numel(),
+                              totals.data_ptr(), _stream_ptr(stream))
+        return ids, offsets, totals
+
+    def sync(self, stream=None):
+        binding.dnatok_sync(self.h, _stream_ptr(stream))
+
+    def encode_host(self, data, seq_offsets=None):
+        """Copy host bytes to the device, encode, wait, and return numpy
+        (ids, offsets) trimmed to the produced counts (a test helper)."""
+        import numpy as np
+        import torch
+        d = torch.from_numpy(np.ascontiguousarray(data, dtype=np.uint8)).cuda()
+        so = None
+        if self.fmt == RAW:
+            if seq_offsets is None:
+                seq_offsets = np.array([0, len(data)], dtype=np.int64)
+            so = torch.from_numpy(np.ascontiguousarray(seq_offsets, dtype=np.int64)).cuda()
+        ids, offs, tot = self.encode(d, so)
+        self.sync()
+        n_ids, n_rec = (int(x) for x in tot.cpu().tolist())
+        return ids[:n_ids].cpu().numpy(), offs[: n_rec + 1].cpu().numpy()

@@ -1,0 +1,157 @@
+"""Thin ctypes binding of libdnatok.so.
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments (integers are raw device / host addresses, streams are
+``cudaStream_t`` values such as ``torch.cuda.Stream.cuda_stream``).  All work
+happens in the CUDA library; there is no Python or CPU fallback -- if the
+library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+CHAR, KMER, BPE = 0, 1, 2
+RAW, FASTA = 0, 1
+
+OK, PENDING = 0, 1
+STATUS_NAMES = {
+    0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_TABLE", -3: "ERR_CAPACITY", -4: "ERR_CUDA",
+    -5: "ERR_BUDGET", -6: "ERR_TIMEOUT", -7: "ERR_UNKNOWN_REQ", -8: "ERR_NOMEM",
+    -9: "ERR_STATE", -10: "ERR_DEVICE_DATA",
+}
+
+END_OF_STREAM = 1
+NEW_RECORD = 2
+HOST_PINNED = 4
+
+
+class DnatokError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+class LaunchCfg(ctypes.Structure):
+    _fields_ = [("tile_bytes", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+class Tables(ctypes.Structure):
+    _fields_ = [("ascii_lut256", ctypes.POINTER(ctypes.c_int32)),
+                ("merges", ctypes.POINTER(ctypes.c_int32)), ("n_merges", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_ST = ctypes.c_int
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libdnatok.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libdnatok.so is not built (%s): run __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        sig = {
+            "dnatok_create": (_ST, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(Tables), ctypes.c_int]),
+            "dnatok_destroy": (None, [_P]),
+            "dnatok_max_tokens": (_ST, [_P, _I64, _I64, ctypes.POINTER(_I64)]),
+            "dnatok_reserve": (_ST, [_P, _I64, _I64]),
+            "dnatok_encode": (_ST, [_P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P]),
+            "dnatok_sync": (_ST, [_P, _P]),
+            "dnatok_last_error": (_ST, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+            "dnatok_get_launch": (_ST, [_P, ctypes.POINTER(LaunchCfg)]),
+            "dnatok_set_launch": (_ST, [_P, ctypes.POINTER(LaunchCfg)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error(h) -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib().dnatok_last_error(h, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def check(st: int, h=None) -> int:
+    if st < 0:
+        raise DnatokError(st, last_error(h))
+    return st
+
+
+# ------------------------------------------------------------------ wrappers
+
+def dnatok_create(mode: int, k: int = 1, lut=None, merges=None, fmt: int = RAW):
+    """Returns the handle (an opaque address).  lut: 256 ints or None;
+    merges: (M, 2) ints or None."""
+    import numpy as np
+    t = Tables()
+    keep = []
+    if lut is not None:
+        a = np.ascontiguousarray(np.asarray(lut, dtype=np.int32).reshape(256))
+        keep.append(a)
+        t.ascii_lut256 = a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    if merges is not None:
+        m = np.ascontiguousarray(np.asarray(merges, dtype=np.int32).reshape(-1, 2))
+        keep.append(m)
+        t.merges = m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        t.n_merges = m.shape[0]
+    h = _P()
+    check(lib().dnatok_create(ctypes.byref(h), mode, k, ctypes.byref(t), fmt), None)
+    return h.value
+
+
+def dnatok_destroy(h) -> None:
+    lib().dnatok_destroy(h)
+
+
+def dnatok_max_tokens(h, n_bytes: int, n_seq: int) -> int:
+    c = _I64()
+    check(lib().dnatok_max_tokens(h, n_bytes, n_seq, ctypes.byref(c)), h)
+    return c.value
+
+
+def dnatok_reserve(h, max_bytes: int, max_seq: int) -> None:
+    check(lib().dnatok_reserve(h, max_bytes, max_seq), h)
+
+
+def dnatok_encode(h, bytes_d: int, n_bytes: int, seq_offsets_d: int, n_seq: int, ids_out_d: int,
+                  ids_capacity: int, id_offsets_d: int, offsets_capacity: int, totals_d: int,
+                  stream: int) -> int:
+    return check(lib().dnatok_encode(h, bytes_d, n_bytes, seq_offsets_d, n_seq, ids_out_d,
+                                     ids_capacity, id_offsets_d, offsets_capacity, totals_d,
+                                     stream), h)
+
+
+def dnatok_sync(h, stream: int) -> int:
+    return check(lib().dnatok_sync(h, stream), h)
+
+
+def dnatok_last_error(h) -> str:
+    return last_error(h)
+
+
+def dnatok_get_launch(h) -> tuple:
+    c = LaunchCfg()
+    check(lib().dnatok_get_launch(h, ctypes.byref(c)), h)
+    return (c.tile_bytes, c.threads, c.ctas_per_sm)
+
+
+def dnatok_set_launch(h, tile_bytes: int, threads: int, ctas_per_sm: int) -> None:
+    c = LaunchCfg(tile_bytes, threads, ctas_per_sm)
+    check(lib().dnatok_set_launch(h, ctypes.byref(c)), h)

@@ -1,0 +1,316 @@
+// api.cu -- the C ABI: handle life cycle, validation, one-shot encode.
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <utility>
+
+#include "handle.h"
+#include "tile_kernel.cuh"
+
+using namespace dnatok;
+
+namespace {
+thread_local std::string g_create_error;
+
+void default_lut(int32_t *lut) {
+    for (int b = 0; b < 256; ++b) lut[b] = 4;  // N-class
+    const char *bases = "ACGT";
+    for (int i = 0; i < 4; ++i) {
+        lut[(unsigned char)bases[i]] = i;
+        lut[(unsigned char)bases[i] + 32] = i;
+    }
+    lut['\n'] = lut['\r'] = lut[' '] = lut['\t'] = -1;
+}
+}  // namespace
+
+namespace dnatok {
+
+dnatok_status fail(dnatok_handle *h, dnatok_status st, const std::string &msg) {
+    if (h) h->last_error = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+dnatok_status fail_cuda(dnatok_handle *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(h, DNATOK_ERR_NOMEM, m);
+    return fail(h, DNATOK_ERR_CUDA, m);
+}
+
+long long tiles_for(long long n_bytes, int head_pad, int tile) {
+    return (head_pad + n_bytes + tile - 1) / tile;
+}
+
+dnatok_status ensure_workspace(dnatok_handle *h, long long n_bytes, long long n_bnd,
+                               const LaunchShape &sh, cudaStream_t s) {
+    const long long tiles = tiles_for(n_bytes, 15, sh.tile) + 1;
+    if (tiles > h->desc_cap) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            return fail(h, DNATOK_ERR_STATE, "workspace must grow during stream capture; call dnatok_reserve first");
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail_cuda(h, e, "cudaDeviceSynchronize");
+        long long cap = tiles + tiles / 4 + 64;
+        TileDesc *d = nullptr;
+        e = cudaMalloc(&d, sizeof(TileDesc) * cap);
+        if (e != cudaSuccess) return fail_cuda(h, e, "cudaMalloc(look-back descriptors)");
+        e = cudaMemset(d, 0, sizeof(TileDesc) * cap);
+        if (e != cudaSuccess) { cudaFree(d); return fail_cuda(h, e, "cudaMemset"); }
+        int *r = nullptr;
+        e = cudaMalloc(&r, sizeof(int) * (cap + 1));
+        if (e != cudaSuccess) { cudaFree(d); return fail_cuda(h, e, "cudaMalloc(tile map)"); }
+        cudaFree(h->d_desc);
+        cudaFree(h->d_tile_rec);
+        h->d_desc = d;
+        h->d_tile_rec = r;
+        h->desc_cap = cap;
+        h->rec_cap = cap;
+        h->epoch = 0;  // fresh zeroed descriptors: epoch 0 is never used
+    }
+    (void)n_bnd;
+    return DNATOK_OK;
+}
+
+dnatok_status next_epoch(dnatok_handle *h, cudaStream_t s, unsigned *epoch) {
+    h->epoch++;
+    if ((h->epoch & 0xffffffu) == 0) {  // 24-bit wrap: forget every old descriptor
+        cudaError_t e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * h->desc_cap, s);
+        if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
+        h->epoch++;
+    }
+    *epoch = h->epoch;
+    return DNATOK_OK;
+}
+
+dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const uint8_t *bytes,
+                              long long n_bytes, const long long *seq_offsets, long long n_bnd,
+                              void *out, long long out_cap, long long *offsets_out,
+                              long long offsets_cap, long long *totals_out, const Carry *carry_in,
+                              Carry *carry_out, int start_boundary, int end_boundary,
+                              cudaStream_t s) {
+    const LaunchShape sh = h->shape;
+    dnatok_status st = ensure_workspace(h, n_bytes, n_bnd, sh, s);
+    if (st != DNATOK_OK) return st;
+    TileParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.bytes = bytes;
+    p.n_bytes = n_bytes;
+    p.seq_offsets = seq_offsets;
+    p.n_bnd = n_bnd;
+    p.tile_rec = h->d_tile_rec;
+    p.out = out;
+    p.out_cap = out_cap;
+    p.offsets_out = offsets_out;
+    p.offsets_cap = offsets_cap;
+    p.totals_out = totals_out;
+    p.desc = h->d_desc;
+    p.tile_counter = h->d_counter;
+    p.carry_in = carry_in;
+    p.carry_out = carry_out;
+    p.status = h->d_status;
+    p.lut = h->d_lut;
+    p.k = k;
+    p.start_boundary = start_boundary;
+    p.end_boundary = end_boundary;
+    p.head_pad = (int)((uintptr_t)bytes & 15u);
+    cudaError_t e;
+    if (n_bytes == 0) {
+        e = launch_empty_chunk(p, bsrc == BSRC_LIST, s);
+        if (e != cudaSuccess) return fail_cuda(h, e, "empty-chunk launch");
+        return DNATOK_OK;
+    }
+    p.n_tiles = tiles_for(n_bytes, p.head_pad, sh.tile);
+    st = next_epoch(h, s, &p.epoch);
+    if (st != DNATOK_OK) return st;
+    if (bsrc == BSRC_LIST) {
+        e = launch_plan_list(seq_offsets, n_bnd, n_bytes, p.head_pad, sh.tile, p.n_tiles,
+                             h->d_tile_rec, h->d_counter, h->d_status, s);
+        if (e != cudaSuccess) return fail_cuda(h, e, "plan launch");
+    } else {
+        e = cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(counter)");
+    }
+    e = launch_tile_kernel(mode, bsrc, p, sh, s, h->sm_count);
+    if (e != cudaSuccess) return fail_cuda(h, e, "tile kernel launch");
+    return DNATOK_OK;
+}
+
+}  // namespace dnatok
+
+// ======================================================================= ABI
+
+extern "C" {
+
+dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
+                            const dnatok_tables *tables, dnatok_format fmt) {
+    if (!out) return fail(nullptr, DNATOK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (mode != DNATOK_CHAR && mode != DNATOK_KMER && mode != DNATOK_BPE)
+        return fail(nullptr, DNATOK_ERR_ARG, "unknown mode");
+    if (fmt != DNATOK_RAW && fmt != DNATOK_FASTA)
+        return fail(nullptr, DNATOK_ERR_ARG, "unknown format");
+    if (mode == DNATOK_KMER && (k < 1 || k > DNATOK_MAX_K))
+        return fail(nullptr, DNATOK_ERR_ARG, "k must be in [1, 15]");
+    dnatok_handle *h = new (std::nothrow) dnatok_handle();
+    if (!h) return fail(nullptr, DNATOK_ERR_NOMEM, "host allocation failed");
+    h->mode = mode;
+    h->k = (mode == DNATOK_KMER) ? k : 1;
+    h->fmt = fmt;
+    if (mode == DNATOK_CHAR && tables && tables->ascii_lut256) {
+        for (int b = 0; b < 256; ++b) {
+            if (tables->ascii_lut256[b] < -1) {
+                delete h;
+                return fail(nullptr, DNATOK_ERR_TABLE, "LUT ids must be >= -1");
+            }
+            h->lut_host[b] = tables->ascii_lut256[b];
+        }
+    } else {
+        default_lut(h->lut_host);
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_lut, sizeof(int) * 256);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_lut, h->lut_host, sizeof(int) * 256, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        std::string m = std::string("CUDA setup failed: ") + cudaGetErrorString(e);
+        dnatok_destroy(h);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? DNATOK_ERR_NOMEM : DNATOK_ERR_CUDA, m);
+    }
+    if (mode == DNATOK_BPE) {
+        if (!tables || (tables->n_merges > 0 && !tables->merges)) {
+            dnatok_destroy(h);
+            return fail(nullptr, DNATOK_ERR_TABLE, "BPE needs a merge table");
+        }
+        dnatok_status st = bpe_create(h, tables->merges, tables->n_merges);
+        if (st != DNATOK_OK) {
+            std::string m = h->last_error;
+            dnatok_destroy(h);
+            return fail(nullptr, st, m);
+        }
+    }
+    *out = h;
+    return DNATOK_OK;
+}
+
+void dnatok_destroy(dnatok_handle *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    stream_destroy(h);
+    bpe_destroy(h);
+    cudaFree(h->d_lut);
+    cudaFree(h->d_desc);
+    cudaFree(h->d_tile_rec);
+    cudaFree(h->d_counter);
+    cudaFree(h->d_status);
+    delete h;
+}
+
+dnatok_status dnatok_max_tokens(const dnatok_handle *h, int64_t n_bytes, int64_t n_seq,
+                                int64_t *cap) {
+    if (!h || !cap || n_bytes < 0 || n_seq < 0) return DNATOK_ERR_ARG;
+    int64_t c = n_bytes;
+    if (h->mode == DNATOK_KMER && h->fmt == DNATOK_RAW && h->k > 1) {
+        const int64_t alt = (n_bytes + n_seq * (int64_t)(h->k - 1)) / h->k;
+        if (alt < c) c = alt;
+    }
+    *cap = c;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_reserve(dnatok_handle *h, int64_t max_bytes, int64_t max_seq) {
+    if (!h || max_bytes < 0 || max_seq < 0) return DNATOK_ERR_ARG;
+    dnatok_status st = ensure_workspace(h, max_bytes, max_seq + 1, h->shape, 0);
+    if (st != DNATOK_OK) return st;
+    if (h->mode == DNATOK_BPE) {
+        // the BPE path runs its symbol pass with the same workspace
+    }
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
+                            const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
+                            int64_t ids_capacity, int64_t *id_offsets_d,
+                            int64_t offsets_capacity, int64_t *totals_d,
+                            dnatok_cuda_stream stream) {
+    if (!h) return DNATOK_ERR_ARG;
+    if (n_bytes < 0 || (n_bytes > 0 && !bytes_d))
+        return fail(h, DNATOK_ERR_ARG, "bad input bytes");
+    if (!id_offsets_d) return fail(h, DNATOK_ERR_ARG, "id_offsets is NULL");
+    if (h->fmt == DNATOK_RAW) {
+        if (!seq_offsets_d || n_seq < 0) return fail(h, DNATOK_ERR_ARG, "RAW needs seq_offsets");
+        if (n_seq >= INT32_MAX - 1) return fail(h, DNATOK_ERR_ARG, "too many sequences");
+        if (offsets_capacity < n_seq + 1)
+            return fail(h, DNATOK_ERR_CAPACITY, "id_offsets needs n_seq + 1 entries");
+        if (n_seq == 0 && n_bytes != 0)
+            return fail(h, DNATOK_ERR_ARG, "bytes without sequences");
+    } else if (offsets_capacity < 1) {
+        return fail(h, DNATOK_ERR_CAPACITY, "id_offsets needs at least one entry");
+    }
+    int64_t need = 0;
+    dnatok_max_tokens(h, n_bytes, n_seq, &need);
+    if (ids_capacity < need || (need > 0 && !ids_out_d))
+        return fail(h, DNATOK_ERR_CAPACITY, "ids_out smaller than dnatok_max_tokens()");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (h->mode == DNATOK_BPE)
+        return bpe_encode(h, bytes_d, n_bytes, seq_offsets_d, n_seq, ids_out_d, ids_capacity,
+                          id_offsets_d, offsets_capacity, totals_d, s);
+    const int mode = (h->mode == DNATOK_CHAR) ? MODE_CHAR : MODE_KMER;
+    if (h->fmt == DNATOK_RAW)
+        return run_tile_encode(h, mode, h->k, BSRC_LIST, bytes_d, n_bytes,
+                               reinterpret_cast<const long long *>(seq_offsets_d), n_seq + 1,
+                               ids_out_d, ids_capacity, reinterpret_cast<long long *>(id_offsets_d),
+                               offsets_capacity, reinterpret_cast<long long *>(totals_d), nullptr,
+                               nullptr, 0, 0, s);
+    return run_tile_encode(h, mode, h->k, BSRC_FASTA, bytes_d, n_bytes, nullptr, 0, ids_out_d,
+                           ids_capacity, reinterpret_cast<long long *>(id_offsets_d),
+                           offsets_capacity, reinterpret_cast<long long *>(totals_d), nullptr,
+                           nullptr, 1, 1, s);
+}
+
+dnatok_status dnatok_sync(dnatok_handle *h, dnatok_cuda_stream stream) {
+    if (!h) return DNATOK_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaStreamSynchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(h, e, "status read");
+    if (st == DEV_OK) return DNATOK_OK;
+    const int zero = 0;
+    cudaMemcpy(h->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (st == DEV_TIMEOUT) return fail(h, DNATOK_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (st == DEV_BAD_OFFSETS)
+        return fail(h, DNATOK_ERR_DEVICE_DATA,
+                    "seq_offsets malformed (must be non-decreasing, [0]=0, [n_seq]=n_bytes)");
+    return fail(h, DNATOK_ERR_CUDA, "device reported error " + std::to_string(st));
+}
+
+dnatok_status dnatok_last_error(const dnatok_handle *h, char *buf, size_t len) {
+    if (!buf || len == 0) return DNATOK_ERR_ARG;
+    const std::string &m = h ? h->last_error : g_create_error;
+    std::snprintf(buf, len, "%s", m.c_str());
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg) {
+    if (!h || !cfg) return DNATOK_ERR_ARG;
+    cfg->tile_bytes = h->shape.tile;
+    cfg->threads = h->shape.threads;
+    cfg->ctas_per_sm = h->shape.ctas_per_sm;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_set_launch(dnatok_handle *h, const dnatok_launch_cfg *cfg) {
+    if (!h || !cfg) return DNATOK_ERR_ARG;
+    LaunchShape sh{cfg->tile_bytes, cfg->threads, cfg->ctas_per_sm};
+    if (!tile_shape_supported(sh) || sh.ctas_per_sm < 1 || sh.ctas_per_sm > 8)
+        return fail(h, DNATOK_ERR_ARG, "unsupported launch shape");
+    h->shape = sh;
+    return DNATOK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,244 @@
+// common.cuh -- device-side building blocks shared by the library's kernels:
+// inline-PTX wrappers (TMA bulk copy, mbarrier, acquire/release), the scan
+// element of the decoupled look-back, and bounded waits.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dnatok {
+
+// ---------------------------------------------------------------- constants
+
+enum : int { MODE_CHAR = 0, MODE_KMER = 1, MODE_BPE = 2, MODE_SYM = 3 };
+enum : int { FMT_RAW = 0, FMT_FASTA = 1 };
+
+// Device status word values (written by kernels, read by the host).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_OFFSETS = 2, DEV_CAPACITY = 3 };
+
+// Byte class bits of the 256-entry class table.
+//   bits 0-1  base code (A0 C1 G2 T3)    bit 2  N-class
+//   bit 3     separator (\n \r space \t) bit 4  '\n'    bit 5  '>'
+enum : uint8_t { CB_N = 4, CB_SEP = 8, CB_NL = 16, CB_GT = 32 };
+
+// Look-back descriptor flags.
+enum : unsigned { LB_EMPTY = 0, LB_AGG = 1, LB_INCL = 2 };
+
+// FASTA line states.
+enum : unsigned { HS_LS = 0, HS_HD = 1, HS_SQ = 2 };
+
+// A bounded spin: about this many polls (each followed by a short sleep)
+// before a wait gives up, records DEV_TIMEOUT and returns.
+constexpr int kSpinLimit = 1 << 22;
+
+// ------------------------------------------------------------ scan element
+//
+// Scan element over a span of the byte stream (the monoid of the single-pass
+// look-back).  Boundaries are record starts (and the end of the stream).
+//   nb    boundaries inside the span
+//   h     kept symbols before the first boundary (all kept symbols if nb == 0)
+//   d     tokens completed after the first boundary: ceil(L/k) for every
+//         record closed inside the span, floor(t/k) for the record still open
+//   t     kept symbols after the last boundary (0 if nb == 0)
+//   codes the last min(open, k-1) kept symbols of the open record, 3 bits each
+//         (base code in bits 0-1, N flag in bit 2), newest in the low bits;
+//         symbol count in bits 58..61.
+// An exclusive prefix from the stream start always has nb >= 1 (position 0
+// is a boundary), so it reads: records seen = nb, tokens completed = d,
+// kept symbols of the open record = t.
+struct Agg {
+    long long nb, h, d, t;
+    unsigned long long codes;
+};
+
+__host__ __device__ __forceinline__ Agg agg_identity() { return Agg{0, 0, 0, 0, 0ull}; }
+
+__host__ __device__ __forceinline__ int codes_count(unsigned long long c) { return (int)(c >> 58); }
+
+__host__ __device__ __forceinline__ unsigned long long codes_concat(unsigned long long a,
+                                                                   unsigned long long b, int k) {
+    if (k <= 1) return 0ull;
+    int na = codes_count(a), nb = codes_count(b);
+    int n = na + nb;
+    if (n > k - 1) n = k - 1;
+    const unsigned long long m58 = (1ull << 58) - 1;
+    unsigned long long bits = ((a & m58) << (3 * nb)) | (b & m58);
+    bits &= (n == 0) ? 0ull : ((1ull << (3 * n)) - 1);
+    return ((unsigned long long)n << 58) | bits;
+}
+
+__host__ __device__ __forceinline__ Agg agg_combine(const Agg &A, const Agg &B, int k) {
+    Agg r;
+    r.nb = A.nb + B.nb;
+    if (A.nb == 0) {
+        r.h = A.h + B.h;
+        r.d = B.d;
+        r.t = B.t;
+    } else if (B.nb == 0) {
+        r.h = A.h;
+        r.d = A.d - A.t / k + (A.t + B.h) / k;
+        r.t = A.t + B.h;
+    } else {
+        r.h = A.h;
+        r.d = A.d - A.t / k + (A.t + B.h + k - 1) / k + B.d;
+        r.t = B.t;
+    }
+    r.codes = (B.nb > 0) ? B.codes : codes_concat(A.codes, B.codes, k);
+    return r;
+}
+
+// Carry between consecutive chunks of one stream: the inclusive prefix at the
+// chunk end plus the FASTA line state there.
+struct Carry {
+    Agg a;
+    unsigned hstate;
+    unsigned pad;
+};
+
+// One look-back descriptor per tile.  The aggregate and the inclusive prefix
+// live in separate slots so a reader that saw LB_AGG never races the later
+// LB_INCL write.
+struct __align__(128) TileDesc {
+    unsigned status;   // epoch << 2 | LB_*
+    unsigned hstatus;  // FASTA line-state map: epoch << 8 | flag << 6 | map
+    unsigned pad0, pad1;
+    Agg agg;           // the tile's own scan element
+    Agg incl;          // inclusive prefix through this tile
+};
+
+// ---------------------------------------------------------------- PTX
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 1-D TMA bulk copy global -> shared, completion counted on an mbarrier.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *smem_dst, const void *gsrc, unsigned bytes,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(smem_dst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ long long ld_relaxed_s64(const long long *p) {
+    long long v;
+    asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_s64(long long *p, long long v) {
+    asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ Agg load_agg(const Agg *p) {
+    const long long *q = reinterpret_cast<const long long *>(p);
+    Agg a;
+    a.nb = ld_relaxed_s64(q + 0);
+    a.h = ld_relaxed_s64(q + 1);
+    a.d = ld_relaxed_s64(q + 2);
+    a.t = ld_relaxed_s64(q + 3);
+    a.codes = (unsigned long long)ld_relaxed_s64(q + 4);
+    return a;
+}
+
+__device__ __forceinline__ void store_agg(Agg *p, const Agg &a) {
+    long long *q = reinterpret_cast<long long *>(p);
+    st_relaxed_s64(q + 0, a.nb);
+    st_relaxed_s64(q + 1, a.h);
+    st_relaxed_s64(q + 2, a.d);
+    st_relaxed_s64(q + 3, a.t);
+    st_relaxed_s64(q + 4, (long long)a.codes);
+}
+
+__device__ __forceinline__ Agg shfl_up_agg(const Agg &a, int o) {
+    Agg r;
+    r.nb = __shfl_up_sync(0xffffffffu, a.nb, o);
+    r.h = __shfl_up_sync(0xffffffffu, a.h, o);
+    r.d = __shfl_up_sync(0xffffffffu, a.d, o);
+    r.t = __shfl_up_sync(0xffffffffu, a.t, o);
+    r.codes = __shfl_up_sync(0xffffffffu, a.codes, o);
+    return r;
+}
+
+__device__ __forceinline__ Agg shfl_agg(const Agg &a, int src) {
+    Agg r;
+    r.nb = __shfl_sync(0xffffffffu, a.nb, src);
+    r.h = __shfl_sync(0xffffffffu, a.h, src);
+    r.d = __shfl_sync(0xffffffffu, a.d, src);
+    r.t = __shfl_sync(0xffffffffu, a.t, src);
+    r.codes = __shfl_sync(0xffffffffu, a.codes, src);
+    return r;
+}
+
+// Record an error in the device status word (first error wins).
+__device__ __forceinline__ void set_dev_status(int *status, int code) {
+    if (status) atomicCAS(status, DEV_OK, code);
+}
+
+__device__ __forceinline__ bool dev_failed(const int *status) {
+    return status && *((volatile const int *)status) != DEV_OK;
+}
+
+// FASTA line-state maps: a map sends each of the three states (LS, HD, SQ) to
+// a state, 2 bits per entry.  compose(f, g) applies f first, then g.
+__host__ __device__ __forceinline__ unsigned hmap_apply(unsigned m, unsigned s) {
+    return (m >> (2 * s)) & 3u;
+}
+__host__ __device__ __forceinline__ unsigned hmap_compose(unsigned f, unsigned g) {
+    return hmap_apply(g, hmap_apply(f, 0)) | (hmap_apply(g, hmap_apply(f, 1)) << 2) |
+           (hmap_apply(g, hmap_apply(f, 2)) << 4);
+}
+constexpr unsigned kHmapIdentity = 0u | (1u << 2) | (2u << 4);
+__host__ __device__ __forceinline__ unsigned hmap_const(unsigned s) {
+    return s | (s << 2) | (s << 4);
+}
+// One byte of the FASTA line-state machine.
+__host__ __device__ __forceinline__ unsigned hstep(unsigned s, uint8_t b) {
+    if (b == '\n') return HS_LS;
+    if (s == HS_LS) return b == '>' ? HS_HD : HS_SQ;
+    return s;
+}
+
+}  // namespace dnatok

@@ -1,0 +1,78 @@
+// handle.h -- the tokenizer handle behind the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+struct StreamState;  // host-streamed pipeline (stream.cu)
+struct BpeState;     // BPE tables and workspace (bpe.cu)
+
+struct dnatok_handle {
+    int mode = 0;
+    int k = 1;
+    int fmt = 0;
+    int device = 0;
+    int sm_count = 0;
+
+    int32_t lut_host[256];
+    int *d_lut = nullptr;  // CHAR table on the device
+
+    // look-back workspace (grows on demand)
+    dnatok::TileDesc *d_desc = nullptr;
+    long long desc_cap = 0;
+    int *d_tile_rec = nullptr;
+    long long rec_cap = 0;
+    unsigned long long *d_counter = nullptr;
+    int *d_status = nullptr;
+    unsigned epoch = 0;
+
+    dnatok::LaunchShape shape{16384, 512, 2};
+
+    StreamState *stream = nullptr;
+    BpeState *bpe = nullptr;
+
+    std::string last_error;
+};
+
+namespace dnatok {
+
+// Set the handle's (or the thread's) last error text and return `st`.
+dnatok_status fail(dnatok_handle *h, dnatok_status st, const std::string &msg);
+dnatok_status fail_cuda(dnatok_handle *h, cudaError_t e, const char *what);
+
+// Grow the look-back workspace for n_bytes of input with n_bnd boundaries in
+// the list (RAW); allocates (synchronously) only when it must grow.
+dnatok_status ensure_workspace(dnatok_handle *h, long long n_bytes, long long n_bnd,
+                               const LaunchShape &sh, cudaStream_t s);
+
+// Next launch epoch (descriptors are reset when the 24-bit epoch wraps).
+dnatok_status next_epoch(dnatok_handle *h, cudaStream_t s, unsigned *epoch);
+
+long long tiles_for(long long n_bytes, int head_pad, int tile);
+
+// Launch the tile kernel over one chunk (the CHAR / KMER / SYM core).
+dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const uint8_t *bytes,
+                              long long n_bytes, const long long *seq_offsets, long long n_bnd,
+                              void *out, long long out_cap, long long *offsets_out,
+                              long long offsets_cap, long long *totals_out, const Carry *carry_in,
+                              Carry *carry_out, int start_boundary, int end_boundary,
+                              cudaStream_t s);
+
+// BPE path (bpe.cu)
+dnatok_status bpe_create(dnatok_handle *h, const int32_t *merges, int32_t n_merges);
+void bpe_destroy(dnatok_handle *h);
+dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
+                         const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
+                         int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
+                         int64_t *totals_d, cudaStream_t s);
+
+// host-streamed pipeline (stream.cu)
+void stream_destroy(dnatok_handle *h);
+
+}  // namespace dnatok
