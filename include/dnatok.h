@@ -143,6 +143,22 @@ DNATOK_API dnatok_status dnatok_encode(dnatok_handle *h, const uint8_t *bytes_d,
                             int64_t offsets_capacity, int64_t *totals_d,
                             dnatok_cuda_stream stream);
 
+/*
+ * Encode from HOST buffers (the end-to-end form): copies host_bytes and
+ * host_seq_offsets (RAW) into device staging owned by the handle, runs the
+ * same kernels as dnatok_encode, and copies the record offsets and totals
+ * back to the HOST arrays id_offsets_host / totals_host (2 int64, may be
+ * NULL).  The ids stay on the device in ids_out_d (the input of an embedding
+ * lookup).  Page-locked (pinned) host buffers give full link bandwidth.
+ * Returns when the results are on the host (it synchronizes `stream`).
+ */
+DNATOK_API dnatok_status dnatok_encode_host(dnatok_handle *h, const uint8_t *host_bytes,
+                                            int64_t n_bytes, const int64_t *host_seq_offsets,
+                                            int64_t n_seq, int32_t *ids_out_d,
+                                            int64_t ids_capacity, int64_t *id_offsets_host,
+                                            int64_t offsets_capacity, int64_t *totals_host,
+                                            dnatok_cuda_stream stream);
+
 /* Wait for `stream`, then report any device-side error recorded by this
  * handle's kernels (clearing it). */
 DNATOK_API dnatok_status dnatok_sync(dnatok_handle *h, dnatok_cuda_stream stream);
@@ -153,13 +169,15 @@ DNATOK_API dnatok_status dnatok_last_error(const dnatok_handle *h, char *buf, si
 
 /* -------------------------------------------------------------- launch */
 
-/* Kernel launch shape for the CHAR / KMER tile kernel: bytes per tile
- * (4096, 8192, 16384 or 32768), threads per CTA (128, 256 or 512), and
- * resident CTAs per SM the grid is sized for (1..8). */
+/* Launch shape of the tokenization kernel: bytes per tile, threads per CTA,
+ * resident CTAs per SM the grid is sized for (1..8), and tiles per chunk
+ * (the unit of the cross-CTA look-back).  Supported (tile, threads, chunk):
+ * (8192, 256, 8), (16384, 256, 4), (16384, 256, 8), (32768, 512, 4). */
 typedef struct {
     int32_t tile_bytes;
     int32_t threads;
     int32_t ctas_per_sm;
+    int32_t chunk_tiles;
 } dnatok_launch_cfg;
 
 DNATOK_API dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg);

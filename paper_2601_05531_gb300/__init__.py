@@ -60,8 +60,8 @@ class Tokenizer:
     def reserve(self, max_bytes: int, max_seq: int = 1):
         binding.dnatok_reserve(self.h, max_bytes, max_seq)
 
-    def set_launch(self, tile_bytes: int, threads: int, ctas_per_sm: int):
-        binding.dnatok_set_launch(self.h, tile_bytes, threads, ctas_per_sm)
+    def set_launch(self, tile_bytes: int, threads: int, ctas_per_sm: int, chunk_tiles: int = 4):
+        binding.dnatok_set_launch(self.h, tile_bytes, threads, ctas_per_sm, chunk_tiles)
 
     def get_launch(self):
         return binding.dnatok_get_launch(self.h)

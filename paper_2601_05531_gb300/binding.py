@@ -36,7 +36,7 @@ class DnatokError(RuntimeError):
 
 class LaunchCfg(ctypes.Structure):
     _fields_ = [("tile_bytes", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32)]
 
 
 class Tables(ctypes.Structure):
@@ -69,6 +69,7 @@ def lib():
             "dnatok_max_tokens": (_ST, [_P, _I64, _I64, ctypes.POINTER(_I64)]),
             "dnatok_reserve": (_ST, [_P, _I64, _I64]),
             "dnatok_encode": (_ST, [_P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P]),
+            "dnatok_encode_host": (_ST, [_P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P]),
             "dnatok_sync": (_ST, [_P, _P]),
             "dnatok_last_error": (_ST, [_P, ctypes.c_char_p, ctypes.c_size_t]),
             "dnatok_get_launch": (_ST, [_P, ctypes.POINTER(LaunchCfg)]),
@@ -138,6 +139,14 @@ def dnatok_encode(h, bytes_d: int, n_bytes: int, seq_offsets_d: int, n_seq: int,
                                      stream), h)
 
 
+def dnatok_encode_host(h, host_bytes: int, n_bytes: int, host_seq_offsets: int, n_seq: int,
+                       ids_out_d: int, ids_capacity: int, id_offsets_host: int,
+                       offsets_capacity: int, totals_host: int, stream: int) -> int:
+    return check(lib().dnatok_encode_host(h, host_bytes, n_bytes, host_seq_offsets, n_seq,
+                                          ids_out_d, ids_capacity, id_offsets_host,
+                                          offsets_capacity, totals_host, stream), h)
+
+
 def dnatok_sync(h, stream: int) -> int:
     return check(lib().dnatok_sync(h, stream), h)
 
@@ -149,9 +158,10 @@ def dnatok_last_error(h) -> str:
 def dnatok_get_launch(h) -> tuple:
     c = LaunchCfg()
     check(lib().dnatok_get_launch(h, ctypes.byref(c)), h)
-    return (c.tile_bytes, c.threads, c.ctas_per_sm)
+    return (c.tile_bytes, c.threads, c.ctas_per_sm, c.chunk_tiles)
 
 
-def dnatok_set_launch(h, tile_bytes: int, threads: int, ctas_per_sm: int) -> None:
-    c = LaunchCfg(tile_bytes, threads, ctas_per_sm)
+def dnatok_set_launch(h, tile_bytes: int, threads: int, ctas_per_sm: int,
+                      chunk_tiles: int = 4) -> None:
+    c = LaunchCfg(tile_bytes, threads, ctas_per_sm, chunk_tiles)
     check(lib().dnatok_set_launch(h, ctypes.byref(c)), h)

@@ -73,7 +73,7 @@ dnatok_status ensure_workspace(dnatok_handle *h, long long n_bytes, long long n_
 
 dnatok_status next_epoch(dnatok_handle *h, cudaStream_t s, unsigned *epoch) {
     h->epoch++;
-    if ((h->epoch & 0xffffffu) == 0) {  // 24-bit wrap: forget every old descriptor
+    if ((h->epoch & ((1u << kEpochBits) - 1)) == 0) {  // epoch wrap: forget every old descriptor
         cudaError_t e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * h->desc_cap, s);
         if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
         h->epoch++;
@@ -97,14 +97,13 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
     p.n_bytes = n_bytes;
     p.seq_offsets = seq_offsets;
     p.n_bnd = n_bnd;
-    p.tile_rec = h->d_tile_rec;
     p.out = out;
     p.out_cap = out_cap;
     p.offsets_out = offsets_out;
     p.offsets_cap = offsets_cap;
     p.totals_out = totals_out;
     p.desc = h->d_desc;
-    p.tile_counter = h->d_counter;
+    p.tile_counter = h->d_counter;  // reset by the last CTA of every launch
     p.carry_in = carry_in;
     p.carry_out = carry_out;
     p.status = h->d_status;
@@ -113,6 +112,9 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
     p.start_boundary = start_boundary;
     p.end_boundary = end_boundary;
     p.head_pad = (int)((uintptr_t)bytes & 15u);
+    p.lut_keeps_bases = 1;
+    for (const char *c = "ACGTacgt"; *c; ++c)
+        if (h->lut_host[(unsigned char)*c] < 0) p.lut_keeps_bases = 0;
     cudaError_t e;
     if (n_bytes == 0) {
         e = launch_empty_chunk(p, bsrc == BSRC_LIST, s);
@@ -120,16 +122,9 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
         return DNATOK_OK;
     }
     p.n_tiles = tiles_for(n_bytes, p.head_pad, sh.tile);
+    p.n_chunks = (p.n_tiles + sh.chunk_tiles - 1) / sh.chunk_tiles;
     st = next_epoch(h, s, &p.epoch);
     if (st != DNATOK_OK) return st;
-    if (bsrc == BSRC_LIST) {
-        e = launch_plan_list(seq_offsets, n_bnd, n_bytes, p.head_pad, sh.tile, p.n_tiles,
-                             h->d_tile_rec, h->d_counter, h->d_status, s);
-        if (e != cudaSuccess) return fail_cuda(h, e, "plan launch");
-    } else {
-        e = cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s);
-        if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(counter)");
-    }
     e = launch_tile_kernel(mode, bsrc, p, sh, s, h->sm_count);
     if (e != cudaSuccess) return fail_cuda(h, e, "tile kernel launch");
     return DNATOK_OK;
@@ -173,7 +168,8 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
     if (e == cudaSuccess) e = cudaMalloc(&h->d_lut, sizeof(int) * 256);
     if (e == cudaSuccess)
         e = cudaMemcpy(h->d_lut, h->lut_host, sizeof(int) * 256, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_counter, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_counter, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -207,6 +203,10 @@ void dnatok_destroy(dnatok_handle *h) {
     cudaFree(h->d_tile_rec);
     cudaFree(h->d_counter);
     cudaFree(h->d_status);
+    cudaFree(h->d_stage_bytes);
+    cudaFree(h->d_stage_offs);
+    cudaFree(h->d_stage_out_offs);
+    cudaFree(h->d_stage_totals);
     delete h;
 }
 
@@ -272,6 +272,72 @@ dnatok_status dnatok_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_
                            nullptr, 1, 1, s);
 }
 
+static dnatok_status grow(dnatok_handle *h, void **buf, long long *cap, long long need,
+                          size_t elem, const char *what) {
+    if (need <= *cap) return DNATOK_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaDeviceSynchronize");
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    long long c = need + need / 8 + 64;
+    e = cudaMalloc(buf, elem * c);
+    if (e != cudaSuccess) return fail_cuda(h, e, what);
+    *cap = c;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_encode_host(dnatok_handle *h, const uint8_t *host_bytes, int64_t n_bytes,
+                                 const int64_t *host_seq_offsets, int64_t n_seq, int32_t *ids_out_d,
+                                 int64_t ids_capacity, int64_t *id_offsets_host,
+                                 int64_t offsets_capacity, int64_t *totals_host,
+                                 dnatok_cuda_stream stream) {
+    if (!h) return DNATOK_ERR_ARG;
+    if (n_bytes < 0 || (n_bytes > 0 && !host_bytes)) return fail(h, DNATOK_ERR_ARG, "bad input bytes");
+    if (h->fmt == DNATOK_RAW && (!host_seq_offsets || n_seq < 0))
+        return fail(h, DNATOK_ERR_ARG, "RAW needs seq_offsets");
+    if (!id_offsets_host || offsets_capacity < 1) return fail(h, DNATOK_ERR_ARG, "bad id_offsets");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    dnatok_status st = grow(h, (void **)&h->d_stage_bytes, &h->stage_bytes_cap, n_bytes, 1,
+                            "cudaMalloc(staging bytes)");
+    if (st != DNATOK_OK) return st;
+    const long long n_off_in = (h->fmt == DNATOK_RAW) ? n_seq + 1 : 0;
+    st = grow(h, (void **)&h->d_stage_offs, &h->stage_offs_cap, n_off_in, 8, "cudaMalloc(staging offsets)");
+    if (st != DNATOK_OK) return st;
+    st = grow(h, (void **)&h->d_stage_out_offs, &h->stage_out_offs_cap, offsets_capacity, 8,
+              "cudaMalloc(staging id offsets)");
+    if (st != DNATOK_OK) return st;
+    if (!h->d_stage_totals) {
+        cudaError_t e = cudaMalloc(&h->d_stage_totals, 2 * sizeof(long long));
+        if (e != cudaSuccess) return fail_cuda(h, e, "cudaMalloc(totals)");
+    }
+    cudaError_t e = cudaSuccess;
+    if (n_bytes > 0)
+        e = cudaMemcpyAsync(h->d_stage_bytes, host_bytes, n_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_off_in > 0)
+        e = cudaMemcpyAsync(h->d_stage_offs, host_seq_offsets, 8 * n_off_in, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemcpyAsync(H2D)");
+    st = dnatok_encode(h, h->d_stage_bytes, n_bytes,
+                       h->fmt == DNATOK_RAW ? reinterpret_cast<int64_t *>(h->d_stage_offs) : nullptr,
+                       n_seq, ids_out_d, ids_capacity,
+                       reinterpret_cast<int64_t *>(h->d_stage_out_offs), offsets_capacity,
+                       reinterpret_cast<int64_t *>(h->d_stage_totals), stream);
+    if (st != DNATOK_OK) return st;
+    long long tot[2] = {0, 0};
+    e = cudaMemcpyAsync(tot, h->d_stage_totals, sizeof(tot), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemcpyAsync(D2H totals)");
+    const long long n_write = (tot[1] + 1 < offsets_capacity) ? tot[1] + 1 : offsets_capacity;
+    e = cudaMemcpyAsync(id_offsets_host, h->d_stage_out_offs, 8 * n_write, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemcpyAsync(D2H offsets)");
+    if (totals_host) {
+        totals_host[0] = tot[0];
+        totals_host[1] = tot[1];
+    }
+    return dnatok_sync(h, stream);
+}
+
 dnatok_status dnatok_sync(dnatok_handle *h, dnatok_cuda_stream stream) {
     if (!h) return DNATOK_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
@@ -282,6 +348,8 @@ dnatok_status dnatok_sync(dnatok_handle *h, dnatok_cuda_stream stream) {
     if (st == DEV_OK) return DNATOK_OK;
     const int zero = 0;
     cudaMemcpy(h->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    // a launch that stopped early may have left its tile counters set
+    cudaMemset(h->d_counter, 0, 2 * sizeof(unsigned long long));
     if (st == DEV_TIMEOUT) return fail(h, DNATOK_ERR_TIMEOUT, "a bounded device wait ran out");
     if (st == DEV_BAD_OFFSETS)
         return fail(h, DNATOK_ERR_DEVICE_DATA,
@@ -301,12 +369,13 @@ dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg) 
     cfg->tile_bytes = h->shape.tile;
     cfg->threads = h->shape.threads;
     cfg->ctas_per_sm = h->shape.ctas_per_sm;
+    cfg->chunk_tiles = h->shape.chunk_tiles;
     return DNATOK_OK;
 }
 
 dnatok_status dnatok_set_launch(dnatok_handle *h, const dnatok_launch_cfg *cfg) {
     if (!h || !cfg) return DNATOK_ERR_ARG;
-    LaunchShape sh{cfg->tile_bytes, cfg->threads, cfg->ctas_per_sm};
+    LaunchShape sh{cfg->tile_bytes, cfg->threads, cfg->ctas_per_sm, cfg->chunk_tiles};
     if (!tile_shape_supported(sh) || sh.ctas_per_sm < 1 || sh.ctas_per_sm > 8)
         return fail(h, DNATOK_ERR_ARG, "unsupported launch shape");
     h->shape = sh;

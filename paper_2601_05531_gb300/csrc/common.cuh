@@ -94,16 +94,35 @@ struct Carry {
     unsigned pad;
 };
 
-// One look-back descriptor per tile.  The aggregate and the inclusive prefix
-// live in separate slots so a reader that saw LB_AGG never races the later
-// LB_INCL write.
-struct __align__(128) TileDesc {
-    unsigned status;   // epoch << 2 | LB_*
+// One look-back descriptor per tile: four 64-bit words that first hold the
+// tile's own scan element (flag LB_AGG) and are then overwritten by the
+// inclusive prefix through the tile (flag LB_INCL).  Every word carries a tag
+// (18-bit launch epoch, 2-bit flag) in its top 20 bits and a 44-bit value
+// below, so status and payload arrive in one round trip and a reader that
+// catches the overwrite half done sees mixed tags and simply polls again.
+//   aggregate: nb | (h << 22 | d) | t | codes   (h, d < 2^22: tile-local)
+//   inclusive: nb | d | t | codes               (h = 0: a prefix from the
+//                                                stream start opens at a
+//                                                boundary)
+// The k-mer symbol count of `codes` is not stored: it equals
+// min(open symbols, k - 1), open = (nb > 0 ? t : h).
+struct __align__(64) TileDesc {
+    unsigned long long w[4];
     unsigned hstatus;  // FASTA line-state map: epoch << 8 | flag << 6 | map
-    unsigned pad0, pad1;
-    Agg agg;           // the tile's own scan element
-    Agg incl;          // inclusive prefix through this tile
+    unsigned pad[7];
 };
+
+constexpr unsigned long long kValMask = (1ull << 44) - 1;
+constexpr unsigned kEpochBits = 18;
+
+__host__ __device__ __forceinline__ unsigned desc_tag(unsigned epoch, unsigned flag) {
+    return ((epoch & ((1u << kEpochBits) - 1)) << 2) | flag;
+}
+
+__host__ __device__ __forceinline__ int codes_open_count(const Agg &a, int k) {
+    const long long open = a.nb > 0 ? a.t : a.h;
+    return (int)(open < k - 1 ? open : (k - 1 > 0 ? k - 1 : 0));
+}
 
 // ---------------------------------------------------------------- PTX
 
@@ -170,6 +189,57 @@ __device__ __forceinline__ long long ld_relaxed_s64(const long long *p) {
 
 __device__ __forceinline__ void st_relaxed_s64(long long *p, long long v) {
     asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_v2u64(unsigned long long *p, unsigned long long a,
+                                                 unsigned long long b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b)
+                 : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v2u64(const unsigned long long *p,
+                                                 unsigned long long &a, unsigned long long &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Publish a tile's scan element (LB_AGG) or inclusive prefix (LB_INCL).
+__device__ __forceinline__ void publish_desc(TileDesc *d, const Agg &a, unsigned epoch,
+                                             unsigned flag) {
+    const unsigned long long tg = (unsigned long long)desc_tag(epoch, flag) << 44;
+    const unsigned long long w1 = (flag == LB_AGG)
+                                      ? (((unsigned long long)a.h << 22) | (unsigned long long)a.d)
+                                      : (unsigned long long)a.d;
+    st_relaxed_v2u64(d->w, tg | ((unsigned long long)a.nb & kValMask), tg | (w1 & kValMask));
+    st_relaxed_v2u64(d->w + 2, tg | ((unsigned long long)a.t & kValMask),
+                     tg | (a.codes & kValMask));
+}
+// Decode four words read from a descriptor: LB_AGG / LB_INCL, or LB_EMPTY
+// when they are stale (another epoch) or torn (mixed tags).
+__device__ __forceinline__ unsigned decode_desc(unsigned long long w0, unsigned long long w1,
+                                                unsigned long long w2, unsigned long long w3,
+                                                unsigned epoch, int k, Agg &a) {
+    const unsigned tg = (unsigned)(w0 >> 44);
+    if ((unsigned)(w1 >> 44) != tg || (unsigned)(w2 >> 44) != tg || (unsigned)(w3 >> 44) != tg)
+        return LB_EMPTY;
+    if ((tg >> 2) != (epoch & ((1u << kEpochBits) - 1))) return LB_EMPTY;
+    const unsigned flag = tg & 3u;
+    if (flag != LB_AGG && flag != LB_INCL) return LB_EMPTY;
+    a.nb = (long long)(w0 & kValMask);
+    if (flag == LB_AGG) {
+        a.h = (long long)((w1 & kValMask) >> 22);
+        a.d = (long long)(w1 & ((1ull << 22) - 1));
+    } else {
+        a.h = 0;
+        a.d = (long long)(w1 & kValMask);
+    }
+    a.t = (long long)(w2 & kValMask);
+    a.codes = ((unsigned long long)codes_open_count(a, k) << 58) | (w3 & kValMask);
+    return flag;
 }
 
 __device__ __forceinline__ Agg load_agg(const Agg *p) {

@@ -32,7 +32,16 @@ struct dnatok_handle {
     int *d_status = nullptr;
     unsigned epoch = 0;
 
-    dnatok::LaunchShape shape{16384, 512, 2};
+    dnatok::LaunchShape shape{16384, 256, 4, 8};
+
+    // device staging of dnatok_encode_host
+    uint8_t *d_stage_bytes = nullptr;
+    long long stage_bytes_cap = 0;
+    long long *d_stage_offs = nullptr;
+    long long stage_offs_cap = 0;
+    long long *d_stage_out_offs = nullptr;
+    long long stage_out_offs_cap = 0;
+    long long *d_stage_totals = nullptr;
 
     StreamState *stream = nullptr;
     BpeState *bpe = nullptr;

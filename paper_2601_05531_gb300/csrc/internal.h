@@ -5,24 +5,22 @@
 #include <cstdint>
 #include <string>
 
-#include "../../include/dnatok.h"
+#include "dnatok.h"
 
 namespace dnatok {
 
 struct TileParams;
 
 struct LaunchShape {
-    int tile;
-    int threads;
-    int ctas_per_sm;
+    int tile;         // bytes per tile
+    int threads;      // threads per CTA
+    int ctas_per_sm;  // resident CTAs per SM the grid is sized for
+    int chunk_tiles;  // tiles per chunk (the unit of the look-back)
 };
 
 bool tile_shape_supported(const LaunchShape &sh);
 cudaError_t launch_tile_kernel(int mode, int bsrc, const TileParams &p, const LaunchShape &sh,
                                cudaStream_t s, int sm_count);
-cudaError_t launch_plan_list(const long long *off, long long n_bnd, long long n_bytes, int head_pad,
-                             int tile, long long n_tiles, int *tile_rec,
-                             unsigned long long *counter, int *status, cudaStream_t s);
 cudaError_t launch_empty_chunk(const TileParams &p, int list_source, cudaStream_t s);
 
 }  // namespace dnatok

@@ -7,31 +7,39 @@
 
 namespace dnatok {
 
-template <int MODE, int BSRC, int NT, int TILE>
+template <int MODE, int BSRC, int NT, int TILE, int NSUB>
 static cudaError_t launch_one(const TileParams &p, cudaStream_t s, int sm_count, int ctas_per_sm) {
     constexpr int SMEM = tile_smem_bytes(TILE, NT);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(tile_kernel<MODE, BSRC, NT, TILE>,
+        cudaError_t e = cudaFuncSetAttribute(tile_kernel<MODE, BSRC, NT, TILE, NSUB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     long long grid = (long long)sm_count * ctas_per_sm;
-    if (grid > p.n_tiles) grid = p.n_tiles;
+    if (grid > p.n_chunks) grid = p.n_chunks;
     if (grid < 1) grid = 1;
-    tile_kernel<MODE, BSRC, NT, TILE><<<(unsigned)grid, NT, SMEM, s>>>(p);
+    tile_kernel<MODE, BSRC, NT, TILE, NSUB><<<(unsigned)grid, NT, SMEM, s>>>(p);
     return cudaGetLastError();
 }
+
+// The supported shapes: tile bytes, threads, tiles per chunk.
+#define DNATOK_SHAPES(X)        \
+    X(8192, 256, 8)             \
+    X(16384, 256, 4)            \
+    X(16384, 256, 8)            \
+    X(32768, 512, 4)
 
 template <int MODE, int BSRC>
 static cudaError_t launch_shape(const TileParams &p, const LaunchShape &sh, cudaStream_t s,
                                 int sm_count) {
     const int c = sh.ctas_per_sm;
-    if (sh.tile == 8192 && sh.threads == 256) return launch_one<MODE, BSRC, 256, 8192>(p, s, sm_count, c);
-    if (sh.tile == 16384 && sh.threads == 256) return launch_one<MODE, BSRC, 256, 16384>(p, s, sm_count, c);
-    if (sh.tile == 16384 && sh.threads == 512) return launch_one<MODE, BSRC, 512, 16384>(p, s, sm_count, c);
-    if (sh.tile == 32768 && sh.threads == 512) return launch_one<MODE, BSRC, 512, 32768>(p, s, sm_count, c);
+#define DNATOK_TRY(T, N, C)                                                   \
+    if (sh.tile == T && sh.threads == N && sh.chunk_tiles == C)               \
+        return launch_one<MODE, BSRC, N, T, C>(p, s, sm_count, c);
+    DNATOK_SHAPES(DNATOK_TRY)
+#undef DNATOK_TRY
     return cudaErrorInvalidValue;
 }
 

@@ -1,41 +1,9 @@
-// tile_launch.cu -- dispatch of the tile kernel, the RAW planning
-// kernel (validates seq_offsets and maps tiles to their record boundaries) and
-// the zero-byte chunk kernel, with their host-side launchers.
+// tile_launch.cu -- dispatch of the tile kernel and the zero-byte chunk
+// kernel, with their host-side launchers.
 #include "internal.h"
 #include "tile_kernel.cuh"
 
 namespace dnatok {
-
-// RAW one-shot: check seq_offsets (non-decreasing, [0] = 0, [last] = n_bytes),
-// record for each tile the first boundary at or after its first byte, and
-// reset the tile counter.
-__global__ void plan_list_kernel(const long long *off, long long n_bnd, long long n_bytes,
-                                 int head_pad, int tile, long long n_tiles, int *tile_rec,
-                                 unsigned long long *counter, int *status) {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    if (gid == 0) *counter = 0ull;
-    for (long long i = gid; i < n_bnd; i += stride) {
-        const long long v = off[i];
-        bool bad = v < 0 || v > n_bytes;
-        if (i == 0 && v != 0) bad = true;
-        if (i == n_bnd - 1 && v != n_bytes) bad = true;
-        if (i > 0 && off[i - 1] > v) bad = true;
-        if (bad) set_dev_status(status, DEV_BAD_OFFSETS);
-    }
-    for (long long t = gid; t < n_tiles; t += stride) {
-        long long first = t * (long long)tile - head_pad;
-        if (first < 0) first = 0;
-        long long lo = 0, hi = n_bnd;
-        while (lo < hi) {
-            const long long mid = (lo + hi) >> 1;
-            if (off[mid] < first) lo = mid + 1;
-            else hi = mid;
-        }
-        tile_rec[t] = (int)lo;
-    }
-    if (gid == 0) tile_rec[n_tiles] = (int)n_bnd;
-}
 
 // A chunk with no bytes: only boundaries (all at one position).  Closes the
 // open record (emitting its UNK tail in k-mer mode) and writes the offsets.
@@ -78,8 +46,9 @@ cudaError_t launch_mode(int bsrc, const TileParams &p, const LaunchShape &sh, cu
                         int sm_count);
 
 bool tile_shape_supported(const LaunchShape &sh) {
-    return (sh.tile == 8192 && sh.threads == 256) || (sh.tile == 16384 && sh.threads == 256) ||
-           (sh.tile == 16384 && sh.threads == 512) || (sh.tile == 32768 && sh.threads == 512);
+    return (sh.tile == 8192 && sh.threads == 256 && sh.chunk_tiles == 8) ||
+           (sh.tile == 16384 && sh.threads == 256 && (sh.chunk_tiles == 4 || sh.chunk_tiles == 8)) ||
+           (sh.tile == 32768 && sh.threads == 512 && sh.chunk_tiles == 4);
 }
 
 cudaError_t launch_tile_kernel(int mode, int bsrc, const TileParams &p, const LaunchShape &sh,
@@ -90,18 +59,6 @@ cudaError_t launch_tile_kernel(int mode, int bsrc, const TileParams &p, const La
     case MODE_SYM: return launch_mode<MODE_SYM>(bsrc, p, sh, s, sm_count);
     default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_plan_list(const long long *off, long long n_bnd, long long n_bytes, int head_pad,
-                             int tile, long long n_tiles, int *tile_rec,
-                             unsigned long long *counter, int *status, cudaStream_t s) {
-    long long work = n_bnd > n_tiles ? n_bnd : n_tiles;
-    int blocks = (int)((work + 255) / 256);
-    if (blocks < 1) blocks = 1;
-    if (blocks > 1024) blocks = 1024;
-    plan_list_kernel<<<blocks, 256, 0, s>>>(off, n_bnd, n_bytes, head_pad, tile, n_tiles, tile_rec,
-                                            counter, status);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_empty_chunk(const TileParams &p, int list_source, cudaStream_t s) {

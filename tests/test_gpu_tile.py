@@ -13,7 +13,7 @@ from tests import _golden as G
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(8192, 256, 4), (16384, 256, 3), (16384, 512, 2), (32768, 512, 2)]
+SHAPES = [(8192, 256, 4, 8), (16384, 256, 4, 4), (16384, 256, 3, 8), (32768, 512, 2, 4)]
 
 
 @pytest.fixture(scope="module")
