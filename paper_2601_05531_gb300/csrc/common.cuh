@@ -66,7 +66,31 @@ __host__ __device__ __forceinline__ unsigned long long codes_concat(unsigned lon
     return ((unsigned long long)n << 58) | bits;
 }
 
-__host__ __device__ __forceinline__ Agg agg_combine(const Agg &A, const Agg &B, int k) {
+// Division by the k-mer length without a division instruction sequence:
+// floor(x / k) = high 64 bits of x * ceil(2^64 / k), exact for x < 2^44
+// (the error term x / 2^64 stays below the gap 1/k between fractions).
+struct KDiv {
+    int k;
+    unsigned long long m64;  // ceil(2^64 / k), k >= 2
+    unsigned m32;            // ceil(2^32 / k), k >= 2: exact for x < 2^17
+    __device__ __forceinline__ long long div(long long x) const {
+        return k == 1 ? x : (long long)__umul64hi((unsigned long long)x, m64);
+    }
+    __device__ __forceinline__ unsigned div32(unsigned x) const {
+        return k == 1 ? x : __umulhi(x, m32);
+    }
+};
+
+__device__ __forceinline__ KDiv make_kdiv(int k) {
+    KDiv d;
+    d.k = k;
+    d.m64 = k > 1 ? ~0ull / (unsigned long long)k + 1ull : 0ull;
+    d.m32 = k > 1 ? (unsigned)((0x100000000ull + (unsigned long long)k - 1) / (unsigned long long)k) : 0u;
+    return d;
+}
+
+__device__ __forceinline__ Agg agg_combine(const Agg &A, const Agg &B, const KDiv &kd) {
+    const int k = kd.k;
     Agg r;
     r.nb = A.nb + B.nb;
     if (A.nb == 0) {
@@ -75,11 +99,11 @@ __host__ __device__ __forceinline__ Agg agg_combine(const Agg &A, const Agg &B, 
         r.t = B.t;
     } else if (B.nb == 0) {
         r.h = A.h;
-        r.d = A.d - A.t / k + (A.t + B.h) / k;
+        r.d = A.d - kd.div(A.t) + kd.div(A.t + B.h);
         r.t = A.t + B.h;
     } else {
         r.h = A.h;
-        r.d = A.d - A.t / k + (A.t + B.h + k - 1) / k + B.d;
+        r.d = A.d - kd.div(A.t) + kd.div(A.t + B.h + k - 1) + B.d;
         r.t = B.t;
     }
     r.codes = (B.nb > 0) ? B.codes : codes_concat(A.codes, B.codes, k);
@@ -169,6 +193,25 @@ __device__ __forceinline__ void tma_load_1d(void *smem_dst, const void *gsrc, un
             "r"(smem_addr(smem_dst)),
         "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// 1-D TMA bulk copy shared -> global (bulk-group completion).  Both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_store_1d(void *gdst, const void *ssrc, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_addr(ssrc)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until this thread's bulk stores have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// Wait until this thread's bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {

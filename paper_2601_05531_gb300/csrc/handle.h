@@ -32,7 +32,7 @@ struct dnatok_handle {
     int *d_status = nullptr;
     unsigned epoch = 0;
 
-    dnatok::LaunchShape shape{16384, 256, 4, 8};
+    dnatok::LaunchShape shape{16384, 256, 4, 8};  // tile, threads, CTAs per SM, tiles per chunk
 
     // device staging of dnatok_encode_host
     uint8_t *d_stage_bytes = nullptr;

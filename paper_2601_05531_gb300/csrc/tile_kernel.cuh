@@ -236,67 +236,79 @@ static __device__ __noinline__ Agg lookback_counts(const TileParams &p, long lon
                                                     const Agg &carry) {
     const int lane = threadIdx.x & 31;
     const int k = p.k;
+    const KDiv kd = make_kdiv(k);
     Agg acc = agg_identity();
     long long base = t;
     for (;;) {
         const long long idx0 = base - 128 + 4 * lane;
+        const unsigned ep = p.epoch & ((1u << kEpochBits) - 1);
         Agg mine;
-        int spins = 0;
+        int spins = 0, sleep_ns = 32;
         int lstar;
         for (;;) {
-            // issue all eight 16-byte loads first, then decode
-            unsigned long long w[4][4];
+            // cheap poll: the tag word of each of this lane's four tiles
+            unsigned fl[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const long long idx = idx0 + j;
                 if (idx >= 0) {
-                    ld_relaxed_v2u64(p.desc[idx].w, w[j][0], w[j][1]);
-                    ld_relaxed_v2u64(p.desc[idx].w + 2, w[j][2], w[j][3]);
+                    const unsigned tg = (unsigned)(ld_relaxed_u64(p.desc[idx].w) >> 44);
+                    fl[j] = ((tg >> 2) == ep) ? (tg & 3u) : LB_EMPTY;
+                    if (fl[j] != LB_AGG && fl[j] != LB_INCL) fl[j] = LB_EMPTY;
                 } else {
-                    w[j][0] = w[j][1] = w[j][2] = w[j][3] = 0ull;
+                    fl[j] = LB_INCL;  // before the chunk: the carry, then nothing
                 }
             }
-            // fold this lane's tiles backward, stopping at an inclusive prefix
-            mine = agg_identity();
-            bool found = false, empty_above = false;
+            int hi = -1;
+            bool empty_above = false;
 #pragma unroll
             for (int j = 3; j >= 0; --j) {
-                if (found) continue;
-                const long long idx = idx0 + j;
-                Agg a;
-                unsigned f;
-                if (idx >= 0) {
-                    f = decode_desc(w[j][0], w[j][1], w[j][2], w[j][3], p.epoch, k, a);
-                } else {  // before the chunk: the carry, then nothing
-                    f = LB_INCL;
-                    a = (idx == -1) ? carry : agg_identity();
-                }
-                if (f == LB_EMPTY) {
-                    empty_above = true;
-                    continue;
-                }
-                mine = agg_combine(a, mine, k);
-                if (f == LB_INCL) found = true;
+                if (hi >= 0) continue;
+                if (fl[j] == LB_INCL) hi = j;
+                else if (fl[j] == LB_EMPTY) empty_above = true;
             }
-            const unsigned has_incl = __ballot_sync(0xffffffffu, found);
+            const unsigned has_incl = __ballot_sync(0xffffffffu, hi >= 0);
             lstar = has_incl ? 31 - __clz(has_incl) : -1;
             // only the tiles after the nearest inclusive prefix must be ready
-            const bool ready = lane < lstar || !empty_above;
-            if (__all_sync(0xffffffffu, ready)) break;
+            bool ok = lane < lstar || !empty_above;
+            if (__all_sync(0xffffffffu, ok)) {
+                // full read of the tiles this lane contributes, folded backward
+                mine = agg_identity();
+                if (lane >= lstar) {
+#pragma unroll
+                    for (int j = 3; j >= 0; --j) {
+                        if (j < (hi < 0 ? 0 : hi)) continue;
+                        const long long idx = idx0 + j;
+                        Agg a;
+                        if (idx >= 0) {
+                            unsigned long long w0, w1, w2, w3;
+                            ld_relaxed_v2u64(p.desc[idx].w, w0, w1);
+                            ld_relaxed_v2u64(p.desc[idx].w + 2, w2, w3);
+                            // a torn or changed slot sends the whole warp back to polling
+                            if (decode_desc(w0, w1, w2, w3, p.epoch, k, a) != fl[j]) ok = false;
+                        } else {
+                            a = (idx == -1) ? carry : agg_identity();
+                        }
+                        mine = agg_combine(a, mine, kd);
+                    }
+                }
+                if (__all_sync(0xffffffffu, ok)) break;
+            }
             if (++spins > kSpinLimit || dev_failed(p.status)) {
                 if (lane == 0) set_dev_status(p.status, DEV_TIMEOUT);
                 return agg_identity();
             }
-            if (spins > 16) __nanosleep(64);
+            __nanosleep(sleep_ns);
+            if (sleep_ns < 1024) sleep_ns <<= 1;
         }
         if (lane < lstar) mine = agg_identity();
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             Agg u = shfl_up_agg(mine, o);
-            if (lane >= o) mine = agg_combine(u, mine, k);
+            if (lane >= o) mine = agg_combine(u, mine, kd);
         }
         const Agg win = shfl_agg(mine, 31);
-        acc = agg_combine(win, acc, k);
+        acc = agg_combine(win, acc, kd);
         if (lstar >= 0) return acc;
         base -= 128;
     }
@@ -376,12 +388,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
     __shared__ long long s_trb[NSUB + 1];
     __shared__ Agg s_tagg[NSUB];
     __shared__ Agg s_prefix, s_cagg;
+    __shared__ long long s_T0, s_R0, s_ttok;
+    __shared__ unsigned long long s_pcodes;
+    __shared__ unsigned s_Jr;
     __shared__ unsigned s_tmap[NSUB + 1], s_hchunk, s_hend;
     __shared__ long long s_red[NW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k = (MODE == MODE_KMER) ? p.k : 1;
-    const unsigned kmagic = (unsigned)((0x100000000ull + k - 1) / k);  // n / k for n < 2^17
+    const KDiv kd = make_kdiv(k);
+    const unsigned kmagic = kd.m32;  // n / k = umulhi(n, kmagic) for n < 2^17, k >= 2
 
     for (int i = tid; i < 256; i += NT) {
         uint8_t c;
@@ -428,6 +444,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
         const int a_lo = (vlo + 15) & ~15, a_hi = vhi & ~15;
         uint8_t *tb = tbuf0 + b * TILE;
         if (tid == 0) {
+            bulk_wait_read();  // a bulk store from this buffer must have read it
+            // the ragged ends (first and last tile of the input only)
+            for (int i = vlo; i < (a_lo < vhi ? a_lo : vhi); ++i) tb[i] = abase[rel_lo + i];
+            for (int i = (a_lo > a_hi ? a_lo : a_hi); i < vhi; ++i)
+                if (i >= vlo) tb[i] = abase[rel_lo + i];
             fence_proxy_async_shared();
             if (a_hi > a_lo) {
                 mbar_arrive_expect_tx(&mbar[b], (unsigned)(a_hi - a_lo));
@@ -436,13 +457,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&mbar[b]))
                              : "memory");
             }
-        }
-        if (tid < 16) {
-            const int i = vlo + tid;
-            if (i < (a_lo < vhi ? a_lo : vhi)) tb[i] = abase[rel_lo + i];
-        } else if (tid < 32) {
-            const int i = (a_lo > a_hi ? a_lo : a_hi) + (tid - 16);
-            if (i >= vlo && i < vhi) tb[i] = abase[rel_lo + i];
         }
         in_flight[b] = true;
     };
@@ -531,7 +545,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
         }
 
         Agg cagg = agg_identity();
-        Agg Pr = agg_identity();
         unsigned hrun = kHmapIdentity;
         for (int it = 0; it < n_items; ++it) {
             const int pass = (BSRC == BSRC_FASTA) ? (it / nt) : (it < nt ? 1 : 2);
@@ -790,7 +803,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                 long long dsum = 0;
                 for (long long i = tid; i + 1 < nb; i += NT) {
                     const unsigned a = bnd_kept(i), b = bnd_kept(i + 1);
-                    dsum += b > a ? (b - a + k - 1) / k : 0;
+                    dsum += b > a ? kd.div32(b - a + k - 1) : 0;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
@@ -807,7 +820,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     } else {
                         a.h = bnd_kept(0);
                         a.t = K - bnd_kept(nb - 1);
-                        a.d = d + a.t / k;
+                        a.d = d + kd.div32((unsigned)a.t);
                         open = a.t;
                     }
                     unsigned long long codes = 0;
@@ -829,7 +842,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     }
                     a.codes = codes;
                     s_tagg[ti] = a;
-                    cagg = agg_combine(cagg, a, k);
+                    cagg = agg_combine(cagg, a, kd);
                     if (ti == nt - 1) {
                         s_cagg = cagg;
                         if (c > 0) publish_desc(&p.desc[c], cagg, p.epoch, LB_AGG);
@@ -841,7 +854,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     if (warp == 0) {
                         const Agg pre = (c == 0) ? carry : lookback_counts(p, c, carry);
                         if (lane == 0) {
-                            const Agg incl = agg_combine(pre, s_cagg, k);
+                            const Agg incl = agg_combine(pre, s_cagg, kd);
                             publish_desc(&p.desc[c], incl, p.epoch, LB_INCL);
                             s_prefix = pre;
                             if (c == p.n_chunks - 1) {
@@ -864,18 +877,27 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                         failed = true;
                         break;
                     }
-                    Pr = s_prefix;
                 }
                 continue;
             }
 
             // ----------------------------------------------------- emit (pass 2)
-            const Agg Pf = Pr;
-            const long long T0 = (Pf.nb > 0) ? Pf.d : 0;
-            const long long R0 = Pf.nb;
-            const long long J = (Pf.nb > 0) ? Pf.t : Pf.h;
-            const unsigned Jr = (unsigned)(J % k);
-
+            // thread 0 advances the running prefix; everyone reads its fields
+            if (tid == 0) {
+                const Agg Pf = s_prefix;
+                const long long J = (Pf.nb > 0) ? Pf.t : Pf.h;
+                const Agg after = agg_combine(Pf, s_tagg[ti], kd);
+                s_T0 = (Pf.nb > 0) ? Pf.d : 0;
+                s_R0 = Pf.nb;
+                s_Jr = (unsigned)(J - kd.div(J) * k);
+                s_pcodes = Pf.codes;
+                s_ttok = after.d - s_T0;
+                s_prefix = after;  // read by no one until the next tile's emission
+            }
+            __syncthreads();
+            const long long T0 = s_T0;
+            const long long R0 = s_R0;
+            const unsigned Jr = s_Jr;
             if (MODE != MODE_KMER || k == 1) {
                 if (MODE == MODE_CHAR && !fast) {
 #pragma unroll
@@ -911,8 +933,23 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                 const unsigned unk = 1u << (2 * k);
                 const unsigned cmask = unk - 1u;
                 const unsigned nkm = (1u << k) - 1u;
+                // The tile's ids are staged in its (now free) byte buffer and leave
+                // with one bulk copy when they fit and the output is 16-byte aligned.
+                const long long tile_tokens = s_ttok;
+                const bool staged = ((reinterpret_cast<uintptr_t>(p.out) & 15u) == 0) &&
+                                    tile_tokens + 4 <= TILE / 4;
+                int *stg = reinterpret_cast<int *>(tbuf0 + cur * TILE);
+                const unsigned shift = (unsigned)(T0 & 3);
+                auto put = [&](unsigned u, unsigned id) {  // u: token index within the tile
+                    if (staged) {
+                        stg[u + shift] = (int)id;
+                    } else {
+                        const long long o = T0 + u;
+                        if (o < p.out_cap) static_cast<int *>(p.out)[o] = (int)id;
+                    }
+                };
                 if (tid == 0) {  // the prefix's partial k-mer becomes word -1
-                    const unsigned long long pcodes = Pf.codes;
+                    const unsigned long long pcodes = s_pcodes;
                     const int cnt = codes_count(pcodes);
                     unsigned w = 0, nbits = 0;
                     for (int q = 0; q < cnt; ++q) {
@@ -923,7 +960,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     P[-1] = w;
                     NB16[-1] = (uint16_t)nbits;
                 }
-                long long tok_base = 0;
+                unsigned tok_base = 0;
                 for (long long seg0 = 0; seg0 < nb + 1; seg0 += kMaxB) {
                     const int nseg = (int)((nb + 1 - seg0) < kMaxB ? (nb + 1 - seg0) : kMaxB);
                     unsigned cnt[1];
@@ -943,7 +980,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                         sC[s] = full + tail;
                     }
                     __syncthreads();
-                    {
+                    if (nseg == 1) {
+                        cnt[0] = sC[0];
+                        __syncthreads();
+                        if (tid == 0) sC[0] = 0;
+                    } else {
                         unsigned run = 0;
                         for (int b0 = 0; b0 < nseg; b0 += NT) {
                             const int s = b0 + tid;
@@ -957,13 +998,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     __syncthreads();
                     for (int s = tid; s < nseg; s += NT) {
                         const long long gs = seg0 + s;
-                        const long long base = T0 + tok_base + sC[s];
-                        if (gs >= 1 && R0 + gs - 1 < p.offsets_cap) p.offsets_out[R0 + gs - 1] = base;
+                        const unsigned base = tok_base + sC[s];
+                        if (gs >= 1 && R0 + gs - 1 < p.offsets_cap)
+                            p.offsets_out[R0 + gs - 1] = T0 + base;
                         if (gs < nb) {
                             const unsigned n = sJr[s] + sL[s];
                             const unsigned full = __umulhi(n, kmagic);
-                            if (n != full * k && base + full < p.out_cap)
-                                static_cast<int *>(p.out)[base + full] = (int)unk;
+                            if (n != full * k) put(base + full, unk);  // the record's tail
                         }
                     }
                     const unsigned kfirst = sks[0];
@@ -972,8 +1013,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                         const unsigned w_lo = kfirst >> 4, w_hi = (klast - 1) >> 4;
                         for (unsigned w = w_lo + tid; w <= w_hi; w += NT) {
                             const unsigned x_lo = 16 * w, x_hi = x_lo + 16;
-                            const unsigned long long win =
-                                ((unsigned long long)P[(int)w - 1] << 32) | P[w];
+                            const unsigned whi = P[(int)w - 1], wlo = P[w];
                             const unsigned nwin =
                                 (unsigned)NB16[(int)w - 1] | ((unsigned)NB16[w] << 16);
                             int s = 0;
@@ -994,13 +1034,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                                 const unsigned n = a - ks + sJr[s];
                                 const unsigned q = __umulhi(n, kmagic);
                                 const unsigned r = n - q * k;
-                                unsigned x = a + (k - 1 - r);
-                                long long o = T0 + tok_base + sC[s] + q;
-                                for (; x < b; x += k, ++o) {
-                                    const unsigned e = x - x_lo;
-                                    unsigned id = (unsigned)(win >> (30 - 2 * e)) & cmask;
+                                unsigned u = tok_base + sC[s] + q;
+                                for (unsigned e = a - x_lo + (k - 1 - r); e < b - x_lo; e += k, ++u) {
+                                    // the k-mer ending at symbol x_lo + e: 2k bits of (whi:wlo)
+                                    unsigned id = __funnelshift_r(wlo, whi, 30 - 2 * e) & cmask;
                                     if ((nwin >> (17 + e - k)) & nkm) id = unk;
-                                    if (o < p.out_cap) static_cast<int *>(p.out)[o] = (int)id;
+                                    put(u, id);
                                 }
                             }
                         }
@@ -1008,8 +1047,27 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     tok_base += cnt[0];
                     __syncthreads();
                 }
+                if (staged && tile_tokens > 0) {
+                    long long g_lo = T0, g_hi = T0 + tile_tokens;
+                    if (g_hi > p.out_cap) g_hi = p.out_cap;
+                    const long long a_lo = (g_lo + 3) & ~3ll, a_hi = g_hi & ~3ll;
+                    if (tid == 0 && a_hi > a_lo) {
+                        fence_proxy_async_shared();
+                        tma_store_1d(static_cast<int *>(p.out) + a_lo, stg + (a_lo - T0 + shift),
+                                     (unsigned)(4 * (a_hi - a_lo)));
+                        bulk_commit();
+                    }
+                    const long long h_end = a_lo < g_hi ? a_lo : g_hi;
+                    const long long t_beg = a_hi > a_lo ? a_hi : a_lo;
+                    if (tid >= 32 && tid < 36) {
+                        const long long o = g_lo + (tid - 32);
+                        if (o < h_end) static_cast<int *>(p.out)[o] = stg[o - T0 + shift];
+                    } else if (tid >= 36 && tid < 40) {
+                        const long long o = t_beg + (tid - 36);
+                        if (o >= g_lo && o < g_hi) static_cast<int *>(p.out)[o] = stg[o - T0 + shift];
+                    }
+                }
             }
-            Pr = agg_combine(Pr, s_tagg[ti], k);
             __syncthreads();
         }
     }
@@ -1026,6 +1084,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
     // The last CTA out resets the chunk counters for the next launch.
     __syncthreads();
     if (tid == 0) {
+        bulk_wait_all();
         __threadfence();
         const unsigned long long done = atomicAdd(&p.tile_counter[1], 1ull);
         if (done == gridDim.x - 1) {

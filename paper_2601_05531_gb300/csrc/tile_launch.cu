@@ -11,16 +11,17 @@ __global__ void empty_chunk_kernel(TileParams p, int list_source) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (dev_failed(p.status)) return;
     const int k = p.k;
+    const KDiv kd = make_kdiv(k);
     const Agg c = p.carry_in ? p.carry_in->a : agg_identity();
     const long long nbz = list_source ? p.n_bnd : (long long)p.end_boundary;
     Agg z = agg_identity();
     z.nb = nbz;
-    const Agg incl = agg_combine(c, z, k);
+    const Agg incl = agg_combine(c, z, kd);
     if (nbz > 0) {
         long long tclose = 0;
         if (c.nb > 0) {
-            tclose = c.d - c.t / k + (c.t + k - 1) / k;
-            if (k > 1 && c.t % k != 0 && c.d < p.out_cap)
+            tclose = c.d - kd.div(c.t) + kd.div(c.t + k - 1);
+            if (k > 1 && c.t != kd.div(c.t) * k && c.d < p.out_cap)
                 static_cast<int *>(p.out)[c.d] = 1 << (2 * k);  // UNK tail
         }
         for (long long i = 0; i < nbz; ++i) {
