@@ -167,6 +167,47 @@ DNATOK_API dnatok_status dnatok_sync(dnatok_handle *h, dnatok_cuda_stream stream
  * h may be NULL for errors of dnatok_create. */
 DNATOK_API dnatok_status dnatok_last_error(const dnatok_handle *h, char *buf, size_t len);
 
+/* ------------------------------------------------------ no allocation */
+
+/*
+ * K-mer encode for callers that may not allocate device memory.  The paper
+ * has no counterpart: this is a deployment form of dnatok_encode (RAW input,
+ * mode DNATOK_KMER, the default base table) for code that runs where
+ * cudaMalloc is off limits -- inside another library's memory pool, under a
+ * framework whose allocator owns the whole device, or in a setting where an
+ * allocation would synchronize the device.  It takes no handle and allocates
+ * nothing: the look-back descriptors, counters and status word live in one
+ * file-scope device array of fixed size, which every GPU that loads this
+ * library holds until the process exits (about 0.5 MB).
+ *
+ *   k, bytes_d, seq_offsets_d, n_seq, ids_out_d, ids_capacity, id_offsets_d,
+ *   offsets_capacity: as for dnatok_encode with a RAW k-mer handle (all
+ *   DEVICE pointers owned by the caller).  ids_capacity must be at least
+ *   min(n_bytes, (n_bytes + n_seq * (k - 1)) / k).
+ *   totals_d: NULL or 2 int64 {number of ids, number of records}; both read
+ *   -1 once the stream gets there if the kernel recorded a device-side error
+ *   (such as malformed seq_offsets).
+ *
+ * n_bytes above DNATOK_NOALLOC_MAX_BYTES is rejected with
+ * DNATOK_ERR_CAPACITY before anything is launched; bad arguments give
+ * DNATOK_ERR_ARG, a failed CUDA call DNATOK_ERR_CUDA.
+ *
+ * The first call on a device (with that device current) looks up the
+ * array's device address and caches it; make that first call before any
+ * stream capture.  Every call clears the parts of the array it uses on
+ * `stream` before launching.  All calls share the one array, so calls whose
+ * work overlaps on the GPU (different streams, no ordering between them)
+ * race: issue them on one stream or order them with events.
+ */
+#define DNATOK_NOALLOC_MAX_BYTES (1LL << 30)
+
+DNATOK_API dnatok_status dnatok_encode_kmer_noalloc(int k, const uint8_t *bytes_d, int64_t n_bytes,
+                                                    const int64_t *seq_offsets_d, int64_t n_seq,
+                                                    int32_t *ids_out_d, int64_t ids_capacity,
+                                                    int64_t *id_offsets_d,
+                                                    int64_t offsets_capacity, int64_t *totals_d,
+                                                    dnatok_cuda_stream stream);
+
 /* -------------------------------------------------------------- launch */
 
 /* Launch shape of the tokenization kernel: bytes per tile, threads per CTA,

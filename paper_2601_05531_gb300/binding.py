@@ -74,6 +74,8 @@ def lib():
             "dnatok_last_error": (_ST, [_P, ctypes.c_char_p, ctypes.c_size_t]),
             "dnatok_get_launch": (_ST, [_P, ctypes.POINTER(LaunchCfg)]),
             "dnatok_set_launch": (_ST, [_P, ctypes.POINTER(LaunchCfg)]),
+            "dnatok_encode_kmer_noalloc": (_ST, [ctypes.c_int, _P, _I64, _P, _I64, _P, _I64, _P,
+                                                 _I64, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -165,3 +167,22 @@ def dnatok_set_launch(h, tile_bytes: int, threads: int, ctas_per_sm: int,
                       chunk_tiles: int = 4) -> None:
     c = LaunchCfg(tile_bytes, threads, ctas_per_sm, chunk_tiles)
     check(lib().dnatok_set_launch(h, ctypes.byref(c)), h)
+
+
+NOALLOC_MAX_BYTES = 1 << 30  # DNATOK_NOALLOC_MAX_BYTES
+
+
+def dnatok_encode_kmer_noalloc(k: int, bytes_d: int, n_bytes: int, seq_offsets_d: int,
+                               n_seq: int, ids_out_d: int, ids_capacity: int, id_offsets_d: int,
+                               offsets_capacity: int, totals_d: int, stream: int) -> int:
+    """The k-mer encode that allocates nothing (all pointers are device
+    addresses the caller owns).  totals read {-1, -1} after a device-side
+    error; inputs above NOALLOC_MAX_BYTES raise DnatokError(CAPACITY)."""
+    st = lib().dnatok_encode_kmer_noalloc(k, bytes_d, n_bytes, seq_offsets_d, n_seq, ids_out_d,
+                                          ids_capacity, id_offsets_d, offsets_capacity, totals_d,
+                                          stream)
+    if st < 0:
+        why = {-1: "bad argument", -3: "n_bytes above %d or an output buffer too small"
+               % NOALLOC_MAX_BYTES, -4: "CUDA call failed"}.get(st, "error")
+        raise DnatokError(st, "dnatok_encode_kmer_noalloc: " + why)
+    return st
