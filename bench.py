@@ -143,6 +143,71 @@ def _workload():
     return synth.kmer_batch_4096()
 
 
+def _h2d_peak(torch, src, dev, chunk: int = 64 << 20, reps: int = 10):
+    """Pinned-host -> device copy GB/s: best single 64 MiB chunk of `reps`, and
+    the sustained rate of back-to-back chunks over the whole buffer."""
+    dst = [torch.empty(chunk, dtype=torch.uint8, device=dev) for _ in range(2)]
+    s = torch.cuda.current_stream()
+    best = 0.0
+    for i in range(reps + 2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        dst[i & 1].copy_(src[:chunk], non_blocking=True)
+        b.record(s)
+        b.synchronize()
+        if i >= 2:
+            best = max(best, chunk / (a.elapsed_time(b) / 1e3) / 1e9)
+    n_chunks = src.numel() // chunk
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for i in range(n_chunks):
+        dst[i & 1].copy_(src[i * chunk:(i + 1) * chunk], non_blocking=True)
+    b.record(s)
+    b.synchronize()
+    sustained = n_chunks * chunk / (a.elapsed_time(b) / 1e3) / 1e9
+    return best, sustained
+
+
+def _streamed(torch, P, dev, n_bytes: int, reps: int = 3):
+    """Host-streamed 6-mer encode of a FASTA stream held in pinned host
+    memory: 64 MiB chunks, 3 device slots, copy and compute streams.  Wall
+    time from the first submit to the completion of the last request."""
+    import synth
+    host = torch.empty(n_bytes, dtype=torch.uint8, pin_memory=True)
+    _, lay = synth.fasta_stream(n_bytes, seed=47, out=host.numpy())
+    n_rec = len(lay.rec_off)
+    k = 6
+    ids = torch.empty(n_bytes // k + 2 * n_rec + 1024, dtype=torch.int32, device=dev)
+    offs = torch.empty(n_rec + 2, dtype=torch.int64, device=dev)
+    best_h2d, sustained_h2d = _h2d_peak(torch, host, dev)
+    out = {"workload": "6-mer ids of a %.2f GiB FASTA stream in pinned host memory "
+                       "(records log-uniform 10 kb-10 Mb, headers 20-80 B, lines 60/80)"
+                       % (n_bytes / 2**30),
+           "chunk_bytes": 64 << 20, "slots": 3, "records": n_rec,
+           "h2d_peak_gbs": best_h2d, "h2d_peak": "best of 10 pinned 64 MiB cudaMemcpyAsync",
+           "h2d_sustained_gbs": sustained_h2d}
+    with P.Tokenizer(P.KMER, k=k, fmt=P.FASTA) as tok:
+        for overlap in (True, False):
+            times, res = [], None
+            for i in range(reps + 1):
+                tok.stream_open(ids, offs, chunk_bytes=64 << 20, n_slots=3, overlap=overlap)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = tok.stream_submit(host, P.HOST_PINNED | P.END_OF_STREAM)
+                res = tok.stream_wait(r)
+                t = time.perf_counter() - t0
+                tok.stream_close()
+                if i > 0:
+                    times.append(t)
+            t = statistics.median(times)
+            key = "overlap" if overlap else "serial"
+            out[key] = {"tokens_per_s": res[0] / t, "ms": 1e3 * t, "h2d_gbs": n_bytes / t / 1e9,
+                        "frac_of_h2d_peak": n_bytes / t / 1e9 / best_h2d}
+            out["tokens"] = res[0]
+    del host
+    return out
+
+
 def _cpu_baseline(data, offs, budget_s: float = 10.0):
     """The oracle as it stands, single-threaded on this host, on a bounded
     sample of the same workload (whole records, repeated until ~budget_s)."""
@@ -321,6 +386,8 @@ def run_gpu(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(data, offs)
+        if args.stream_gib > 0:
+            line["host_streamed"] = _streamed(torch, P, dev, int(args.stream_gib * 2**30))
         print(json.dumps(line), flush=True)
     tok.close()
     if ws > 1:
@@ -336,6 +403,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--shape", default=None, help="tile_bytes,threads,ctas_per_sm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stream-gib", type=float, default=8.0,
+                    help="size of the host-streamed FASTA measurement (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -167,6 +167,77 @@ DNATOK_API dnatok_status dnatok_sync(dnatok_handle *h, dnatok_cuda_stream stream
  * h may be NULL for errors of dnatok_create. */
 DNATOK_API dnatok_status dnatok_last_error(const dnatok_handle *h, char *buf, size_t len);
 
+/* ------------------------------------------------------- host-streamed */
+
+/*
+ * Host-streamed encode: the bytes path's pinned staging with the pipelined
+ * path's two streams, so that the copy of one chunk overlaps the
+ * tokenization of the previous one (Sec. 2.2 "Encoding paths"; the overlap
+ * on/off ablation of Sec. 3.5 and the crossover of Sec. 4.2).  The caller feeds one logical byte stream in pieces of
+ * any size; the handle cuts them into chunks, copies each chunk into a ring
+ * of device slots on a copy stream and tokenizes it on a compute stream,
+ * carrying the scan state (open record, partial k-mer, FASTA line state)
+ * from chunk to chunk, so that the result equals dnatok_encode of the whole
+ * stream.  Ids and record offsets are written at their global positions in
+ * the caller's DEVICE arrays given to dnatok_stream_open.
+ *
+ * Records: FASTA handles find them as dnatok_encode does.  RAW handles: the
+ * first piece opens record 0, a piece flagged DNATOK_NEW_RECORD opens the
+ * next record, DNATOK_END_OF_STREAM closes the last one; no more pieces may
+ * follow it.  Not available for DNATOK_BPE handles (DNATOK_ERR_STATE).
+ * While a stream is open the handle runs nothing else.
+ */
+#define DNATOK_END_OF_STREAM 1 /* this piece ends the stream */
+#define DNATOK_NEW_RECORD 2    /* RAW: a record starts at this piece's first byte */
+#define DNATOK_HOST_PINNED 4   /* host_bytes is page-locked and stays valid until the
+                                  request completes: copied by DMA straight from it */
+
+typedef struct {
+    int64_t chunk_bytes; /* bytes per chunk (0 = 64 MiB) */
+    int32_t n_slots;     /* device slots in the ring, 2..8 (0 = 3) */
+    int32_t overlap;     /* 1 = copies on their own stream (default); 0 = copy and
+                            compute serialized on one stream (the ablation) */
+} dnatok_stream_cfg;
+
+typedef struct {
+    int64_t n_ids;     /* ids written so far (whole stream through this request) */
+    int64_t n_records; /* records closed so far */
+    int64_t bytes_in;  /* input bytes submitted through this request */
+} dnatok_stream_result;
+
+/* Open a stream on h.  ids_out_d / id_offsets_d: caller-owned DEVICE arrays
+ * that receive the whole stream's ids and record offsets; they must stay
+ * valid until dnatok_stream_close.  Ids past ids_capacity are not written
+ * (the poll then reports DNATOK_ERR_CAPACITY); offsets past
+ * offsets_capacity are not written either (n_records still counts them).
+ * Allocates the device ring (and, on first need, a page-locked host ring). */
+DNATOK_API dnatok_status dnatok_stream_open(dnatok_handle *h, const dnatok_stream_cfg *cfg,
+                                            int32_t *ids_out_d, int64_t ids_capacity,
+                                            int64_t *id_offsets_d, int64_t offsets_capacity);
+
+/* Queue n bytes of the stream.  Without DNATOK_HOST_PINNED the bytes are
+ * copied into the page-locked ring before this returns (the caller may reuse
+ * its buffer at once); with it, they are copied by DMA from host_bytes, which
+ * must stay valid until the request completes.  *req_id identifies the
+ * request for poll / wait. */
+DNATOK_API dnatok_status dnatok_stream_submit(dnatok_handle *h, const uint8_t *host_bytes,
+                                              int64_t n, int flags, uint64_t *req_id);
+
+/* DNATOK_PENDING while the request's chunks are still in flight; DNATOK_OK
+ * once its ids and offsets are on the device (out filled in);
+ * DNATOK_ERR_UNKNOWN_REQ for an id never issued or more than 1024 requests
+ * old; a device-side error of any chunk so far is returned here. */
+DNATOK_API dnatok_status dnatok_stream_poll(dnatok_handle *h, uint64_t req_id,
+                                            dnatok_stream_result *out);
+
+/* Block until the request completes, then as dnatok_stream_poll. */
+DNATOK_API dnatok_status dnatok_stream_wait(dnatok_handle *h, uint64_t req_id,
+                                            dnatok_stream_result *out);
+
+/* Wait for every request, release the ring.  The handle can open another
+ * stream afterwards. */
+DNATOK_API dnatok_status dnatok_stream_close(dnatok_handle *h);
+
 /* ------------------------------------------------------ no allocation */
 
 /*

@@ -95,6 +95,36 @@ class Tokenizer:
     def sync(self, stream=None):
         binding.dnatok_sync(self.h, _stream_ptr(stream))
 
+    # ---------------------------------------------------------------- streams
+    def stream_open(self, ids, offsets, chunk_bytes: int = 0, n_slots: int = 0,
+                    overlap: bool = True):
+        """Open a host-streamed encode writing into the CUDA tensors ids
+        (int32) and offsets (int64); keep them alive until stream_close."""
+        binding.dnatok_stream_open(self.h, ids.data_ptr(), ids.numel(), offsets.data_ptr(),
+                                   offsets.numel(), chunk_bytes, n_slots, int(bool(overlap)))
+
+    def stream_submit(self, data, flags: int = 0) -> int:
+        """Queue host bytes (numpy uint8 / pinned CPU tensor).  Pass
+        HOST_PINNED only for page-locked memory kept alive until completion."""
+        import numpy as np
+        if hasattr(data, "data_ptr"):
+            ptr, n = data.data_ptr(), int(data.numel())
+        else:
+            a = np.ascontiguousarray(data, dtype=np.uint8)
+            ptr, n = a.ctypes.data, a.size
+            if flags & HOST_PINNED:
+                raise ValueError("HOST_PINNED needs a page-locked tensor")
+        return binding.dnatok_stream_submit(self.h, ptr if n else 0, n, flags)
+
+    def stream_poll(self, req_id: int):
+        return binding.dnatok_stream_poll(self.h, req_id)
+
+    def stream_wait(self, req_id: int):
+        return binding.dnatok_stream_wait(self.h, req_id)
+
+    def stream_close(self):
+        binding.dnatok_stream_close(self.h)
+
     def encode_host(self, data, seq_offsets=None):
         """Copy host bytes to the device, encode, wait, and return numpy
         (ids, offsets) trimmed to the produced counts (a test helper)."""

@@ -34,6 +34,16 @@ class DnatokError(RuntimeError):
         self.status = status
 
 
+class StreamCfg(ctypes.Structure):
+    _fields_ = [("chunk_bytes", ctypes.c_int64), ("n_slots", ctypes.c_int32),
+                ("overlap", ctypes.c_int32)]
+
+
+class StreamResult(ctypes.Structure):
+    _fields_ = [("n_ids", ctypes.c_int64), ("n_records", ctypes.c_int64),
+                ("bytes_in", ctypes.c_int64)]
+
+
 class LaunchCfg(ctypes.Structure):
     _fields_ = [("tile_bytes", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32)]
@@ -74,6 +84,12 @@ def lib():
             "dnatok_last_error": (_ST, [_P, ctypes.c_char_p, ctypes.c_size_t]),
             "dnatok_get_launch": (_ST, [_P, ctypes.POINTER(LaunchCfg)]),
             "dnatok_set_launch": (_ST, [_P, ctypes.POINTER(LaunchCfg)]),
+            "dnatok_stream_open": (_ST, [_P, ctypes.POINTER(StreamCfg), _P, _I64, _P, _I64]),
+            "dnatok_stream_submit": (_ST, [_P, _P, _I64, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+            "dnatok_stream_poll": (_ST, [_P, ctypes.c_uint64, ctypes.POINTER(StreamResult)]),
+            "dnatok_stream_wait": (_ST, [_P, ctypes.c_uint64, ctypes.POINTER(StreamResult)]),
+            "dnatok_stream_close": (_ST, [_P]),
             "dnatok_encode_kmer_noalloc": (_ST, [ctypes.c_int, _P, _I64, _P, _I64, _P, _I64, _P,
                                                  _I64, _P, _P]),
         }
@@ -167,6 +183,39 @@ def dnatok_set_launch(h, tile_bytes: int, threads: int, ctas_per_sm: int,
                       chunk_tiles: int = 4) -> None:
     c = LaunchCfg(tile_bytes, threads, ctas_per_sm, chunk_tiles)
     check(lib().dnatok_set_launch(h, ctypes.byref(c)), h)
+
+
+def dnatok_stream_open(h, ids_out_d: int, ids_capacity: int, id_offsets_d: int,
+                       offsets_capacity: int, chunk_bytes: int = 0, n_slots: int = 0,
+                       overlap: int = 1) -> None:
+    c = StreamCfg(chunk_bytes, n_slots, overlap)
+    check(lib().dnatok_stream_open(h, ctypes.byref(c), ids_out_d, ids_capacity, id_offsets_d,
+                                   offsets_capacity), h)
+
+
+def dnatok_stream_submit(h, host_bytes: int, n: int, flags: int = 0) -> int:
+    r = ctypes.c_uint64()
+    check(lib().dnatok_stream_submit(h, host_bytes, n, flags, ctypes.byref(r)), h)
+    return r.value
+
+
+def dnatok_stream_poll(h, req_id: int):
+    """None while pending, else (n_ids, n_records, bytes_in)."""
+    out = StreamResult()
+    st = check(lib().dnatok_stream_poll(h, req_id, ctypes.byref(out)), h)
+    if st == 1:
+        return None
+    return (out.n_ids, out.n_records, out.bytes_in)
+
+
+def dnatok_stream_wait(h, req_id: int):
+    out = StreamResult()
+    check(lib().dnatok_stream_wait(h, req_id, ctypes.byref(out)), h)
+    return (out.n_ids, out.n_records, out.bytes_in)
+
+
+def dnatok_stream_close(h) -> None:
+    check(lib().dnatok_stream_close(h), h)
 
 
 NOALLOC_MAX_BYTES = 1 << 30  # DNATOK_NOALLOC_MAX_BYTES
