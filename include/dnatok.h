@@ -295,6 +295,16 @@ typedef struct {
 DNATOK_API dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg);
 DNATOK_API dnatok_status dnatok_set_launch(dnatok_handle *h, const dnatok_launch_cfg *cfg);
 
+/* BPE handles: symbols per segment of the merge pass (64..65536, a multiple
+ * of 16, at least twice the longest token) and the halo each segment's pass
+ * starts before it (0..seg_symbols, a multiple of 16).  A segment whose
+ * halo pass does not agree with its left neighbour over the longest token's
+ * length is recomputed exactly, so any halo gives the same ids; a short one
+ * only costs time.  Defaults: 1024 and max(64, 4 x longest token). */
+DNATOK_API dnatok_status dnatok_set_bpe_launch(dnatok_handle *h, int32_t seg_symbols, int32_t halo);
+DNATOK_API dnatok_status dnatok_get_bpe_launch(const dnatok_handle *h, int32_t *seg_symbols,
+                                               int32_t *halo);
+
 #ifdef __cplusplus
 }
 #endif

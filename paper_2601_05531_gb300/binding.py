@@ -90,6 +90,9 @@ def lib():
             "dnatok_stream_poll": (_ST, [_P, ctypes.c_uint64, ctypes.POINTER(StreamResult)]),
             "dnatok_stream_wait": (_ST, [_P, ctypes.c_uint64, ctypes.POINTER(StreamResult)]),
             "dnatok_stream_close": (_ST, [_P]),
+            "dnatok_set_bpe_launch": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
+            "dnatok_get_bpe_launch": (_ST, [_P, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]),
             "dnatok_encode_kmer_noalloc": (_ST, [ctypes.c_int, _P, _I64, _P, _I64, _P, _I64, _P,
                                                  _I64, _P, _P]),
         }
@@ -216,6 +219,16 @@ def dnatok_stream_wait(h, req_id: int):
 
 def dnatok_stream_close(h) -> None:
     check(lib().dnatok_stream_close(h), h)
+
+
+def dnatok_set_bpe_launch(h, seg_symbols: int, halo: int) -> None:
+    check(lib().dnatok_set_bpe_launch(h, seg_symbols, halo), h)
+
+
+def dnatok_get_bpe_launch(h) -> tuple:
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    check(lib().dnatok_get_bpe_launch(h, ctypes.byref(a), ctypes.byref(b)), h)
+    return (a.value, b.value)
 
 
 NOALLOC_MAX_BYTES = 1 << 30  # DNATOK_NOALLOC_MAX_BYTES

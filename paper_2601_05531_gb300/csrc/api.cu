@@ -226,9 +226,7 @@ dnatok_status dnatok_reserve(dnatok_handle *h, int64_t max_bytes, int64_t max_se
     if (!h || max_bytes < 0 || max_seq < 0) return DNATOK_ERR_ARG;
     dnatok_status st = ensure_workspace(h, max_bytes, max_seq + 1, h->shape, 0);
     if (st != DNATOK_OK) return st;
-    if (h->mode == DNATOK_BPE) {
-        // the BPE path runs its symbol pass with the same workspace
-    }
+    if (h->mode == DNATOK_BPE) return bpe_reserve(h, max_bytes);
     return DNATOK_OK;
 }
 
@@ -351,6 +349,8 @@ dnatok_status dnatok_sync(dnatok_handle *h, dnatok_cuda_stream stream) {
     // a launch that stopped early may have left its tile counters set
     cudaMemset(h->d_counter, 0, 2 * sizeof(unsigned long long));
     if (st == DEV_TIMEOUT) return fail(h, DNATOK_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (st == DEV_CAPACITY)
+        return fail(h, DNATOK_ERR_CAPACITY, "id_offsets has no room for every record found");
     if (st == DEV_BAD_OFFSETS)
         return fail(h, DNATOK_ERR_DEVICE_DATA,
                     "seq_offsets malformed (must be non-decreasing, [0]=0, [n_seq]=n_bytes)");
@@ -371,6 +371,16 @@ dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg) 
     cfg->ctas_per_sm = h->shape.ctas_per_sm;
     cfg->chunk_tiles = h->shape.chunk_tiles;
     return DNATOK_OK;
+}
+
+dnatok_status dnatok_set_bpe_launch(dnatok_handle *h, int32_t seg_symbols, int32_t halo) {
+    if (!h) return DNATOK_ERR_ARG;
+    return bpe_set_launch(h, seg_symbols, halo);
+}
+
+dnatok_status dnatok_get_bpe_launch(const dnatok_handle *h, int32_t *seg_symbols, int32_t *halo) {
+    if (!h || !seg_symbols || !halo) return DNATOK_ERR_ARG;
+    return bpe_get_launch(h, seg_symbols, halo);
 }
 
 dnatok_status dnatok_set_launch(dnatok_handle *h, const dnatok_launch_cfg *cfg) {

@@ -76,6 +76,9 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
 // BPE path (bpe.cu)
 dnatok_status bpe_create(dnatok_handle *h, const int32_t *merges, int32_t n_merges);
 void bpe_destroy(dnatok_handle *h);
+dnatok_status bpe_reserve(dnatok_handle *h, long long max_bytes);
+dnatok_status bpe_set_launch(dnatok_handle *h, int seg_symbols, int halo);
+dnatok_status bpe_get_launch(const dnatok_handle *h, int *seg_symbols, int *halo);
 dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
                          const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
                          int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
