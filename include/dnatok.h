@@ -295,6 +295,46 @@ typedef struct {
 DNATOK_API dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg);
 DNATOK_API dnatok_status dnatok_set_launch(dnatok_handle *h, const dnatok_launch_cfg *cfg);
 
+/* ------------------------------------------------- graphs and autotuning */
+
+/*
+ * CUDA-graph capture (the batched form: one replay launches a whole batch,
+ * or many encodes, with no per-call host work).  dnatok_graph_begin starts
+ * capturing `stream` (a non-default stream, thread-local capture mode);
+ * every dnatok_encode on it until dnatok_graph_end is recorded, not run.
+ * Encodes recorded this way clear the look-back state they use inside the
+ * graph, so replays are independent; all pointers are fixed in the graph
+ * (refresh input bytes in place between replays).  Reserve workspace first
+ * (dnatok_reserve): an encode that would have to allocate fails with
+ * DNATOK_ERR_STATE under capture.  A handle must not run other work while
+ * one of its graphs replays.  Not for the stream API (it waits on the host).
+ */
+typedef struct dnatok_graph dnatok_graph;
+DNATOK_API dnatok_status dnatok_graph_begin(dnatok_handle *h, dnatok_cuda_stream stream);
+DNATOK_API dnatok_status dnatok_graph_end(dnatok_handle *h, dnatok_cuda_stream stream,
+                                          dnatok_graph **out);
+DNATOK_API dnatok_status dnatok_graph_launch(dnatok_graph *g, dnatok_cuda_stream stream);
+DNATOK_API void dnatok_graph_destroy(dnatok_graph *g);
+
+/*
+ * Autotuner: time every supported launch shape (tile bytes, threads, tiles
+ * per chunk, resident CTAs per SM; for BPE handles the merge pass's segment
+ * size) on this input -- `reps` timed runs each after one warm-up, L2
+ * flushed before each -- and keep the fastest on the handle.  Arguments as
+ * for dnatok_encode (device pointers; outputs are overwritten).  cache_path:
+ * NULL or a text file; a line for this GPU, mode, k, format and input size
+ * class (power of two) is reused without timing, and a new result is
+ * appended.  best / best_ms (either may be NULL) receive the choice (for
+ * BPE: {segment, halo, 0, 0}) and its mean time (-1 on a cache hit).
+ * Synchronizes; allocates a 192 MB scratch buffer while it runs.
+ */
+DNATOK_API dnatok_status dnatok_autotune(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
+                                         const int64_t *seq_offsets_d, int64_t n_seq,
+                                         int32_t *ids_out_d, int64_t ids_capacity,
+                                         int64_t *id_offsets_d, int64_t offsets_capacity,
+                                         int32_t reps, const char *cache_path,
+                                         dnatok_launch_cfg *best, float *best_ms);
+
 /* BPE handles: symbols per segment of the merge pass (64..65536, a multiple
  * of 16, at least twice the longest token) and the halo each segment's pass
  * starts before it (0..seg_symbols, a multiple of 16).  A segment whose

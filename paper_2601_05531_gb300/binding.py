@@ -93,6 +93,13 @@ def lib():
             "dnatok_set_bpe_launch": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
             "dnatok_get_bpe_launch": (_ST, [_P, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
+            "dnatok_graph_begin": (_ST, [_P, _P]),
+            "dnatok_graph_end": (_ST, [_P, _P, ctypes.POINTER(_P)]),
+            "dnatok_graph_launch": (_ST, [_P, _P]),
+            "dnatok_graph_destroy": (None, [_P]),
+            "dnatok_autotune": (_ST, [_P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.c_int32,
+                                      ctypes.c_char_p, ctypes.POINTER(LaunchCfg),
+                                      ctypes.POINTER(ctypes.c_float)]),
             "dnatok_encode_kmer_noalloc": (_ST, [ctypes.c_int, _P, _I64, _P, _I64, _P, _I64, _P,
                                                  _I64, _P, _P]),
         }
@@ -229,6 +236,37 @@ def dnatok_get_bpe_launch(h) -> tuple:
     a, b = ctypes.c_int32(), ctypes.c_int32()
     check(lib().dnatok_get_bpe_launch(h, ctypes.byref(a), ctypes.byref(b)), h)
     return (a.value, b.value)
+
+
+def dnatok_graph_begin(h, stream: int) -> None:
+    check(lib().dnatok_graph_begin(h, stream), h)
+
+
+def dnatok_graph_end(h, stream: int) -> int:
+    g = _P()
+    check(lib().dnatok_graph_end(h, stream, ctypes.byref(g)), h)
+    return g.value
+
+
+def dnatok_graph_launch(g, stream: int) -> None:
+    check(lib().dnatok_graph_launch(g, stream))
+
+
+def dnatok_graph_destroy(g) -> None:
+    lib().dnatok_graph_destroy(g)
+
+
+def dnatok_autotune(h, bytes_d: int, n_bytes: int, seq_offsets_d: int, n_seq: int,
+                    ids_out_d: int, ids_capacity: int, id_offsets_d: int, offsets_capacity: int,
+                    reps: int = 5, cache_path: str | None = None):
+    """Returns ((tile, threads, ctas_per_sm, chunk_tiles) or BPE (seg, halo, 0, 0), ms)."""
+    c = LaunchCfg()
+    ms = ctypes.c_float()
+    check(lib().dnatok_autotune(h, bytes_d, n_bytes, seq_offsets_d, n_seq, ids_out_d,
+                                ids_capacity, id_offsets_d, offsets_capacity, reps,
+                                cache_path.encode() if cache_path else None, ctypes.byref(c),
+                                ctypes.byref(ms)), h)
+    return (c.tile_bytes, c.threads, c.ctas_per_sm, c.chunk_tiles), ms.value
 
 
 NOALLOC_MAX_BYTES = 1 << 30  # DNATOK_NOALLOC_MAX_BYTES

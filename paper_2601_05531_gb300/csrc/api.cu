@@ -125,6 +125,15 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
     p.n_chunks = (p.n_tiles + sh.chunk_tiles - 1) / sh.chunk_tiles;
     st = next_epoch(h, s, &p.epoch);
     if (st != DNATOK_OK) return st;
+    {
+        // Under stream capture the epoch is baked into the graph and every
+        // replay reuses it, so the graph clears the descriptors it uses first.
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * (size_t)p.n_chunks, s);
+            if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
+        }
+    }
     e = launch_tile_kernel(mode, bsrc, p, sh, s, h->sm_count);
     if (e != cudaSuccess) return fail_cuda(h, e, "tile kernel launch");
     return DNATOK_OK;

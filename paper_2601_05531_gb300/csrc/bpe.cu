@@ -912,11 +912,13 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     if (W.max_seg == 0) W.max_seg = 1;
 
     const size_t smem = trie_smem_bytes(b);
-    const bool use_smem = smem <= 96 * 1024;
+    const bool use_smem = smem <= 96 * 1024 + 16;
     const size_t dyn = use_smem ? smem : 0;
-    if (use_smem) {
-        cudaFuncSetAttribute(bpe_dp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        cudaFuncSetAttribute(bpe_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    static bool attr_done = false;  // once per process: allow the largest trie we stage
+    if (!attr_done) {
+        cudaFuncSetAttribute(bpe_dp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 16);
+        cudaFuncSetAttribute(bpe_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 16);
+        attr_done = true;
     }
     const unsigned g128 = (unsigned)((W.max_seg + 127) / 128);
     const unsigned g256 = (unsigned)((W.max_seg + 255) / 256);

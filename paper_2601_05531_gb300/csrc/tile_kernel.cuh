@@ -107,9 +107,39 @@ __device__ __forceinline__ unsigned nonbase4(unsigned x, unsigned c) {
 __device__ __forceinline__ unsigned low4(unsigned x) {
     return ~((x | 0x80808080u) - 0x21212121u) & ~x & 0x80808080u;
 }
+// 0x80 in every byte lane of t that is zero.
+__device__ __forceinline__ unsigned zero4(unsigned t) {
+    return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+}
+// 0x80 in every byte lane that is one of the four separators (C3).
+__device__ __forceinline__ unsigned sep4(unsigned x) {
+    if (!low4(x)) return 0u;
+    return zero4(x ^ 0x09090909u) | zero4(x ^ 0x0A0A0A0Au) | zero4(x ^ 0x0D0D0D0Du) |
+           zero4(x ^ 0x20202020u);
+}
 // High bits of the four byte lanes -> 4 bits, byte 0 in bit 0.
 __device__ __forceinline__ unsigned gather4(unsigned m) {
     return (((m >> 7) & 0x01010101u) * 0x01020408u) >> 24;
+}
+// Separator lanes of a 16-byte vector as 16 bits (byte j in bit j).
+__device__ __forceinline__ unsigned sepmask16(const uint4 &w) {
+    return gather4(sep4(w.x)) | (gather4(sep4(w.y)) << 4) | (gather4(sep4(w.z)) << 8) |
+           (gather4(sep4(w.w)) << 12);
+}
+__device__ __forceinline__ bool has_byte16(const uint4 &w, unsigned pat) {
+    return (zero4(w.x ^ pat) | zero4(w.y ^ pat) | zero4(w.z ^ pat) | zero4(w.w ^ pat)) != 0u;
+}
+// Remove the symbols whose bits are set in `drop` (16-bit, symbol j in bit j)
+// from 16 MSB-first 2-bit codes and from an LSB-first 16-bit flag word.
+__device__ __forceinline__ void compact16(unsigned drop, unsigned &codes, unsigned &flags) {
+    while (drop) {
+        const int j = 31 - __clz(drop);  // highest first: lower indices stay put
+        drop &= ~(1u << j);
+        const unsigned hi = j ? (0xFFFFFFFFu << (32 - 2 * j)) : 0u;
+        codes = (codes & hi) | ((codes << 2) & ~hi);
+        const unsigned lo = (1u << j) - 1u;
+        flags = (flags & lo) | ((flags >> 1) & ~lo);
+    }
 }
 // Four byte-lane codes -> one byte, first byte in the two top bits.
 __device__ __forceinline__ unsigned pack4(unsigned c) {
@@ -572,6 +602,18 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     const bool full = (16 * v >= vlo) && (16 * v + 16 <= vhi);
                     if (full && !nb0) {
                         m[q] = HS_SQ | (HS_HD << 2) | (HS_SQ << 4);  // only bases
+                    } else if (full && !has_byte16(w4, 0x3E3E3E3Eu)) {
+                        // no '>': a newline decides the state after it, alone
+                        const unsigned nl = gather4(zero4(w4.x ^ 0x0A0A0A0Au)) |
+                                            (gather4(zero4(w4.y ^ 0x0A0A0A0Au)) << 4) |
+                                            (gather4(zero4(w4.z ^ 0x0A0A0A0Au)) << 8) |
+                                            (gather4(zero4(w4.w ^ 0x0A0A0A0Au)) << 12);
+                        if (!nl) {
+                            m[q] = HS_SQ | (HS_HD << 2) | (HS_SQ << 4);
+                        } else {
+                            const unsigned e = (nl & 0x8000u) ? HS_LS : HS_SQ;
+                            m[q] = e | (e << 2) | (e << 4);
+                        }
                     } else {
                         for (int j = 0; j < 16; ++j) {
                             const int i = 16 * v + j;
@@ -623,8 +665,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
 
             // -------------------------------------------------- classify (SWAR)
             const bool full_pass = (pass == 2);
-            unsigned pc[VPT], nb16[VPT];
-            bool slow[VPT];
+            unsigned pc[VPT], nb16[VPT], sepm[VPT];
+            bool slow[VPT], med[VPT];
             bool tile_plain = (vlo == 0 && vhi == TILE);
 #pragma unroll
             for (int q = 0; q < VPT; ++q) {
@@ -632,8 +674,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                 const uint4 w4 = *reinterpret_cast<const uint4 *>(tb + 16 * v);
                 const bool full = (16 * v >= vlo) && (16 * v + 16 <= vhi);
                 bool s = !full;
+                bool md = false;
                 pc[q] = 0u;
                 nb16[q] = 0u;
+                sepm[q] = 0u;
                 if (MODE == MODE_CHAR && !p.lut_keeps_bases) {
                     s = true;
                 } else if (full_pass || BSRC == BSRC_FASTA || MODE == MODE_CHAR) {
@@ -652,16 +696,33 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                                    (low4(w4.w) & n3)) {
                             s = true;  // a separator (or a control byte) is present
                         }
+                        // separators and N-class bytes only, and no header can
+                        // start or continue here: the SWAR compaction path
+                        if (PACKED && s && full &&
+                            (BSRC != BSRC_FASTA ||
+                             (hin[q] != HS_HD && !has_byte16(w4, 0x3E3E3E3Eu)))) {
+                            md = true;
+                            sepm[q] = sepmask16(w4);
+                        }
                     }
                 } else {
                     // pass 1 of RAW input: only separators change the kept counts
-                    if (low4(w4.x) | low4(w4.y) | low4(w4.z) | low4(w4.w)) s = true;
+                    if (low4(w4.x) | low4(w4.y) | low4(w4.z) | low4(w4.w)) {
+                        s = true;
+                        if (PACKED && full) {
+                            md = true;
+                            sepm[q] = sepmask16(w4);
+                        }
+                    }
                 }
                 if (BSRC == BSRC_FASTA && hin[q] == HS_HD) s = true;  // inside a header line
                 if (BSRC != BSRC_LIST && p.start_boundary && t == 0 && 16 * v <= vlo &&
-                    vlo < 16 * v + 16)
+                    vlo < 16 * v + 16) {
                     s = true;
+                    md = false;
+                }
                 slow[q] = s;
+                med[q] = md && s;
                 tile_plain &= !s;
             }
             if (BSRC == BSRC_FASTA) tile_plain = false;
@@ -687,6 +748,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     if (!slow[q]) {
                         km[q] = 0xFFFFu;
                         bm[q] = 0u;
+                    } else if (med[q]) {
+                        km[q] = ~sepm[q] & 0xFFFFu;
+                        bm[q] = 0u;
+                        if (PACKED && full_pass) {
+                            unsigned cw = pc[q], nf = nb16[q] & ~sepm[q];
+                            compact16(sepm[q], cw, nf);
+                            pc[q] = cw;
+                            nb16[q] = nf;
+                        }
                     } else {
                         unsigned kmv = 0, bmv = 0, acc = 0, nac = 0, n = 0;
                         unsigned s = (BSRC == BSRC_FASTA) ? hin[q] : 0u;
