@@ -5,8 +5,10 @@ Workload (seeded, synthetic): 4096 sequences with lengths log-uniform in
 [1 kb, 128 kb] (about 109 MB), order-3 Markov DNA at 40% GC with N runs and
 soft-masked lowercase stretches; 6-mer ids (4096 k-mers + UNK), int32.
 
-One step = one dnatok_encode of the whole batch (one launch of the
-single-pass tile kernel) with inputs resident in HBM.  L2 is flushed (a
+One step = one dnatok_encode of the whole batch with inputs resident in
+HBM: three launches -- the record plan, the direct k-mer kernel, and the
+general tile kernel behind it, which exits at once when the input holds no
+separators (it runs only when the direct path's premise fails).  L2 is flushed (a
 256 MB write) before every timed step, outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -33,7 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "encode tokens/s (device-resident, host-streamed) vs HBM/H2D roofline; p99 ms"
 WORKLOAD = "6-mer (k=6) ids of 4096 sequences, lengths log-uniform 1-128 kb (~109 MB), " \
            "order-3 Markov 40% GC, N runs, soft-masked"
-KERNEL = "dnatok::tile_kernel<MODE_KMER, BSRC_LIST>"
+KERNEL = "dnatok::direct_kernel<MODE_KMER> (after direct_plan_kernel; the general " \
+         "tile_kernel<MODE_KMER, BSRC_LIST> is launched gated and exits at once)"
 
 
 def _dist():
@@ -111,7 +114,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for fn in ("tile_kernel.cuh", "common.cuh"):
+    for fn in ("direct.cu", "tile_kernel.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2601_05531_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -120,7 +123,7 @@ def _kernel_hash():
 def _traffic(n_bytes_workload: int):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (scaled to this workload by bytes)."""
-    path = os.path.join(ROOT, "profiles", "tile_kernel_kmer6_4096seq_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "direct_kernel_kmer6_4096seq_traffic.txt")
     d = {}
     try:
         with open(path) as f:
@@ -206,6 +209,198 @@ def _streamed(torch, P, dev, n_bytes: int, reps: int = 3):
             out["tokens"] = res[0]
     del host
     return out
+
+
+def _batched(torch, P, dev, data, offs, d_bytes, d_offs, reps: int = 5):
+    """The batched form against per-request plain launches: the whole
+    config-2 batch as one launch (direct and replayed from a CUDA graph)
+    versus one dnatok_encode per sequence; and 64 independent 1 MB
+    single-nucleotide calls as plain launches versus one graph replay."""
+    import numpy as np
+    import synth
+    B = P.binding
+    n, n_seq = len(data), len(offs) - 1
+    s = torch.cuda.Stream()
+    out = {}
+    with P.Tokenizer(P.KMER, k=6) as tok:
+        tok.reserve(n, n_seq)
+        ids, o, tot = tok.alloc_outputs(n, n_seq, device=dev)
+        with torch.cuda.stream(s):
+            tok.encode(d_bytes, d_offs, ids, o, tot, stream=s)
+        s.synchronize()
+        id_off = o[: n_seq + 1].cpu().numpy()
+        n_ids = int(tot[0])
+
+        def timed(fn):
+            fn()
+            s.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            a.record(s)
+            for _ in range(reps):
+                fn()
+            b.record(s)
+            b.synchronize()
+            return a.elapsed_time(b) / reps, 1e3 * (time.perf_counter() - t0) / reps
+
+        one_ms, one_wall = timed(lambda: B.dnatok_encode(
+            tok.h, d_bytes.data_ptr(), n, d_offs.data_ptr(), n_seq, ids.data_ptr(), ids.numel(),
+            o.data_ptr(), o.numel(), tot.data_ptr(), s.cuda_stream))
+        # per-sequence plain launches, ids written at the same places
+        scratch_o = torch.empty(2 * n_seq, dtype=torch.int64, device=dev)
+        offs_d = torch.from_numpy(np.stack([np.zeros(n_seq, np.int64),
+                                            np.diff(offs)], axis=1).reshape(-1)).to(dev)
+        bp, ip = d_bytes.data_ptr(), ids.data_ptr()
+        op, sp = offs_d.data_ptr(), scratch_o.data_ptr()
+
+        def per_seq():
+            for r in range(n_seq):
+                ln = int(offs[r + 1] - offs[r])
+                cap = int(id_off[r + 1] - id_off[r])
+                B.dnatok_encode(tok.h, bp + int(offs[r]) if ln else 0, ln, op + 16 * r, 1,
+                                ip + 4 * int(id_off[r]), max(cap, (ln + 5) // 6 + 1),
+                                sp + 16 * r, 2, 0, s.cuda_stream)
+
+        seq_ms, seq_wall = timed(per_seq)
+        B.dnatok_graph_begin(tok.h, s.cuda_stream)
+        B.dnatok_encode(tok.h, d_bytes.data_ptr(), n, d_offs.data_ptr(), n_seq, ids.data_ptr(),
+                        ids.numel(), o.data_ptr(), o.numel(), tot.data_ptr(), s.cuda_stream)
+        g = B.dnatok_graph_end(tok.h, s.cuda_stream)
+        g_ms, g_wall = timed(lambda: B.dnatok_graph_launch(g, s.cuda_stream))
+        B.dnatok_graph_destroy(g)
+        tok.sync(s)
+        out["kmer6_4096seq"] = {
+            "tokens": n_ids,
+            "one_launch": {"ms": one_ms, "wall_ms": one_wall, "tokens_per_s": n_ids / one_wall * 1e3},
+            "graph_replay": {"ms": g_ms, "wall_ms": g_wall, "tokens_per_s": n_ids / g_wall * 1e3},
+            "per_sequence_launches": {"launches": n_seq, "ms": seq_ms, "wall_ms": seq_wall,
+                                      "tokens_per_s": n_ids / seq_wall * 1e3},
+            "note": "ids may be cut short in the per-sequence arm only where a sequence's "
+                    "capacity bound exceeds the batched result; tokens counted from the batch"}
+    # config 1: 64 independent 1 MB single-nucleotide calls
+    one, _ = synth.single_sequence_1mb()
+    m1 = len(one)
+    calls = 64
+    with P.Tokenizer(P.CHAR) as tok:
+        tok.reserve(m1, 1)
+        ins = [torch.from_numpy(synth.single_sequence_1mb(seed=43 + i)[0]).to(dev)
+               for i in range(calls)]
+        so = torch.tensor([0, m1], dtype=torch.int64, device=dev)
+        outs = [tok.alloc_outputs(m1, 1, device=dev) for _ in range(calls)]
+
+        def plain():
+            for i in range(calls):
+                ids, o, tot = outs[i]
+                B.dnatok_encode(tok.h, ins[i].data_ptr(), m1, so.data_ptr(), 1, ids.data_ptr(),
+                                ids.numel(), o.data_ptr(), o.numel(), tot.data_ptr(),
+                                s.cuda_stream)
+
+        p_ms, p_wall = timed(plain)
+        B.dnatok_graph_begin(tok.h, s.cuda_stream)
+        plain()
+        g = B.dnatok_graph_end(tok.h, s.cuda_stream)
+        g_ms, g_wall = timed(lambda: B.dnatok_graph_launch(g, s.cuda_stream))
+        B.dnatok_graph_destroy(g)
+        tok.sync(s)
+        toks = calls * int(outs[0][2][0])
+        out["char_64x1MB"] = {
+            "calls": calls,
+            "plain_launches": {"us_per_call": 1e3 * p_wall / calls,
+                               "tokens_per_s": toks / p_wall * 1e3},
+            "graph_replay": {"us_per_call": 1e3 * g_wall / calls,
+                             "tokens_per_s": toks / g_wall * 1e3}}
+    return out
+
+
+def _serving(torch, P, dev, seconds: float):
+    """Config-5 request trace (Poisson 2000/s, 200 B-1 MB, 30% single-
+    nucleotide / 50% 6-mer / 20% BPE with the 4096-merge table) replayed in
+    real time through the serving loop, and through per-request plain
+    launches (host copy + encode + wait, one request at a time)."""
+    import numpy as np
+    import synth
+    B = P.binding
+    tr = synth.request_trace(duration_s=seconds)
+    n = len(tr.sizes)
+    m = np.loadtxt(os.path.join(ROOT, "tests", "golden", "bpe_merges_markov45_seed45_4096.txt"),
+                   dtype=np.int32)
+    pin = torch.from_numpy(tr.data).pin_memory()
+    base = pin.data_ptr()
+    res = {"requests": n, "offered_bytes_per_s": float(tr.sizes.sum() / seconds),
+           "budget_bytes": 4 << 30}
+
+    # --- serving loop
+    srv = B.dnatok_server_create(budget_bytes=4 << 30, host_arena_bytes=1 << 30,
+                                 max_batch_bytes=32 << 20, max_batch_requests=256, n_slots=4,
+                                 kmer_k=6, merges=m)
+    lat = np.zeros(n)
+    toks = 0
+    done_t = 0.0
+    try:
+        pending = []
+        t0 = time.perf_counter() + 0.05
+        i = 0
+        while i < n or pending:
+            now = time.perf_counter() - t0
+            while i < n and tr.arrival_s[i] <= now:
+                r = B.dnatok_server_submit(srv, int(tr.modes[i]), base + int(tr.offsets[i]),
+                                           int(tr.sizes[i]))
+                if r is None:
+                    break
+                pending.append((i, r))
+                i += 1
+            still = []
+            for (k, r) in pending:
+                out = B.dnatok_server_poll(srv, r)
+                if out is None:
+                    still.append((k, r))
+                    continue
+                lat[k] = out[2] / 1e3
+                toks += out[1]
+                B.dnatok_server_release(srv, r)
+                done_t = time.perf_counter() - t0
+            pending = still
+        st = B.dnatok_server_stats(srv)
+    finally:
+        B.dnatok_server_destroy(srv)
+    res["served"] = {"tokens_per_s": toks / done_t, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "batches": st["batches_launched"],
+                     "wall_s": done_t, "tokens": int(toks)}
+
+    # --- per-request plain launches
+    toks_b = {0: P.Tokenizer(P.CHAR), 1: P.Tokenizer(P.KMER, k=6), 2: P.Tokenizer(P.BPE, merges=m)}
+    mx = int(tr.sizes.max())
+    for t in toks_b.values():
+        t.reserve(mx, 1)
+    ids = torch.empty(mx + 16, dtype=torch.int32, device=dev)
+    hso = torch.zeros(2, dtype=torch.int64).pin_memory()
+    hoo = torch.zeros(2, dtype=torch.int64).pin_memory()
+    hto = torch.zeros(2, dtype=torch.int64).pin_memory()
+    s = torch.cuda.Stream()
+    lat_b = np.zeros(n)
+    toks2 = 0
+    t0 = time.perf_counter() + 0.05
+    for k in range(n):
+        while time.perf_counter() - t0 < tr.arrival_s[k]:
+            pass
+        ln = int(tr.sizes[k])
+        hso[1] = ln
+        B.dnatok_encode_host(toks_b[int(tr.modes[k])].h, base + int(tr.offsets[k]), ln,
+                             hso.data_ptr(), 1, ids.data_ptr(), ids.numel(), hoo.data_ptr(), 2,
+                             hto.data_ptr(), s.cuda_stream)
+        now = time.perf_counter() - t0
+        lat_b[k] = 1e3 * (now - tr.arrival_s[k])
+        toks2 += int(hto[0])
+    wall_b = time.perf_counter() - t0
+    for t in toks_b.values():
+        t.close()
+    res["per_request_launches"] = {"tokens_per_s": toks2 / wall_b,
+                                   "p50_ms": float(np.percentile(lat_b, 50)),
+                                   "p99_ms": float(np.percentile(lat_b, 99)), "wall_s": wall_b,
+                                   "tokens": toks2}
+    res["latency"] = "served: submit -> completion seen by the worker; per-request: arrival -> " \
+                     "result on the host (includes waiting behind earlier requests)"
+    return res
 
 
 def _cpu_baseline(data, offs, budget_s: float = 10.0):
@@ -376,16 +571,21 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": KERNEL,
-                         "algorithmic_bytes_per_launch": alg_bytes},
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "duration": "CUDA events around the whole step (all three launches)"},
             "e2e": {"value": n_ids * ws / e2e_s, "unit": "tokens/s",
                     "h2d_bytes_per_step": n_bytes + 8 * (n_seq + 1),
                     "d2h_bytes_per_step": 8 * (n_seq + 1) + 16,
                     "ms_per_step": 1e3 * e2e_s, "api": "dnatok_encode_host (pinned host buffers)"},
-            "gpu_launches": args.steps,
+            "gpu_launches": 3 * args.steps,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(data, offs)
+        if ws == 1 and not args.no_extras:
+            line["batched"] = _batched(torch, P, dev, data, offs, d_bytes, d_offs)
+            if args.serve_seconds > 0:
+                line["serving"] = _serving(torch, P, dev, args.serve_seconds)
         if args.stream_gib > 0:
             line["host_streamed"] = _streamed(torch, P, dev, int(args.stream_gib * 2**30))
         print(json.dumps(line), flush=True)
@@ -403,6 +603,10 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--shape", default=None, help="tile_bytes,threads,ctas_per_sm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the served request trace (0 = skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched / serving measurements")
     ap.add_argument("--stream-gib", type=float, default=8.0,
                     help="size of the host-streamed FASTA measurement (0 = skip)")
     args = ap.parse_args()

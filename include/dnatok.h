@@ -238,6 +238,64 @@ DNATOK_API dnatok_status dnatok_stream_wait(dnatok_handle *h, uint64_t req_id,
  * stream afterwards. */
 DNATOK_API dnatok_status dnatok_stream_close(dnatok_handle *h);
 
+/* -------------------------------------------------------------- serving */
+
+/*
+ * Serving loop: requests of mixed modes and sizes are submitted at any time
+ * (host bytes, one request = one record); a worker thread admits them under a
+ * device-memory budget, packs the queued requests of one mode into a batch
+ * and launches it on one of n_slots streams while earlier batches still run
+ * (continuous batching).  Every slot holds its own handle per mode, so the
+ * tables stay resident; inputs and outputs live in one device arena of
+ * budget_bytes (a request's ids stay there until it is released).  The paper
+ * names serving as a target use (Sec. 4.4) without a design.
+ */
+typedef struct dnatok_server dnatok_server;
+typedef struct {
+    int64_t budget_bytes;        /* device arena: inputs + outputs of admitted requests */
+    int64_t host_arena_bytes;    /* page-locked staging of submitted bytes */
+    int64_t max_batch_bytes;     /* input bytes packed into one batch (also the largest request) */
+    int32_t max_batch_requests;  /* requests in one batch */
+    int32_t n_slots;             /* batches in flight at once (streams), 1..16 */
+    int32_t kmer_k;              /* k of the DNATOK_KMER mode */
+    int32_t n_merges;            /* BPE table (DNATOK_BPE mode), may be 0 */
+    const int32_t *merges;
+} dnatok_server_cfg;
+
+typedef struct {
+    const int32_t *ids_d;  /* device ids of the request, valid until it is released */
+    int64_t n_ids;
+    double latency_us;     /* submit -> completion seen by the worker */
+} dnatok_server_result;
+
+typedef struct {
+    int64_t device_bytes_in_use;
+    int64_t batches_launched;
+    int64_t queued;
+    int64_t batches_running;
+} dnatok_server_counters;
+
+DNATOK_API dnatok_status dnatok_server_create(const dnatok_server_cfg *cfg, dnatok_server **out);
+/* Copy n host bytes into the staging arena and queue them (mode: DNATOK_CHAR
+ * with the default table, DNATOK_KMER with cfg.kmer_k, DNATOK_BPE with
+ * cfg.merges).  DNATOK_ERR_BUDGET if the staging arena is full (retry after
+ * releasing), DNATOK_ERR_CAPACITY if n exceeds max_batch_bytes. */
+DNATOK_API dnatok_status dnatok_server_submit(dnatok_server *s, int32_t mode,
+                                              const uint8_t *host_bytes, int64_t n,
+                                              uint64_t *req_id);
+/* DNATOK_PENDING, or DNATOK_OK with the result filled in. */
+DNATOK_API dnatok_status dnatok_server_poll(dnatok_server *s, uint64_t req_id,
+                                            dnatok_server_result *out);
+/* Copy a finished request's ids to host memory (capacity ids; *n_ids gets the
+ * count; DNATOK_ERR_CAPACITY if they do not fit).  Synchronous. */
+DNATOK_API dnatok_status dnatok_server_read(dnatok_server *s, uint64_t req_id, int32_t *host_ids,
+                                            int64_t capacity, int64_t *n_ids);
+/* Give the request's device output back to the arena. */
+DNATOK_API dnatok_status dnatok_server_release(dnatok_server *s, uint64_t req_id);
+DNATOK_API dnatok_status dnatok_server_stats(dnatok_server *s, dnatok_server_counters *out);
+/* Stop the worker, wait for the device, free everything. */
+DNATOK_API void dnatok_server_destroy(dnatok_server *s);
+
 /* ------------------------------------------------------ no allocation */
 
 /*
@@ -334,6 +392,13 @@ DNATOK_API dnatok_status dnatok_autotune(dnatok_handle *h, const uint8_t *bytes_
                                          int64_t *id_offsets_d, int64_t offsets_capacity,
                                          int32_t reps, const char *cache_path,
                                          dnatok_launch_cfg *best, float *best_ms);
+
+/* RAW input through dnatok_encode first tries the direct path: when no byte
+ * is below 0x21 (no separators), token positions follow from the record
+ * lengths alone and the kernel needs no cross-tile scan; the general kernel
+ * runs behind it only if the premise fails (same results either way).
+ * enable = 0 sends every encode straight to the general kernel.  Default 1. */
+DNATOK_API dnatok_status dnatok_set_direct(dnatok_handle *h, int32_t enable);
 
 /* BPE handles: symbols per segment of the merge pass (64..65536, a multiple
  * of 16, at least twice the longest token) and the halo each segment's pass

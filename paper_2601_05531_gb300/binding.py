@@ -44,6 +44,23 @@ class StreamResult(ctypes.Structure):
                 ("bytes_in", ctypes.c_int64)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("host_arena_bytes", ctypes.c_int64),
+                ("max_batch_bytes", ctypes.c_int64), ("max_batch_requests", ctypes.c_int32),
+                ("n_slots", ctypes.c_int32), ("kmer_k", ctypes.c_int32),
+                ("n_merges", ctypes.c_int32), ("merges", ctypes.POINTER(ctypes.c_int32))]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("ids_d", ctypes.c_void_p), ("n_ids", ctypes.c_int64),
+                ("latency_us", ctypes.c_double)]
+
+
+class ServerCounters(ctypes.Structure):
+    _fields_ = [("device_bytes_in_use", ctypes.c_int64), ("batches_launched", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("batches_running", ctypes.c_int64)]
+
+
 class LaunchCfg(ctypes.Structure):
     _fields_ = [("tile_bytes", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32)]
@@ -91,6 +108,7 @@ def lib():
             "dnatok_stream_wait": (_ST, [_P, ctypes.c_uint64, ctypes.POINTER(StreamResult)]),
             "dnatok_stream_close": (_ST, [_P]),
             "dnatok_set_bpe_launch": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
+            "dnatok_set_direct": (_ST, [_P, ctypes.c_int32]),
             "dnatok_get_bpe_launch": (_ST, [_P, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
             "dnatok_graph_begin": (_ST, [_P, _P]),
@@ -100,6 +118,14 @@ def lib():
             "dnatok_autotune": (_ST, [_P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.c_int32,
                                       ctypes.c_char_p, ctypes.POINTER(LaunchCfg),
                                       ctypes.POINTER(ctypes.c_float)]),
+            "dnatok_server_create": (_ST, [ctypes.POINTER(ServerCfg), ctypes.POINTER(_P)]),
+            "dnatok_server_submit": (_ST, [_P, ctypes.c_int32, _P, _I64,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+            "dnatok_server_poll": (_ST, [_P, ctypes.c_uint64, ctypes.POINTER(ServerResult)]),
+            "dnatok_server_read": (_ST, [_P, ctypes.c_uint64, _P, _I64, ctypes.POINTER(_I64)]),
+            "dnatok_server_release": (_ST, [_P, ctypes.c_uint64]),
+            "dnatok_server_stats": (_ST, [_P, ctypes.POINTER(ServerCounters)]),
+            "dnatok_server_destroy": (None, [_P]),
             "dnatok_encode_kmer_noalloc": (_ST, [ctypes.c_int, _P, _I64, _P, _I64, _P, _I64, _P,
                                                  _I64, _P, _P]),
         }
@@ -228,6 +254,10 @@ def dnatok_stream_close(h) -> None:
     check(lib().dnatok_stream_close(h), h)
 
 
+def dnatok_set_direct(h, enable: bool) -> None:
+    check(lib().dnatok_set_direct(h, int(bool(enable))), h)
+
+
 def dnatok_set_bpe_launch(h, seg_symbols: int, halo: int) -> None:
     check(lib().dnatok_set_bpe_launch(h, seg_symbols, halo), h)
 
@@ -267,6 +297,74 @@ def dnatok_autotune(h, bytes_d: int, n_bytes: int, seq_offsets_d: int, n_seq: in
                                 cache_path.encode() if cache_path else None, ctypes.byref(c),
                                 ctypes.byref(ms)), h)
     return (c.tile_bytes, c.threads, c.ctas_per_sm, c.chunk_tiles), ms.value
+
+
+def dnatok_server_create(budget_bytes: int = 4 << 30, host_arena_bytes: int = 1 << 30,
+                         max_batch_bytes: int = 32 << 20, max_batch_requests: int = 256,
+                         n_slots: int = 4, kmer_k: int = 6, merges=None):
+    """Returns (server address, keep-alive objects)."""
+    import numpy as np
+    m = None
+    c = ServerCfg(budget_bytes, host_arena_bytes, max_batch_bytes, max_batch_requests, n_slots,
+                  kmer_k, 0, None)
+    if merges is not None:
+        m = np.ascontiguousarray(np.asarray(merges, dtype=np.int32).reshape(-1, 2))
+        c.n_merges = m.shape[0]
+        c.merges = m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    srv = _P()
+    st = lib().dnatok_server_create(ctypes.byref(c), ctypes.byref(srv))
+    if st < 0:
+        raise DnatokError(st, "dnatok_server_create: " + last_error(None))
+    return srv.value
+
+
+def dnatok_server_submit(srv, mode: int, host_bytes: int, n: int) -> int:
+    """Request id, or None when the staging arena is full (retry later)."""
+    r = ctypes.c_uint64()
+    st = lib().dnatok_server_submit(srv, mode, host_bytes, n, ctypes.byref(r))
+    if st == -5:
+        return None
+    if st < 0:
+        raise DnatokError(st, "dnatok_server_submit")
+    return r.value
+
+
+def dnatok_server_poll(srv, req_id: int):
+    """None while pending, else (ids device address, n_ids, latency_us)."""
+    out = ServerResult()
+    st = lib().dnatok_server_poll(srv, req_id, ctypes.byref(out))
+    if st == 1:
+        return None
+    if st < 0:
+        raise DnatokError(st, "dnatok_server_poll")
+    return (out.ids_d or 0, out.n_ids, out.latency_us)
+
+
+def dnatok_server_read(srv, req_id: int, n_ids: int):
+    """The request's ids as a numpy int32 array (the request must be done)."""
+    import numpy as np
+    out = np.empty(max(n_ids, 1), dtype=np.int32)
+    n = _I64()
+    st = lib().dnatok_server_read(srv, req_id, out.ctypes.data, n_ids, ctypes.byref(n))
+    if st < 0:
+        raise DnatokError(st, "dnatok_server_read")
+    return out[:n.value]
+
+
+def dnatok_server_release(srv, req_id: int) -> None:
+    st = lib().dnatok_server_release(srv, req_id)
+    if st < 0:
+        raise DnatokError(st, "dnatok_server_release")
+
+
+def dnatok_server_stats(srv) -> dict:
+    c = ServerCounters()
+    check(lib().dnatok_server_stats(srv, ctypes.byref(c)))
+    return {k: getattr(c, k) for k, _ in ServerCounters._fields_}
+
+
+def dnatok_server_destroy(srv) -> None:
+    lib().dnatok_server_destroy(srv)
 
 
 NOALLOC_MAX_BYTES = 1 << 30  # DNATOK_NOALLOC_MAX_BYTES

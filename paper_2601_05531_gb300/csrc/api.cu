@@ -75,6 +75,7 @@ dnatok_status next_epoch(dnatok_handle *h, cudaStream_t s, unsigned *epoch) {
     h->epoch++;
     if ((h->epoch & ((1u << kEpochBits) - 1)) == 0) {  // epoch wrap: forget every old descriptor
         cudaError_t e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * h->desc_cap, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_gate, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
         h->epoch++;
     }
@@ -123,13 +124,31 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
     }
     p.n_tiles = tiles_for(n_bytes, p.head_pad, sh.tile);
     p.n_chunks = (p.n_tiles + sh.chunk_tiles - 1) / sh.chunk_tiles;
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(s, &capst) == cudaSuccess &&
+                           capst != cudaStreamCaptureStatusNone;
+    if (bsrc == BSRC_LIST && !carry_in && !carry_out && h->direct &&
+        direct_eligible(mode, n_bnd - 1, h->lut_host)) {
+        // RAW input: the direct path, with the general kernel behind it
+        unsigned ep = 0;
+        st = next_epoch(h, s, &ep);
+        if (st != DNATOK_OK) return st;
+        if (capturing) {  // replays must not see an earlier replay's switch
+            e = cudaMemsetAsync(h->d_gate, 0, sizeof(unsigned), s);
+            if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(gate)");
+        }
+        e = launch_direct(mode, bytes, n_bytes, seq_offsets, n_bnd - 1, out, offsets_out,
+                          totals_out, h->d_gate, ep, k, h->d_lut, h->sm_count, s);
+        if (e != cudaSuccess) return fail_cuda(h, e, "direct kernel launch");
+        p.gate = h->d_gate;
+        p.gate_epoch = ep;
+    }
     st = next_epoch(h, s, &p.epoch);
     if (st != DNATOK_OK) return st;
     {
         // Under stream capture the epoch is baked into the graph and every
         // replay reuses it, so the graph clears the descriptors it uses first.
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        if (capturing) {
             e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * (size_t)p.n_chunks, s);
             if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
         }
@@ -181,6 +200,8 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
     if (e == cudaSuccess) e = cudaMemset(h->d_counter, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_gate, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(h->d_gate, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
         std::string m = std::string("CUDA setup failed: ") + cudaGetErrorString(e);
         dnatok_destroy(h);
@@ -212,6 +233,7 @@ void dnatok_destroy(dnatok_handle *h) {
     cudaFree(h->d_tile_rec);
     cudaFree(h->d_counter);
     cudaFree(h->d_status);
+    cudaFree(h->d_gate);
     cudaFree(h->d_stage_bytes);
     cudaFree(h->d_stage_offs);
     cudaFree(h->d_stage_out_offs);
@@ -248,6 +270,9 @@ dnatok_status dnatok_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_
     if (n_bytes < 0 || (n_bytes > 0 && !bytes_d))
         return fail(h, DNATOK_ERR_ARG, "bad input bytes");
     if (!id_offsets_d) return fail(h, DNATOK_ERR_ARG, "id_offsets is NULL");
+    if (((uintptr_t)id_offsets_d | (uintptr_t)seq_offsets_d | (uintptr_t)totals_d) & 7u)
+        return fail(h, DNATOK_ERR_ARG, "int64 arrays must be 8-byte aligned");
+    if ((uintptr_t)ids_out_d & 3u) return fail(h, DNATOK_ERR_ARG, "ids_out must be 4-byte aligned");
     if (h->fmt == DNATOK_RAW) {
         if (!seq_offsets_d || n_seq < 0) return fail(h, DNATOK_ERR_ARG, "RAW needs seq_offsets");
         if (n_seq >= INT32_MAX - 1) return fail(h, DNATOK_ERR_ARG, "too many sequences");
@@ -379,6 +404,12 @@ dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg) 
     cfg->threads = h->shape.threads;
     cfg->ctas_per_sm = h->shape.ctas_per_sm;
     cfg->chunk_tiles = h->shape.chunk_tiles;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_set_direct(dnatok_handle *h, int32_t enable) {
+    if (!h || (enable != 0 && enable != 1)) return DNATOK_ERR_ARG;
+    h->direct = enable != 0;
     return DNATOK_OK;
 }
 

@@ -50,11 +50,21 @@ constexpr int kScanThreads = 256;
 struct BpeTables {
     int V;            // 4 + M token ids; N_ID = V
     int lmax;         // longest self-encoding token
-    int n_nodes;      // trie nodes (root = 0)
-    const uint2 *child;          // per node: 4 x u16 children (0 = none)
-    const unsigned short *tok;   // per node: token id ending here or kNoTok
+    int n_deep;       // deep trie nodes (index 0 = "none")
+    // tokens of 1..5 bases: direct tables indexed by the d-mer code (last
+    // base in the low bits), at offsets 0, 4, 20, 84, 340 (1364 entries)
+    const unsigned short *kmtok;
+    // tokens of 6+ bases: the last 6 bases index node6 (4096 entries) -> a
+    // node of the trie of reversed strings below depth 6
+    const unsigned short *node6;
+    const uint2 *child;          // per deep node: 4 x u16 children (0 = none)
+    const unsigned short *tok;   // per deep node: token id ending here or kNoTok
     const unsigned *compat;      // V x V bits, row = left token
 };
+
+// offset of the d-base table: (4^d - 4) / 3 = 0, 4, 20, 84, 340 for d = 1..5
+__host__ __device__ constexpr int km_off(int d) { return ((1 << (2 * d)) - 4) / 3; }
+constexpr int kKmTotal = 1364;
 
 struct BpeWork {
     const uint8_t *sym;          // symbols 0..3 bases, 4 N-class
@@ -69,6 +79,7 @@ struct BpeWork {
     long long *base;             // per segment: exclusive prefix of count
     long long *block_sums;
     int *bad;                    // [0] = count, then segment ids
+    unsigned *bits;              // per segment: token ends, one bit per symbol
     long long *tot;              // {n_sym, n_rec} from the symbol pass
     long long *rec_off;          // record starts (symbols), rewritten as id offsets
     long long offsets_cap;
@@ -93,11 +104,15 @@ __device__ __forceinline__ bool compat_bit(const unsigned *compat, int V, unsign
     return (__ldg(compat + (bit >> 5)) >> (bit & 31)) & 1u;
 }
 
-// Token id of the symbols [e - L + 1, e] (reversed-string trie walk).
+// Token id of the L symbols ending at e (L <= lmax).
 __device__ __forceinline__ unsigned token_at(const BpeTables &T, const uint8_t *sym, long long e,
                                              int L) {
-    unsigned node = 0;
-    for (int d = 1; d <= L; ++d) node = trie_child(T.child, node, sym[e - d + 1]);
+    unsigned code = 0;
+    const int d0 = L < 6 ? L : 6;
+    for (int d = d0; d >= 1; --d) code = (code << 2) | sym[e - d + 1];
+    if (L <= 5) return T.kmtok[km_off(L) + code];
+    unsigned node = T.node6[code];
+    for (int d = 7; d <= L; ++d) node = trie_child(T.child, node, sym[e - d + 1]);
     return T.tok[node];
 }
 
@@ -114,33 +129,45 @@ __device__ __forceinline__ long long rec_upper(const long long *rec_off, long lo
 
 // One step of the prefix DP at symbol j (a base).  reg: codes of the word so
 // far (newest in the low bits); wd: symbols of the word through j; ring:
-// last token ids by position mod 32.  Returns (length << 16) | token.
+// last token ids by position mod 32.  Candidates are tried longest first;
+// the first that starts the word or is compatible with the token before it
+// is last(j).  Returns (length << 16) | token.
 __device__ __forceinline__ unsigned dp_step(const BpeTables &T, unsigned long long reg, int wd,
                                             long long j, const unsigned short *ring) {
-    unsigned cand[kMaxTokLen];
-    int nc = 0;
-    const int dmax = wd < T.lmax ? wd : T.lmax;
-    unsigned node = 0;
-    for (int d = 1; d <= dmax; ++d) {
-        node = trie_child(T.child, node, (unsigned)(reg >> (2 * (d - 1))) & 3u);
-        if (!node) break;
-        const unsigned t = T.tok[node];
-        if (t != kNoTok) cand[nc++] = ((unsigned)d << 16) | t;
-    }
-    unsigned pick = cand[0];
-    for (int q = nc - 1; q >= 0; --q) {
-        const int d = (int)(cand[q] >> 16);
-        if (d == wd) {
-            pick = cand[q];
-            break;
+    const int dm = wd < T.lmax ? wd : T.lmax;
+    auto fits = [&](int d, unsigned t) -> bool {
+        if (d == wd) return true;
+        return compat_bit(T.compat, T.V, ring[(j - d) & 31], t);
+    };
+    if (dm >= 6) {
+        const unsigned n6 = T.node6[(unsigned)reg & 0xFFFu];
+        if (n6) {
+            unsigned short deep[kMaxTokLen];
+            int nd = 0;
+            unsigned node = n6;
+            for (int d = 7; d <= dm; ++d) {
+                node = trie_child(T.child, node, (unsigned)(reg >> (2 * (d - 1))) & 3u);
+                if (!node) break;
+                const unsigned t = T.tok[node];
+                deep[d - 7] = (unsigned short)t;
+                nd = d - 6;
+            }
+            for (int q = nd - 1; q >= 0; --q) {
+                const unsigned t = deep[q];
+                if (t != kNoTok && fits(q + 7, t)) return ((unsigned)(q + 7) << 16) | t;
+            }
+            const unsigned t6 = T.tok[n6];
+            if (t6 != kNoTok && fits(6, t6)) return (6u << 16) | t6;
         }
-        const unsigned prev = ring[(j - d) & 31];
-        if (compat_bit(T.compat, T.V, prev, cand[q] & 0xFFFFu)) {
-            pick = cand[q];
-            break;
-        }
     }
-    return pick;
+    unsigned t5[5];
+#pragma unroll
+    for (int d = 1; d <= 5; ++d)
+        t5[d - 1] = T.kmtok[km_off(d) + ((unsigned)reg & ((1u << (2 * d)) - 1u))];
+#pragma unroll
+    for (int d = 5; d >= 2; --d)
+        if (d <= dm && t5[d - 1] != kNoTok && fits(d, t5[d - 1])) return ((unsigned)d << 16) | t5[d - 1];
+    return (1u << 16) | t5[0];  // a single base: no other candidate fits
 }
 
 // ------------------------------------------------------- table building
@@ -243,20 +270,26 @@ __global__ void bpe_compat_kernel(RankHash h, const uint8_t *pool, const int *po
 
 extern __shared__ __align__(16) unsigned char bpe_smem[];
 
-// Copy the trie into shared memory (when it fits) and return the tables the
-// block uses.
+// Copy the lookup tables into shared memory (when they fit) and return the
+// tables the block uses.
 __device__ BpeTables stage_tables(const BpeTables &G, bool smem) {
     if (!smem) return G;
     uint2 *c = reinterpret_cast<uint2 *>(bpe_smem);
-    unsigned short *t = reinterpret_cast<unsigned short *>(c + G.n_nodes);
-    for (int i = threadIdx.x; i < G.n_nodes; i += blockDim.x) {
+    unsigned short *t = reinterpret_cast<unsigned short *>(c + G.n_deep);
+    unsigned short *n6 = t + G.n_deep;
+    unsigned short *km = n6 + 4096;
+    for (int i = threadIdx.x; i < G.n_deep; i += blockDim.x) {
         c[i] = G.child[i];
         t[i] = G.tok[i];
     }
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) n6[i] = G.node6[i];
+    for (int i = threadIdx.x; i < kKmTotal; i += blockDim.x) km[i] = G.kmtok[i];
     __syncthreads();
     BpeTables T = G;
     T.child = c;
     T.tok = t;
+    T.node6 = n6;
+    T.kmtok = km;
     return T;
 }
 
@@ -288,32 +321,53 @@ __global__ void __launch_bounds__(256) bpe_dp_kernel(BpeTables G, bool smem, Bpe
     unsigned long long reg = 0;
     int wd = 0;
     uint8_t *halo = W.halo + seg * (long long)W.H;
-    for (long long x = s - W.H; x < a; ++x) halo[x - (s - W.H)] = 0;
-    for (long long j = a; j < e; ++j) {
-        while (j == next_b) {
-            wd = 0;
-            reg = 0;
-            ++r;
-            next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
+    const long long h0 = s - W.H;  // first halo position (a multiple of 16)
+    // 16 symbols per load and 16 lengths per store: s, H and the buffers are
+    // 16-byte aligned; a record start inside the halo only shifts where the
+    // pass begins within its 16-symbol block
+    for (long long j0 = (a > h0 ? a : h0) & ~15ll; j0 < e; j0 += 16) {
+        const uint4 sv = *reinterpret_cast<const uint4 *>(W.sym + j0);
+        const unsigned long long s_lo = ((unsigned long long)sv.y << 32) | sv.x;
+        const unsigned long long s_hi = ((unsigned long long)sv.w << 32) | sv.z;
+        unsigned long long l_lo = 0, l_hi = 0;
+        const int q0 = (j0 < a) ? (int)(a - j0) : 0;
+        const int q1 = (e - j0 < 16) ? (int)(e - j0) : 16;
+#pragma unroll 1
+        for (int q = q0; q < q1; ++q) {
+            const long long j = j0 + q;
+            while (j == next_b) {
+                wd = 0;
+                reg = 0;
+                ++r;
+                next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
+            }
+            const unsigned c = (unsigned)((q < 8 ? s_lo >> (8 * q) : s_hi >> (8 * (q - 8))) & 0xFFu);
+            unsigned L, t;
+            if (c >= 4) {
+                L = 1;
+                t = (unsigned)T.V;
+                wd = 0;
+                reg = 0;
+                if (j < s) exact = true;  // a word starts after it, before the segment
+            } else {
+                reg = (reg << 2) | c;
+                if (wd < 63) ++wd;
+                const unsigned pk = dp_step(T, reg, wd, j, ring);
+                L = pk >> 16;
+                t = pk & 0xFFFFu;
+            }
+            ring[j & 31] = (unsigned short)t;
+            if (q < 8) l_lo |= (unsigned long long)L << (8 * q);
+            else l_hi |= (unsigned long long)L << (8 * (q - 8));
         }
-        const unsigned c = W.sym[j];
-        unsigned L, t;
-        if (c >= 4) {
-            L = 1;
-            t = (unsigned)T.V;
-            wd = 0;
-            reg = 0;
-            if (j < s) exact = true;  // a word starts after it, before the segment
-        } else {
-            reg = (reg << 2) | c;
-            if (wd < 63) ++wd;
-            const unsigned pk = dp_step(T, reg, wd, j, ring);
-            L = pk >> 16;
-            t = pk & 0xFFFFu;
-        }
-        ring[j & 31] = (unsigned short)t;
-        if (j >= s) W.len[j] = (uint8_t)L;
-        else halo[j - (s - W.H)] = (uint8_t)L;
+        const uint4 lv = make_uint4((unsigned)l_lo, (unsigned)(l_lo >> 32), (unsigned)l_hi,
+                                    (unsigned)(l_hi >> 32));
+        if (j0 >= s) *reinterpret_cast<uint4 *>(W.len + j0) = lv;
+        else if (W.H > 0) *reinterpret_cast<uint4 *>(halo + (j0 - h0)) = lv;
+    }
+    if (a > h0) {
+        // halo positions before the pass began hold 0 (no value)
+        for (long long x = h0; x < (a & ~15ll); ++x) halo[x - h0] = 0;
     }
     W.flags[seg] = exact ? 1 : 0;
 }
@@ -538,23 +592,68 @@ __global__ void __launch_bounds__(kScanThreads) bpe_scan_down(BpeWork W) {
         }
 }
 
-// Each segment writes its tokens walking its chain backwards.
+// Thread per segment walks its chain (from its entry, backwards) and marks
+// the token ends in a bitmap, one bit per symbol, in global memory; then each
+// warp emits its 32 segments one after another with lane w taking bitmap word
+// w (symbols 32w..32w+31), so the warp writes one contiguous run of ids.
 __global__ void __launch_bounds__(256) bpe_emit_kernel(BpeTables G, bool smem, BpeWork W) {
     const BpeTables T = stage_tables(G, smem);
+    const int lane = threadIdx.x & 31;
     const long long seg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (dev_failed(W.status)) return;
     const long long n_sym = W.tot[0];
-    const long long s = seg * W.S;
-    if (s >= n_sym) return;
-    const long long e_end = (s + W.S < n_sym) ? s + W.S : n_sym;
-    long long e = e_end - 1 - W.entry[seg];
-    long long pos = W.base[seg] + W.count[seg] - 1;
-    while (e >= s) {
-        const int L = W.len[e];
-        const unsigned id = (W.sym[e] >= 4) ? (unsigned)T.V : token_at(T, W.sym, e, L);
-        if (pos >= 0 && pos < W.out_cap) W.out[pos] = (int)id;
-        --pos;
-        e -= L;
+    const long long n_seg = (n_sym + W.S - 1) / W.S;
+    const int words = (W.S + 31) / 32;
+    if (seg < n_seg) {
+        const long long s = seg * W.S;
+        const long long e_end = (s + W.S < n_sym) ? s + W.S : n_sym;
+        unsigned *bits = W.bits + seg * words;
+        long long e = e_end - 1 - W.entry[seg];
+        int cw = words - 1;
+        unsigned acc = 0;
+        while (e >= s) {
+            const int x = (int)(e - s);
+            while ((x >> 5) < cw) {
+                bits[cw--] = acc;
+                acc = 0;
+            }
+            acc |= 1u << (x & 31);
+            e -= W.len[e];
+        }
+        for (; cw >= 0; --cw) {
+            bits[cw] = acc;
+            acc = 0;
+        }
+    }
+    __syncwarp();
+    const long long seg0 = seg - lane;
+    for (int i = 0; i < 32; ++i) {
+        const long long sg = seg0 + i;
+        if (sg >= n_seg) break;
+        const long long s = sg * W.S;
+        const unsigned *bits = W.bits + sg * words;
+        long long out = W.base[sg];
+        for (int w0 = 0; w0 < words; w0 += 32) {
+            const int w = w0 + lane;
+            const unsigned wb = (w < words) ? bits[w] : 0u;
+            const unsigned c = __popc(wb);
+            unsigned x = c;  // inclusive scan of the counts over the warp
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            long long pos = out + (x - c);
+            unsigned m = wb;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const long long j = s + 32ll * w + b;
+                const unsigned id = (W.sym[j] >= 4) ? (unsigned)T.V : token_at(T, W.sym, j, W.len[j]);
+                if (pos < W.out_cap) W.out[pos] = (int)id;
+                ++pos;
+            }
+            out += __shfl_sync(0xffffffffu, x, 31);
+        }
     }
 }
 
@@ -588,9 +687,11 @@ __global__ void bpe_offsets_kernel(BpeWork W) {
 // ======================================================================= host
 
 struct BpeState {
-    int M = 0, V = 0, lmax = 1, n_nodes = 1;
+    int M = 0, V = 0, lmax = 1, n_nodes = 1;  // n_nodes: deep trie nodes
     uint2 *d_child = nullptr;
     unsigned short *d_tok = nullptr;
+    unsigned short *d_node6 = nullptr;
+    unsigned short *d_kmtok = nullptr;
     unsigned *d_compat = nullptr;
     int S = 1024, H = 64;
 
@@ -602,6 +703,7 @@ struct BpeState {
     unsigned *d_count = nullptr;
     long long *d_base = nullptr, *d_bsums = nullptr, *d_tot = nullptr;
     int *d_bad = nullptr;
+    unsigned *d_bits = nullptr;
     long long seg_cap = 0;
     int ws_S = 0, ws_H = 0;
 };
@@ -622,6 +724,8 @@ void free_workspace(BpeState *b) {
     cudaFree(b->d_bsums);
     cudaFree(b->d_tot);
     cudaFree(b->d_bad);
+    cudaFree(b->d_bits);
+    b->d_bits = nullptr;
     b->d_sym = b->d_len = b->d_halo = b->d_flags = b->d_map_v = b->d_const = b->d_entry = nullptr;
     b->d_map_c = nullptr;
     b->d_count = nullptr;
@@ -652,13 +756,13 @@ dnatok_status ensure_bpe_workspace(dnatok_handle *h, long long n_bytes, cudaStre
     size_t sz[] = {(size_t)cap + 16, (size_t)cap + 16, (size_t)(nseg * b->H + 16), (size_t)nseg,
                    (size_t)nseg * 32, (size_t)nseg, (size_t)nseg, (size_t)nseg * 32 * 2,
                    (size_t)nseg * 4, (size_t)(nseg + 1) * 8, (size_t)nblk * 8, 16,
-                   (size_t)(nseg + 1) * 4};
+                   (size_t)(nseg + 1) * 4, (size_t)nseg * 4 * ((b->S + 31) / 32) + 16};
     void **ptr[] = {(void **)&b->d_sym,   (void **)&b->d_len,   (void **)&b->d_halo,
                     (void **)&b->d_flags, (void **)&b->d_map_v, (void **)&b->d_const,
                     (void **)&b->d_entry, (void **)&b->d_map_c, (void **)&b->d_count,
                     (void **)&b->d_base,  (void **)&b->d_bsums, (void **)&b->d_tot,
-                    (void **)&b->d_bad};
-    for (int i = 0; i < 13; ++i) {
+                    (void **)&b->d_bad,   (void **)&b->d_bits};
+    for (int i = 0; i < 14; ++i) {
         e = cudaMalloc(ptr[i], sz[i]);
         if (e != cudaSuccess) {
             free_workspace(b);
@@ -673,7 +777,8 @@ dnatok_status ensure_bpe_workspace(dnatok_handle *h, long long n_bytes, cudaStre
 }
 
 size_t trie_smem_bytes(const BpeState *b) {
-    return (size_t)b->n_nodes * (sizeof(uint2) + sizeof(unsigned short)) + 16;
+    return (size_t)b->n_nodes * (sizeof(uint2) + sizeof(unsigned short)) +
+           sizeof(unsigned short) * (4096 + kKmTotal) + 16;
 }
 
 }  // namespace
@@ -798,28 +903,63 @@ dnatok_status bpe_create(dnatok_handle *h, const int32_t *merges, int32_t n_merg
         }
         tk[node] = (unsigned short)t;
     }
-    const int n_nodes = (int)tk.size();
-    if (n_nodes > 65535) {
+    if (tk.size() > 65535) {
         cleanup();
         return fail(h, DNATOK_ERR_TABLE, "BPE token trie exceeds 65535 nodes");
     }
-    std::vector<uint2> child(n_nodes);
-    for (int i = 0; i < n_nodes; ++i) {
-        child[i].x = ch[4 * i] | (ch[4 * i + 1] << 16);
-        child[i].y = ch[4 * i + 2] | (ch[4 * i + 3] << 16);
+    // Split the lookup: tokens of 1..5 bases in direct tables by their code
+    // (last base in the low bits); the 6-base suffix indexes node6, which
+    // points into the part of the trie at depth >= 6 (renumbered from 1).
+    std::vector<unsigned short> kmtok(kKmTotal, (unsigned short)kNoTok);
+    std::vector<unsigned short> node6(4096, 0);
+    std::vector<int> depth(tk.size(), 0), deep_id(tk.size(), 0);
+    std::vector<unsigned> code(tk.size(), 0);
+    std::vector<unsigned> order(1, 0);  // BFS over the full trie
+    int n_deep = 1;                     // deep index 0 = none
+    for (size_t qi = 0; qi < order.size(); ++qi) {
+        const unsigned u = order[qi];
+        if (depth[u] >= 6) deep_id[u] = n_deep++;
+        if (depth[u] >= 1 && depth[u] <= 5 && tk[u] != kNoTok) kmtok[km_off(depth[u]) + code[u]] = tk[u];
+        for (unsigned c = 0; c < 4; ++c) {
+            const unsigned v = ch[u * 4 + c];
+            if (!v) continue;
+            depth[v] = depth[u] + 1;
+            // reversed path: the d-th symbol back from the end lands at bits 2(d-1)
+            code[v] = depth[v] <= 6 ? code[u] | (c << (2 * (depth[v] - 1))) : code[u];
+            order.push_back(v);
+        }
+    }
+    std::vector<uint2> child(n_deep, make_uint2(0, 0));
+    std::vector<unsigned short> dtok(n_deep, (unsigned short)kNoTok);
+    for (size_t u = 0; u < tk.size(); ++u) {
+        if (depth[u] < 6) continue;
+        const int id = deep_id[u];
+        if (depth[u] == 6) node6[code[u]] = (unsigned short)id;
+        dtok[id] = tk[u];
+        unsigned cc[4];
+        for (int c = 0; c < 4; ++c) cc[c] = ch[u * 4 + c] ? (unsigned)deep_id[ch[u * 4 + c]] : 0u;
+        child[id].x = cc[0] | (cc[1] << 16);
+        child[id].y = cc[2] | (cc[3] << 16);
     }
     b->lmax = lmax;
-    b->n_nodes = n_nodes;
+    b->n_nodes = n_deep;
     b->H = std::max(64, ((4 * lmax + 15) / 16) * 16);
     const unsigned long long nbits = (unsigned long long)V * V;
     const size_t cwords = (size_t)((nbits + 31) / 32) + 2;
-    e = cudaMalloc(&b->d_child, sizeof(uint2) * n_nodes);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tok, sizeof(unsigned short) * n_nodes);
+    e = cudaMalloc(&b->d_child, sizeof(uint2) * n_deep);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tok, sizeof(unsigned short) * n_deep);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_node6, sizeof(unsigned short) * 4096);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_kmtok, sizeof(unsigned short) * kKmTotal);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_compat, cwords * 4);
     if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_child, child.data(), sizeof(uint2) * n_nodes, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(b->d_child, child.data(), sizeof(uint2) * n_deep, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_tok, tk.data(), sizeof(unsigned short) * n_nodes, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(b->d_tok, dtok.data(), sizeof(unsigned short) * n_deep, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_node6, node6.data(), sizeof(unsigned short) * 4096, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_kmtok, kmtok.data(), sizeof(unsigned short) * kKmTotal,
+                       cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_compat, 0, cwords * 4);
     if (e == cudaSuccess) {
         const long long threads = (long long)V * ((V + 31) / 32);
@@ -839,6 +979,8 @@ void bpe_destroy(dnatok_handle *h) {
     free_workspace(b);
     cudaFree(b->d_child);
     cudaFree(b->d_tok);
+    cudaFree(b->d_node6);
+    cudaFree(b->d_kmtok);
     cudaFree(b->d_compat);
     delete b;
     h->bpe = nullptr;
@@ -884,7 +1026,7 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     cudaError_t e = cudaMemsetAsync(b->d_bad, 0, sizeof(int), s);
     if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync");
 
-    BpeTables T{b->V, b->lmax, b->n_nodes, b->d_child, b->d_tok, b->d_compat};
+    BpeTables T{b->V, b->lmax, b->n_nodes, b->d_kmtok, b->d_node6, b->d_child, b->d_tok, b->d_compat};
     BpeWork W;
     std::memset(&W, 0, sizeof(W));
     W.sym = b->d_sym;
@@ -899,6 +1041,7 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     W.base = b->d_base;
     W.block_sums = b->d_bsums;
     W.bad = b->d_bad;
+    W.bits = b->d_bits;
     W.tot = b->d_tot;
     W.rec_off = reinterpret_cast<long long *>(id_offsets_d);
     W.offsets_cap = offsets_capacity;

@@ -30,9 +30,11 @@ struct dnatok_handle {
     long long rec_cap = 0;
     unsigned long long *d_counter = nullptr;
     int *d_status = nullptr;
+    unsigned *d_gate = nullptr;  // direct path -> general path switch (an epoch)
     unsigned epoch = 0;
 
-    dnatok::LaunchShape shape{16384, 256, 4, 8};  // tile, threads, CTAs per SM, tiles per chunk
+    dnatok::LaunchShape shape{16384, 256, 4, 8};
+    bool direct = true;  // try the direct path on RAW input (dnatok_set_direct)  // tile, threads, CTAs per SM, tiles per chunk
 
     // device staging of dnatok_encode_host
     uint8_t *d_stage_bytes = nullptr;
@@ -72,6 +74,13 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
                               long long offsets_cap, long long *totals_out, const Carry *carry_in,
                               Carry *carry_out, int start_boundary, int end_boundary,
                               cudaStream_t s);
+
+// Direct path for RAW input without separators (direct.cu)
+bool direct_eligible(int mode, long long n_seq, const int32_t *lut_host);
+cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const long long *so,
+                          long long n_seq, void *out, long long *offsets_out,
+                          long long *totals_out, unsigned *gate, unsigned epoch, int k,
+                          const int *lut, int sm_count, cudaStream_t s);
 
 // BPE path (bpe.cu)
 dnatok_status bpe_create(dnatok_handle *h, const int32_t *merges, int32_t n_merges);

@@ -71,6 +71,8 @@ struct TileParams {
     int end_boundary;              // boundary after the chunk's last byte (non-list sources)
     int head_pad;                  // (uintptr_t)bytes & 15
     int lut_keeps_bases;           // MODE_CHAR: the table keeps all of A C G T a c g t
+    const unsigned *gate;          // non-null: run only if *gate == gate_epoch
+    unsigned gate_epoch;
 };
 
 constexpr int kMaxB = 256;     // segments per emission round
@@ -393,6 +395,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
     constexpr int NW = NT / 32;
     static_assert(VPT >= 1 && NV % NT == 0 && NW >= 4, "tile / thread shape");
     constexpr bool PACKED = (MODE == MODE_KMER || MODE == MODE_SYM);
+    // behind the direct path: run only when it found its premise broken
+    if (p.gate && *(volatile const unsigned *)p.gate != p.gate_epoch) return;
 
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t *tbuf0 = smem;

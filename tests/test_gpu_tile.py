@@ -27,11 +27,16 @@ def P():
     return P
 
 
-def run_gpu(P, data, mode, k=1, offs=None, fmt=0, lut=None, shape=None, pad=0):
+def run_gpu(P, data, mode, k=1, offs=None, fmt=0, lut=None, shape=None, pad=0, direct=None):
+    """direct: try the direct path on RAW input (default: only when no launch
+    shape is forced, since a shape is a setting of the general kernel)."""
     import torch
     with P.Tokenizer(mode, k=k, lut=lut, fmt=fmt) as tok:
         if shape:
             tok.set_launch(*shape)
+        if direct is None:
+            direct = shape is None
+        P.binding.dnatok_set_direct(tok.h, direct)
         raw = np.zeros(len(data) + pad, dtype=np.uint8)
         raw[pad:] = data
         d = torch.from_numpy(raw).cuda()[pad:]
@@ -99,10 +104,11 @@ def test_worked_examples_on_gpu(P):
 
 # -------------------------------------------------------------------- RAW input
 
+@pytest.mark.parametrize("direct", [True, False])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8, 11, 14, 15])
-def test_kmer_raw_ragged(P, k):
+def test_kmer_raw_ragged(P, k, direct):
     data, offs = ragged(100 + k, 300, 0, 3000)
-    assert_same(run_gpu(P, data, P.KMER, k=k, offs=offs),
+    assert_same(run_gpu(P, data, P.KMER, k=k, offs=offs, direct=direct),
                 oracle.encode(data, oracle.KMER, k=k, seq_offsets=offs), "k=%d" % k)
 
 
@@ -116,11 +122,12 @@ def test_kmer_raw_every_shape(P, shape):
                 oracle.encode(data, oracle.CHAR, seq_offsets=offs), str(shape))
 
 
+@pytest.mark.parametrize("direct", [True, False])
 @pytest.mark.parametrize("pad", [1, 3, 7, 8, 15])
-def test_misaligned_input(P, pad):
+def test_misaligned_input(P, pad, direct):
     data, offs = ragged(50 + pad, 60, 0, 5000)
     for mode, k in ((P.CHAR, 1), (P.KMER, 6), (P.KMER, 5)):
-        assert_same(run_gpu(P, data, mode, k=k, offs=offs, pad=pad),
+        assert_same(run_gpu(P, data, mode, k=k, offs=offs, pad=pad, direct=direct),
                     oracle.encode(data, mode, k=k, seq_offsets=offs), "pad %d" % pad)
 
 
@@ -268,12 +275,15 @@ def test_bad_tables_rejected(P):
 
 # ------------------------------------------------------------ full-size workloads
 
-def test_full_single_sequence_1mb(P):
+@pytest.mark.parametrize("direct", [True, False])
+def test_full_single_sequence_1mb(P, direct):
     data, offs = synth.single_sequence_1mb()
-    assert_same(run_gpu(P, data, P.CHAR, offs=offs), oracle.encode(data, oracle.CHAR, seq_offsets=offs))
+    assert_same(run_gpu(P, data, P.CHAR, offs=offs, direct=direct),
+                oracle.encode(data, oracle.CHAR, seq_offsets=offs))
 
 
-def test_full_kmer_batch_4096(P):
+@pytest.mark.parametrize("direct", [True, False])
+def test_full_kmer_batch_4096(P, direct):
     data, offs = synth.kmer_batch_4096()
-    assert_same(run_gpu(P, data, P.KMER, k=6, offs=offs),
+    assert_same(run_gpu(P, data, P.KMER, k=6, offs=offs, direct=direct),
                 oracle.encode(data, oracle.KMER, k=6, seq_offsets=offs))
