@@ -326,6 +326,16 @@ __device__ __forceinline__ Agg shfl_agg(const Agg &a, int src) {
 }
 
 // Record an error in the device status word (first error wins).
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while the previous kernel on its
+// stream is still running; pdl_wait() blocks until that kernel has finished
+// and its memory is visible (a no-op otherwise); pdl_launch_dependents() lets
+// the next such kernel start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_dev_status(int *status, int code) {
     if (status) atomicCAS(status, DEV_OK, code);
 }

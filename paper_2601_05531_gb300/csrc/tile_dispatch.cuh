@@ -20,8 +20,23 @@ static cudaError_t launch_one(const TileParams &p, cudaStream_t s, int sm_count,
     long long grid = (long long)sm_count * ctas_per_sm;
     if (grid > p.n_chunks) grid = p.n_chunks;
     if (grid < 1) grid = 1;
-    tile_kernel<MODE, BSRC, NT, TILE, NSUB><<<(unsigned)grid, NT, SMEM, s>>>(p);
-    return cudaGetLastError();
+    if (!p.gate) {
+        tile_kernel<MODE, BSRC, NT, TILE, NSUB><<<(unsigned)grid, NT, SMEM, s>>>(p);
+        return cudaGetLastError();
+    }
+    // behind the direct path: launched as a programmatic dependent so its
+    // launch overlaps the direct kernel's tail (it waits for it on the device)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tile_kernel<MODE, BSRC, NT, TILE, NSUB>, p);
 }
 
 // The supported shapes: tile bytes, threads, tiles per chunk.

@@ -396,7 +396,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
     static_assert(VPT >= 1 && NV % NT == 0 && NW >= 4, "tile / thread shape");
     constexpr bool PACKED = (MODE == MODE_KMER || MODE == MODE_SYM);
     // behind the direct path: run only when it found its premise broken
-    if (p.gate && *(volatile const unsigned *)p.gate != p.gate_epoch) return;
+    if (p.gate) {
+        pdl_wait();
+        if (*(volatile const unsigned *)p.gate != p.gate_epoch) return;
+    }
 
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t *tbuf0 = smem;
