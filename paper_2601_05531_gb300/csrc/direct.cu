@@ -24,10 +24,7 @@ namespace dnatok {
 
 namespace {
 
-constexpr int kDTile = 16384;  // bytes per tile
 constexpr int kDThreads = 256;
-constexpr int kDVec = kDTile / 16;             // 16-byte vectors per tile
-constexpr int kDVpt = kDVec / kDThreads;       // per thread
 constexpr int kPlanThreads = 1024;
 
 struct DirectParams {
@@ -201,162 +198,317 @@ __device__ __forceinline__ long long warp_rec_search(const long long *so, long l
     return lo + (31 - __clz(b));
 }
 
-// k-mer ids.  Each CTA walks a contiguous range of tiles, loading the next
-// tile's vectors while it emits the current one; k-mers whose first byte lies
-// in a tile are written by that tile, record batches of 32 flattened so that
-// every thread has work even when records are short.
-__global__ void __launch_bounds__(kDThreads) direct_kmer_kernel(DirectParams q) {
-    __shared__ uint2 PN[kDVec + 1];     // per vector: 2-bit codes (first in the top bits), N flags
-    __shared__ long long s_obase[32];   // output index of the batch's first k-mer, per record
-    __shared__ int s_ap0[32], s_lim[32], s_pre[33];
-    __shared__ long long s_r0, s_next;
-    __shared__ int s_more;
-    __shared__ int s_stop;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long lo = q.head_pad, hi = q.head_pad + q.n;      // valid aligned range
-    const int k = q.k;
-    const unsigned unk = 1u << (2 * k);
-    const unsigned nmask = (1u << k) - 1u;
-    const long long per = (q.n_tiles + gridDim.x - 1) / gridDim.x;
-    const long long t_begin = blockIdx.x * per;
-    const long long t_end = (t_begin + per < q.n_tiles) ? t_begin + per : q.n_tiles;
-    bool sep = false;
-    uint4 cur[kDVpt];
-    // tile-relative 32-bit offsets from here on: the tile's own pointer and
-    // the number of its bytes that exist are computed once per tile
-    auto tile_valid = [&](long long t) -> int {
-        const long long v = hi - t * kDTile;
-        return v <= 0 ? 0 : (v >= kDTile + 16 ? kDTile + 16 : (int)v);
+// ------------------------------------------------------------ k-mer ids
+//
+// Warp-streamed: each warp owns a contiguous run of 512-byte steps (one
+// 16-byte vector per lane) and keeps kDepth steps in flight in registers.
+// The k-mers that start in a lane's vector are written by that lane; the
+// codes of the vector after it come from the next lane by shuffle (from the
+// next step's lane 0 for lane 31, so a step is emitted one iteration after
+// it is classified).  A step that lies inside one record (the usual case)
+// needs only the warp-uniform phase of the record's k-mer frame and the
+// output index of its next k-mer, both advanced in registers; steps that hold
+// record boundaries resolve them per lane from a per-warp window of kWin
+// entries of seq_offsets / id_offsets in shared memory.  No block-wide
+// barrier anywhere.  k is a template parameter, so every shift, mask and
+// division by k is a constant.
+
+constexpr int kSThreads = 256;
+constexpr int kSWarps = kSThreads / 32;
+constexpr int kStep = 512;   // bytes per warp step
+constexpr int kDepth = 4;    // warp steps in flight per lane
+constexpr int kWin = 32;     // records in a warp's window
+
+struct RecWin {
+    long long s[kWin + 1];   // seq_offsets[rb .. rb + kWin] (n past the end)
+    long long o[kWin];       // id_offsets[rb .. rb + kWin - 1]
+};
+
+// Largest r in [0, n] with so[r] <= x, by one warp (32-way probes).  Only
+// reads so[0..n]; on non-monotone offsets it returns some index in range
+// (the plan kernel rejects those before any result is used).
+__device__ __forceinline__ long long warp_rec_search_safe(const long long *so, long long n,
+                                                          long long x, int lane) {
+    long long lo = 0, hi = n;
+    for (int round = 0; round < 16 && hi - lo > 31; ++round) {
+        const long long step = ((hi - lo) >> 5) + 1;
+        const long long idx = lo + lane * step;
+        const bool ok = idx <= hi && __ldg(so + idx) <= x;
+        const unsigned b = __ballot_sync(0xffffffffu, ok);
+        if (b == 0u) return lo;
+        const int L = 31 - __clz(b);
+        const long long nlo = lo + L * step;
+        if (L < 31 && nlo + step <= hi) hi = nlo + step - 1;
+        lo = nlo;
+    }
+    const long long idx = lo + lane;
+    const bool ok = idx <= hi && __ldg(so + idx) <= x;
+    const unsigned b = __ballot_sync(0xffffffffu, ok);
+    return b == 0u ? lo : lo + (31 - __clz(b));
+}
+
+// One 16-byte vector classified for the k-mer path: 2-bit codes (first byte
+// in the top bits) and, when any byte is not one of ACGTacgt, the N flags
+// (byte j in bit j) and the below-0x21 flags.
+//
+// A byte x is one of ACGTacgt iff its bits 0,3,4,6,7 are those of 'A' (0x41),
+// or those of 'T' (0x50) when it is a T, T being bit 2 set and bit 1 clear:
+// (x & 0xD9) ^ (0x41 + 0x0F * T) == 0.  The code is bit1^bit2 (low bit) and
+// bit2^bit3 (high bit).
+struct KVec {
+    unsigned codes, bad;  // bad: nonzero iff a byte is not a base letter
+};
+__device__ __forceinline__ unsigned kv_word(unsigned x, unsigned &code) {
+    const unsigned s1 = x >> 1, s2 = x >> 2;
+    code = (s1 ^ s2) & 0x03030303u;
+    const unsigned t = s2 & ~s1 & 0x01010101u;                 // T per byte
+    return (x & 0xD9D9D9D9u) ^ (t * 0x0Fu + 0x41414141u);  // zero bytes: bases
+}
+__device__ __forceinline__ unsigned kv_pack(unsigned c0, unsigned c1, unsigned c2, unsigned c3) {
+    // each product's top byte holds its word's four codes, first byte highest
+    const unsigned p0 = c0 * 0x40100401u, p1 = c1 * 0x40100401u;
+    const unsigned p2 = c2 * 0x40100401u, p3 = c3 * 0x40100401u;
+    return __byte_perm(__byte_perm(p3, p2, 0x0073), __byte_perm(p1, p0, 0x0073), 0x5410);
+}
+// N flags of a vector from its four check words (zero byte = base)
+__device__ __forceinline__ unsigned kv_nflags(unsigned v0, unsigned v1, unsigned v2, unsigned v3) {
+    auto nib = [](unsigned v) -> unsigned {
+        const unsigned nz = (((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
+        return ((nz >> 7) * 0x10204080u) >> 28;  // byte j's flag -> bit j
     };
-    auto load_tile = [&](long long t, uint4 *dst) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(q.base + t * kDTile) + tid;
-        const int nv = tile_valid(t);
+    return nib(v0) | (nib(v1) << 4) | (nib(v2) << 8) | (nib(v3) << 12);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams q) {
+    static_assert(K >= 2 && K <= 15, "k-mer length");
+    constexpr unsigned UNK = 1u << (2 * K);
+    constexpr unsigned KMASK = (1u << K) - 1u;
+    constexpr unsigned M32 = (unsigned)((0x100000000ull + K - 1) / K);  // ceil(2^32 / K)
+    constexpr int SLOTS = (16 + K - 1) / K;     // k-mer starts per vector, at most
+    constexpr int SURE = (16 - (K - 1) + K - 1) / K;  // slots present whatever the phase
+    __shared__ RecWin wins[kSWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RecWin &W = wins[warp];
+    const long long lo = q.head_pad, hi = q.head_pad + q.n;  // valid aligned range
+    const long long S = (hi + kStep - 1) / kStep;
+    const long long nw = (long long)gridDim.x * kSWarps;
+    const long long gw = (long long)blockIdx.x * kSWarps + warp;
+    const long long s_begin = gw * S / nw, s_end = (gw + 1) * S / nw;
+    if (s_begin >= s_end) return;
+    const int n_steps = (int)(s_end - s_begin);
+    auto div_k = [](unsigned x) -> unsigned { return __umulhi(x, M32); };  // x < 2^17
+
+    // This lane's vectors: step u (relative to s_begin) holds vector
+    // (s_begin + u) * 32 + lane; step n_steps is the halo (lane 0 only).
+    const uint4 *vp = reinterpret_cast<const uint4 *>(q.base) + s_begin * 32 + lane;
+    int u_lim;  // steps u < u_lim are read by this lane
+    {
+        const long long nvec = (hi + 15) / 16;  // vectors holding input bytes
+        const long long mine = nvec - (s_begin * 32 + lane);  // vectors of mine: u*32 < mine
+        const long long by_data = mine <= 0 ? 0 : (mine + 31) / 32;
+        const long long by_range = lane == 0 ? n_steps + 1 : n_steps;
+        u_lim = (int)(by_data < by_range ? by_data : by_range);
+    }
+    uint4 buf[kDepth];
 #pragma unroll
-        for (int i = 0; i < kDVpt; ++i)
-            dst[i] = (16 * (i * kDThreads + tid) < nv) ? __ldg(src + i * kDThreads)
-                                                        : make_uint4(0u, 0u, 0u, 0u);
+    for (int d = 0; d < kDepth; ++d) buf[d] = d < u_lim ? __ldg(vp + d * 32) : make_uint4(0u, 0u, 0u, 0u);
+
+    // The record holding the first step: seq_offsets is input, so this runs
+    // while the plan kernel (a programmatic predecessor) is still working.
+    long long rb;
+    int nv, ic;
+    {
+        const long long X = s_begin * kStep - q.head_pad;
+        long long r = warp_rec_search_safe(q.so, q.n_seq, X > 0 ? X : 0, lane);
+        if (r > q.n_seq - 1) r = q.n_seq - 1;
+        rb = r;
+        ic = 0;
+        const long long i = rb + lane;
+        W.s[lane] = i <= q.n_seq ? __ldg(q.so + i) : q.n;
+        if (lane == 0) W.s[kWin] = rb + kWin <= q.n_seq ? __ldg(q.so + rb + kWin) : q.n;
+        nv = (q.n_seq - rb < kWin) ? (int)(q.n_seq - rb) : kWin;
+    }
+    // id offsets come from the plan kernel: wait for it, then see whether it
+    // rejected seq_offsets
+    pdl_wait();
+    if (*(volatile const unsigned *)q.gate == q.epoch) return;
+    W.o[lane] = rb + lane < q.n_seq ? q.offsets_out[rb + lane] : 0;
+    __syncwarp();
+
+    auto win_fill = [&](long long nrb) {
+        __syncwarp();
+        const long long i = nrb + lane;
+        W.s[lane] = i <= q.n_seq ? __ldg(q.so + i) : q.n;
+        if (lane == 0) W.s[kWin] = nrb + kWin <= q.n_seq ? __ldg(q.so + nrb + kWin) : q.n;
+        W.o[lane] = i < q.n_seq ? q.offsets_out[i] : 0;
+        rb = nrb;
+        nv = (q.n_seq - nrb < kWin) ? (int)(q.n_seq - nrb) : kWin;
+        __syncwarp();
     };
-    if (t_begin < t_end) load_tile(t_begin, cur);
-    for (long long t = t_begin; t < t_end; ++t) {
-        const long long A0 = t * kDTile;
-        uint4 nxt[kDVpt];
-        if (t + 1 < t_end) load_tile(t + 1, nxt);
-        const long long x_lo = (A0 > lo ? A0 : lo) - q.head_pad;
-        const long long x_hi = ((A0 + kDTile < hi) ? A0 + kDTile : hi) - q.head_pad;
-        if (t == t_begin) {
-            // the id offsets come from the plan kernel, which may still be
-            // running (programmatic launch): wait for it, then see whether it
-            // rejected the offsets
-            pdl_wait();
-            if (tid == 0) s_stop = (*(volatile const unsigned *)q.gate == q.epoch) ? 1 : 0;
-            __syncthreads();
-            if (s_stop) return;
-        }
-        if (warp == 0) {
-            const long long r0 = warp_rec_search(q.so, q.n_seq, x_lo, lane);
-            if (lane == 0) s_r0 = r0;
-        }
-        {
-            const int nv = tile_valid(t);  // bytes of the tile that exist
-            const int first = (A0 < lo) ? (int)(lo - A0) : 0;  // the head pad, first tile only
+
+    // warp-uniform state of the step to emit, which starts at X
+    long long X = s_begin * kStep - q.head_pad;
+    long long re;   // end of record ic
+    long long obJ;  // output index of the record's first k-mer starting at or after X
+    int ph;         // that k-mer's start - X (>= K only before the input's first byte)
+    {
+        const long long xc = X > 0 ? X : 0, rs = W.s[0];
+        const long long J = rec_tokens(q, xc - rs);  // ceil((xc - rs) / k)
+        ph = (int)(rs + J * K - X);
+        obJ = W.o[0] + J;
+        re = W.s[1];
+    }
+    const int c_lane = 16 * lane + K - 1;
+    int *const out = static_cast<int *>(q.out);
+
+    unsigned cw_p = 0u, nf_p = 0u;  // the previous step's codes and N flags
+    bool sep = false, give_up = false;
+    for (int u0 = 0; u0 <= n_steps; u0 += kDepth) {
 #pragma unroll
-            for (int i = 0; i < kDVpt; ++i) {
-                const int v = i * kDThreads + tid;
-                const Vec16 c = classify16(cur[i]);
-                if (c.low) {
-                    const int b0 = 16 * v;
-                    unsigned m = 0xFFFFu;
-                    if (b0 < first) m &= 0xFFFFu << (first - b0 < 16 ? first - b0 : 16);
-                    if (b0 + 16 > nv) m &= (nv - b0 <= 0) ? 0u : ((1u << (nv - b0)) - 1u);
-                    if (c.low & m) sep = true;
+        for (int d = 0; d < kDepth; ++d) {
+            const int u = u0 + d;
+            if (u > n_steps) break;
+            const uint4 w = buf[d];
+            buf[d] = u + kDepth < u_lim ? __ldg(vp + (d + kDepth) * 32) : make_uint4(0u, 0u, 0u, 0u);
+            unsigned c0, c1, c2, c3;
+            const unsigned v0 = kv_word(w.x, c0), v1 = kv_word(w.y, c1);
+            const unsigned v2 = kv_word(w.z, c2), v3 = kv_word(w.w, c3);
+            const unsigned codes = kv_pack(c0, c1, c2, c3);
+            unsigned nf = 0u;
+            if ((v0 | v1 | v2 | v3) != 0u) {  // rare: something other than a base letter
+                nf = kv_nflags(v0, v1, v2, v3);
+                if (u < n_steps) {
+                    const unsigned low = dgather4(dlow4(w.x)) | (dgather4(dlow4(w.y)) << 4) |
+                                         (dgather4(dlow4(w.z)) << 8) | (dgather4(dlow4(w.w)) << 12);
+                    if (low & lane_mask16(16 * ((s_begin + u) * 32 + lane), lo, hi)) sep = true;
                 }
-                PN[v] = make_uint2(c.codes, c.nflags);
             }
-        }
-        if (tid == 0) {  // halo: the first vector of the next tile
-            const long long ab = A0 + kDTile;
-            if (ab < hi) {
-                const Vec16 c = classify16(__ldg(reinterpret_cast<const uint4 *>(q.base + ab)));
-                PN[kDVec] = make_uint2(c.codes, c.nflags);
-            } else {
-                PN[kDVec] = make_uint2(0u, 0u);
-            }
-        }
-        __syncthreads();
-        long long r = s_r0;
-        const long long shift = q.head_pad - A0;  // input position -> tile offset
-        while (true) {
-            if (warp == 0) {
-                const long long rr = r + lane;
-                int cnt = 0;
-                if (rr < q.n_seq) {
-                    const long long rs = q.so[rr];
-                    if (rs < x_hi) {
-                        const long long re = q.so[rr + 1];
-                        const long long s0 = rs > x_lo ? rs : x_lo;
-                        const long long s1 = re < x_hi ? re : x_hi;
-                        if (s1 > s0) {
-                            const long long m_lo = rec_tokens(q, s0 - rs);
-                            cnt = (int)(rec_tokens(q, s1 - rs) - m_lo);
-                            s_ap0[lane] = (int)(rs + m_lo * k + shift);
-                            const long long re_t = re + shift;
-                            s_lim[lane] = re_t > kDTile + 32 ? kDTile + 32 : (int)re_t;
-                            s_obase[lane] = q.offsets_out[rr] + m_lo;
+            if (u > 0) {
+                // emit step u - 1, whose codes are cw_p
+                const unsigned a = __shfl_down_sync(0xffffffffu, cw_p, 1);
+                const unsigned b = __shfl_sync(0xffffffffu, codes, 0);
+                const unsigned cw = cw_p, cw_nx = lane == 31 ? b : a;
+                const long long Xe = X + kStep;
+                // N flags only where the warp's step (or the next vector) has any
+                const bool anyN = __any_sync(0xffffffffu, (nf_p | (lane == 0 ? nf : 0u)) != 0u);
+                unsigned nwin = 0u;
+                if (anyN) {
+                    const unsigned na = __shfl_down_sync(0xffffffffu, nf_p, 1);
+                    const unsigned nb = __shfl_sync(0xffffffffu, nf, 0);
+                    nwin = nf_p | ((lane == 31 ? nb : na) << 16);
+                }
+                if (re >= Xe + 16 && X >= 0) {
+                    // the whole step (and 16 bytes past it) lies in one record
+                    const unsigned qd = div_k((unsigned)(c_lane - ph));
+                    const int o0 = ph + (int)qd * K - 16 * lane;  // first start, in [0, K)
+                    int *dst = out + (obJ + qd);
+#pragma unroll
+                    for (int t = 0; t < SLOTS; ++t) {
+                        const int o = o0 + t * K;
+                        if (t >= SURE && o >= 16) break;
+                        unsigned id = __umulhi(__funnelshift_l(cw_nx, cw, 2 * o), 1u << (2 * K));
+                        if (anyN && ((nwin >> o) & KMASK)) id = UNK;
+                        dst[t] = (int)id;
+                    }
+                    const unsigned qn = div_k((unsigned)(kStep - ph + K - 1));
+                    ph += (int)qn * K - kStep;
+                    obJ += qn;
+                } else {
+                    // record boundaries, a tail or the input's edges in this step
+                    if (!(rb + nv >= q.n_seq || W.s[nv] >= Xe)) {
+                        if (ic > 0) {
+                            win_fill(rb + ic);
+                            ic = 0;
+                        }
+                        if (!(rb + nv >= q.n_seq || W.s[nv] >= Xe)) {
+                            give_up = true;  // > kWin records in 512 bytes: the general path
+                            break;
                         }
                     }
+                    auto kmer_at = [&](int o) -> unsigned {  // k-mer starting at byte o of the vector
+                        const unsigned id = __funnelshift_l(cw_nx, cw, 2 * o) >> (32 - 2 * K);
+                        return ((nwin >> o) & KMASK) ? UNK : id;
+                    };
+                    const int x0r = 16 * lane;
+                    int i = ic;
+                    while (i + 1 < nv && W.s[i + 1] <= X + x0r) ++i;
+                    int p, rer;
+                    long long ob;
+                    if (i == ic) {
+                        const int qd = x0r > ph ? (int)div_k((unsigned)(x0r - ph + K - 1)) : 0;
+                        p = ph + qd * K;
+                        ob = obJ + qd;
+                    } else {
+                        const int rs = (int)(W.s[i] - X);
+                        const int qd = x0r > rs ? (int)div_k((unsigned)(x0r - rs + K - 1)) : 0;
+                        p = rs + qd * K;
+                        ob = W.o[i] + qd;
+                    }
+                    {
+                        const long long e = W.s[i + 1] - X;
+                        rer = e >= (1 << 30) ? (1 << 30) : (int)e;
+                    }
+                    while (true) {
+                        const int lim = rer < x0r + 16 ? rer : x0r + 16;
+                        int *dst = out + ob;
+                        for (int t = 0; p < lim; p += K, ++t) {
+                            const unsigned id = kmer_at(p - x0r);
+                            dst[t] = (int)(p + K > rer ? UNK : id);
+                        }
+                        if (rer >= x0r + 16 || i + 1 >= nv) break;
+                        ++i;  // the next record starts inside this vector
+                        p = rer;
+                        ob = W.o[i];
+                        const long long e = W.s[i + 1] - X;
+                        rer = e >= (1 << 30) ? (1 << 30) : (int)e;
+                    }
+                    if (u < n_steps) {
+                        // the record state for the next step, which starts at Xe
+                        int j = ic;
+                        bool moved = false;
+                        while (true) {
+                            while (j + 1 < nv && W.s[j + 1] <= Xe) ++j;
+                            if (j + 1 == nv && rb + nv < q.n_seq && W.s[nv] <= Xe) {
+                                win_fill(rb + nv);  // slide past the window
+                                j = 0;
+                                moved = true;
+                                continue;
+                            }
+                            break;
+                        }
+                        if (j == ic && !moved) {
+                            // same record: its next k-mer start at or after Xe
+                            const int dd = (int)(X + ph - Xe);  // start - Xe, > -kStep
+                            if (dd < 0) {
+                                const unsigned qn = div_k((unsigned)(-dd + K - 1));
+                                ph = dd + (int)qn * K;
+                                obJ += qn;
+                            } else {
+                                ph = dd;
+                            }
+                        } else {  // a record that starts in (X, Xe]
+                            ic = j;
+                            const unsigned qn = div_k((unsigned)(Xe - W.s[j]) + K - 1);
+                            ph = (int)(W.s[j] + (long long)qn * K - Xe);
+                            obJ = W.o[j] + qn;
+                        }
+                        re = W.s[ic + 1];
+                    }
                 }
-                int x = cnt;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                s_pre[lane + 1] = x;
-                if (lane == 0) {
-                    s_pre[0] = 0;
-                    const long long nr = r + 32;
-                    s_more = (nr < q.n_seq && q.so[nr] < x_hi) ? 1 : 0;
-                    s_next = nr;
-                }
+                X = Xe;
             }
-            __syncthreads();
-            const int total = s_pre[32];
-            auto kmer_id = [&](int ap, int lim) -> unsigned {
-                unsigned id = unk;
-                if (ap + k <= lim) {
-                    const int wi = ap >> 4, off = ap & 15;
-                    const uint2 a = PN[wi], b = PN[wi + 1];
-                    const unsigned tw = __funnelshift_l(b.x, a.x, 2 * off);
-                    const unsigned nw = a.y | (b.y << 16);
-                    if (!((nw >> off) & nmask)) id = tw >> (32 - 2 * k);
-                }
-                return id;
-            };
-            if (s_pre[1] == total) {
-                // one record holds every k-mer of the batch (the usual case)
-                const int ap0 = s_ap0[0], lim = s_lim[0];
-                int *o = static_cast<int *>(q.out) + s_obase[0];
-                for (int i = tid; i < total; i += kDThreads) o[i] = (int)kmer_id(ap0 + i * k, lim);
-            } else {
-                for (int f = tid; f < total; f += kDThreads) {
-                    int j = 0;  // largest j with s_pre[j] <= f
-#pragma unroll
-                    for (int b = 16; b > 0; b >>= 1)
-                        if (j + b <= 32 && s_pre[j + b] <= f) j += b;
-                    const int i = f - s_pre[j];
-                    static_cast<int *>(q.out)[s_obase[j] + i] = (int)kmer_id(s_ap0[j] + i * k, s_lim[j]);
-                }
-            }
-            const bool more = s_more != 0;
-            r = s_next;
-            __syncthreads();
-            if (!more) break;
+            cw_p = codes;
+            nf_p = nf;
         }
-        if (t + 1 < t_end) {
-#pragma unroll
-            for (int i = 0; i < kDVpt; ++i) cur[i] = nxt[i];
-        }
+        if (give_up) break;
+        vp += kDepth * 32;  // vp points at step u0 of the next round
     }
-    if (__syncthreads_or(sep) && tid == 0) raise_gate(q);
+    if (give_up) {
+        if (lane == 0) raise_gate(q);
+        return;
+    }
+    if (__any_sync(0xffffffffu, sep) && lane == 0) raise_gate(q);
 }
 
 // Single-nucleotide ids / BPE symbols: one output per byte at the byte's own
@@ -426,6 +578,17 @@ __global__ void __launch_bounds__(kDThreads) direct_byte_kernel(DirectParams q) 
     if (__syncthreads_or(sep) && tid == 0) raise_gate(q);
 }
 
+cudaError_t launch_kmer_k(int k, const cudaLaunchConfig_t &cfg, const DirectParams &q) {
+    switch (k) {
+#define DNATOK_K(KK) \
+    case KK: return cudaLaunchKernelEx(&cfg, direct_kmer_kernel<KK>, q);
+        DNATOK_K(2) DNATOK_K(3) DNATOK_K(4) DNATOK_K(5) DNATOK_K(6) DNATOK_K(7) DNATOK_K(8)
+        DNATOK_K(9) DNATOK_K(10) DNATOK_K(11) DNATOK_K(12) DNATOK_K(13) DNATOK_K(14) DNATOK_K(15)
+#undef DNATOK_K
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 bool direct_eligible(int mode, long long n_seq, const int32_t *lut_host) {
@@ -455,11 +618,9 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
     q.k = k;
     q.kinv = k > 1 ? ~0ull / (unsigned long long)k + 1ull : 0ull;
     q.lut = lut;
-    q.n_tiles = (q.head_pad + n + kDTile - 1) / kDTile;
+    q.n_tiles = 0;
     direct_plan_kernel<<<1, kPlanThreads, 0, s>>>(q);
     if (n > 0) {
-        long long grid = (long long)sm_count * 8;
-        if (grid > q.n_tiles) grid = q.n_tiles;
         // programmatic dependent launch: it starts while the plan runs
         cudaLaunchConfig_t cfg = {};
         cfg.blockDim = dim3(kDThreads);
@@ -469,14 +630,30 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
         attr.val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
-        if (mode == MODE_KMER) {
+        if (mode == MODE_KMER && k >= 2) {
+            // one wave of resident CTAs, every warp with at least one step
+            static int occ = 0;
+            if (occ == 0) {
+                int o = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, direct_kmer_kernel<6>, kSThreads,
+                                                                  0) != cudaSuccess || o < 1)
+                    o = 1;
+                occ = o;
+            }
+            const long long steps = (q.head_pad + n + kStep - 1) / kStep;
+            long long grid = (long long)sm_count * occ;
+            const long long need = (steps + kSWarps - 1) / kSWarps;
+            if (grid > need) grid = need;
+            cfg.blockDim = dim3(kSThreads);
             cfg.gridDim = dim3((unsigned)grid);
-            return cudaLaunchKernelEx(&cfg, direct_kmer_kernel, q);
+            return launch_kmer_k(k, cfg, q);
         }
+        // single-nucleotide ids, symbols, and 1-mers (the default table maps
+        // A/C/G/T to 0..3 and every other kept byte to 4 = UNK)
         long long g2 = ((q.head_pad + n + 15) / 16 + kDThreads - 1) / kDThreads;
         if (g2 > (long long)sm_count * 8) g2 = (long long)sm_count * 8;
         cfg.gridDim = dim3((unsigned)g2);
-        if (mode == MODE_CHAR) return cudaLaunchKernelEx(&cfg, direct_byte_kernel<MODE_CHAR>, q);
+        if (mode != MODE_SYM) return cudaLaunchKernelEx(&cfg, direct_byte_kernel<MODE_CHAR>, q);
         return cudaLaunchKernelEx(&cfg, direct_byte_kernel<MODE_SYM>, q);
     }
     return cudaGetLastError();

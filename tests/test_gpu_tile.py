@@ -186,9 +186,25 @@ def test_many_boundaries_in_one_tile(P):
     lens[1000:2500] = 0
     data, offs = synth.markov_batch(lens, 0.4, seed=9)
     for mode, k in ((P.KMER, 3), (P.KMER, 6), (P.CHAR, 1)):
-        for shape in (SHAPES[0], SHAPES[3]):
+        for shape in (SHAPES[0], SHAPES[3], None):
             assert_same(run_gpu(P, data, mode, k=k, offs=offs, shape=shape),
                         oracle.encode(data, mode, k=k, seq_offsets=offs))
+
+
+@pytest.mark.parametrize("k", [2, 6, 15])
+def test_direct_record_density(P, k):
+    # the direct path with 1-600 byte records: steps holding from zero to
+    # dozens of record starts, runs of empty records, records ending inside a
+    # k-mer's 16-byte window
+    rng = np.random.default_rng(40 + k)
+    for hi in (8, 40, 600):
+        lens = rng.integers(0, hi + 1, size=3000)
+        lens[rng.random(3000) < 0.05] = 0
+        data, offs = synth.markov_batch(lens, 0.4, seed=int(hi))
+        for pad in (0, 5):
+            assert_same(run_gpu(P, data, P.KMER, k=k, offs=offs, pad=pad, direct=True),
+                        oracle.encode(data, oracle.KMER, k=k, seq_offsets=offs),
+                        "k=%d hi=%d pad=%d" % (k, hi, pad))
 
 
 def test_empty_inputs(P):
