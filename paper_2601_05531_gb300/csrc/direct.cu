@@ -121,11 +121,6 @@ __device__ __forceinline__ unsigned dlow4(unsigned x) {
 __device__ __forceinline__ unsigned dgather4(unsigned m) {
     return (((m >> 7) & 0x01010101u) * 0x01020408u) >> 24;
 }
-__device__ __forceinline__ unsigned dpack4(unsigned c) {
-    const unsigned r = __byte_perm(c, 0, 0x0123);
-    const unsigned m = r | (r >> 6);
-    return (m & 0xFu) | ((m >> 12) & 0xF0u);
-}
 // mask of the byte lanes of a vector at aligned position ab that lie in
 // [lo, hi) (aligned coordinates), byte j in bit j
 __device__ __forceinline__ unsigned lane_mask16(long long ab, long long lo, long long hi) {
@@ -270,26 +265,167 @@ __device__ __forceinline__ unsigned kv_pack(unsigned c0, unsigned c1, unsigned c
     const unsigned p2 = c2 * 0x40100401u, p3 = c3 * 0x40100401u;
     return __byte_perm(__byte_perm(p3, p2, 0x0073), __byte_perm(p1, p0, 0x0073), 0x5410);
 }
-// N flags of a vector from its four check words (zero byte = base)
+// N flags of a vector from its four check words (zero byte = base), base i
+// in bit i.  Two words' nonzero-byte flags go to bits 0 and 4 of each byte;
+// one multiply then moves byte j's two flags to bits 24 + j and 28 + j (every
+// partial product lands on its own bit, so nothing carries).
 __device__ __forceinline__ unsigned kv_nflags(unsigned v0, unsigned v1, unsigned v2, unsigned v3) {
-    auto nib = [](unsigned v) -> unsigned {
-        const unsigned nz = (((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
-        return ((nz >> 7) * 0x10204080u) >> 28;  // byte j's flag -> bit j
+    auto nz = [](unsigned v) -> unsigned {  // 0x80 per nonzero byte
+        return (((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
     };
-    return nib(v0) | (nib(v1) << 4) | (nib(v2) << 8) | (nib(v3) << 12);
+    const unsigned a = ((nz(v0) >> 7) | (nz(v1) >> 3)) * 0x01020408u;
+    const unsigned b = ((nz(v2) >> 7) | (nz(v3) >> 3)) * 0x01020408u;
+    return __byte_perm(a, b, 0x0073) & 0xFFFFu;  // bytes 2 and 3 of the permute are not zero
 }
+
+template <int K>
+struct KC {
+    static constexpr unsigned UNK = 1u << (2 * K);
+    static constexpr unsigned KMASK = (1u << K) - 1u;
+    static constexpr unsigned M32 = (unsigned)((0x100000000ull + K - 1) / K);  // ceil(2^32 / K)
+    static constexpr int SLOTS = (16 + K - 1) / K;  // k-mer starts per vector, at most
+    static constexpr int SURE = 16 / K;             // slots present whatever the phase
+    static constexpr int PERW = 16 / K;             // k-mers per 16-base funnel window
+    __device__ static __forceinline__ unsigned div(unsigned x) { return __umulhi(x, M32); }  // x < 2^17
+};
+
+// Record state of a warp between steps (all lanes hold the same values).
+struct RecState {
+    long long rb;   // record index of window entry 0
+    long long obJ;  // output index of record ic's first k-mer starting at or after the step
+    long long re;   // end of record ic
+    int nv;         // records in the window: min(kWin, n_seq - rb)
+    int ic;         // window index of the record holding the step's start
+    int ph;         // that k-mer's start - the step's start (>= K only before the first byte)
+    int give_up;    // more than kWin record starts in one step
+};
+
+// A step [X, X + kStep) that holds record boundaries, a record tail or the
+// input's edges: every lane resolves its own records from the window, then
+// the state moves on to the next step.
+template <int K>
+__device__ __forceinline__ RecState slow_step(RecState R, RecWin &W, const DirectParams &q, long long X,
+                                           unsigned cw, unsigned cw_nx, unsigned nwin, bool advance) {
+    using C = KC<K>;
+    if (R.give_up) return R;  // the general path redoes everything
+    const int lane = threadIdx.x & 31;
+    const long long Xe = X + kStep;
+    auto win_fill = [&](long long nrb) {
+        __syncwarp();
+        const long long i = nrb + lane;
+        W.s[lane] = i <= q.n_seq ? __ldg(q.so + i) : q.n;
+        if (lane == 0) W.s[kWin] = nrb + kWin <= q.n_seq ? __ldg(q.so + nrb + kWin) : q.n;
+        W.o[lane] = i < q.n_seq ? q.offsets_out[i] : 0;
+        R.rb = nrb;
+        R.nv = (q.n_seq - nrb < kWin) ? (int)(q.n_seq - nrb) : kWin;
+        __syncwarp();
+    };
+    // the window must hold every record that starts in [X, Xe)
+    if (!(R.rb + R.nv >= q.n_seq || W.s[R.nv] >= Xe)) {
+        if (R.ic > 0) {
+            win_fill(R.rb + R.ic);
+            R.ic = 0;
+        }
+        if (!(R.rb + R.nv >= q.n_seq || W.s[R.nv] >= Xe)) {
+            R.give_up = 1;  // the general path takes over
+            return R;
+        }
+    }
+    auto kmer_at = [&](int o) -> unsigned {  // k-mer starting at byte o of the lane's vector
+        const unsigned id = __funnelshift_l(cw_nx, cw, 2 * o) >> (32 - 2 * K);
+        return ((nwin >> o) & C::KMASK) ? C::UNK : id;
+    };
+    int *const out = static_cast<int *>(q.out);
+    const int x0r = 16 * lane;
+    int i = R.ic;
+    while (i + 1 < R.nv && W.s[i + 1] <= X + x0r) ++i;
+    int p, rer;
+    long long ob;
+    if (i == R.ic) {
+        const int qd = x0r > R.ph ? (int)C::div((unsigned)(x0r - R.ph + K - 1)) : 0;
+        p = R.ph + qd * K;
+        ob = R.obJ + qd;
+    } else {
+        const int rs = (int)(W.s[i] - X);
+        const int qd = x0r > rs ? (int)C::div((unsigned)(x0r - rs + K - 1)) : 0;
+        p = rs + qd * K;
+        ob = W.o[i] + qd;
+    }
+    {
+        const long long e = W.s[i + 1] - X;
+        rer = e >= (1 << 30) ? (1 << 30) : (int)e;
+    }
+    while (true) {
+        const int lim = rer < x0r + 16 ? rer : x0r + 16;
+        int *dst = out + ob;
+        for (int t = 0; p < lim; p += K, ++t) {
+            const unsigned id = kmer_at(p - x0r);
+            dst[t] = (int)(p + K > rer ? C::UNK : id);
+        }
+        if (rer >= x0r + 16 || i + 1 >= R.nv) break;
+        ++i;  // the next record starts inside this vector
+        p = rer;
+        ob = W.o[i];
+        const long long e = W.s[i + 1] - X;
+        rer = e >= (1 << 30) ? (1 << 30) : (int)e;
+    }
+    if (!advance) return R;
+    // the record state for the next step, which starts at Xe
+    int j = R.ic;
+    bool moved = false;
+    while (true) {
+        while (j + 1 < R.nv && W.s[j + 1] <= Xe) ++j;
+        if (j + 1 == R.nv && R.rb + R.nv < q.n_seq && W.s[R.nv] <= Xe) {
+            win_fill(R.rb + R.nv);  // slide past the window
+            j = 0;
+            moved = true;
+            continue;
+        }
+        break;
+    }
+    if (j == R.ic && !moved) {
+        // same record: its next k-mer start at or after Xe
+        const int dd = R.ph - kStep;  // start - Xe
+        if (dd < 0) {
+            const unsigned qn = C::div((unsigned)(-dd + K - 1));
+            R.ph = dd + (int)qn * K;
+            R.obJ += qn;
+        } else {
+            R.ph = dd;
+        }
+    } else {  // a record that starts in (X, Xe]
+        R.ic = j;
+        const unsigned qn = C::div((unsigned)(Xe - W.s[j]) + K - 1);
+        R.ph = (int)(W.s[j] + (long long)qn * K - Xe);
+        R.obJ = W.o[j] + qn;
+    }
+    R.re = W.s[R.ic + 1];
+    return R;
+}
+
+// 16-byte global -> shared copy that bypasses registers (zero-filled when
+// `full` is false, in which case nothing is read)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool full) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem),
+                 "r"(full ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kRing = 8;  // warp steps in flight: a ring of 8 x 512 bytes per warp
 
 template <int K>
 __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams q) {
     static_assert(K >= 2 && K <= 15, "k-mer length");
-    constexpr unsigned UNK = 1u << (2 * K);
-    constexpr unsigned KMASK = (1u << K) - 1u;
-    constexpr unsigned M32 = (unsigned)((0x100000000ull + K - 1) / K);  // ceil(2^32 / K)
-    constexpr int SLOTS = (16 + K - 1) / K;     // k-mer starts per vector, at most
-    constexpr int SURE = (16 - (K - 1) + K - 1) / K;  // slots present whatever the phase
+    using C = KC<K>;
     __shared__ RecWin wins[kSWarps];
+    __shared__ uint4 ring_s[kSWarps][kRing][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RecWin &W = wins[warp];
+    uint4 *const ring = &ring_s[warp][0][lane];  // this lane's slot of stage 0
     const long long lo = q.head_pad, hi = q.head_pad + q.n;  // valid aligned range
     const long long S = (hi + kStep - 1) / kStep;
     const long long nw = (long long)gridDim.x * kSWarps;
@@ -297,213 +433,146 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
     const long long s_begin = gw * S / nw, s_end = (gw + 1) * S / nw;
     if (s_begin >= s_end) return;
     const int n_steps = (int)(s_end - s_begin);
-    auto div_k = [](unsigned x) -> unsigned { return __umulhi(x, M32); };  // x < 2^17
 
     // This lane's vectors: step u (relative to s_begin) holds vector
     // (s_begin + u) * 32 + lane; step n_steps is the halo (lane 0 only).
-    const uint4 *vp = reinterpret_cast<const uint4 *>(q.base) + s_begin * 32 + lane;
+    const uint4 *const vp = reinterpret_cast<const uint4 *>(q.base) + s_begin * 32 + lane;
     int u_lim;  // steps u < u_lim are read by this lane
     {
         const long long nvec = (hi + 15) / 16;  // vectors holding input bytes
-        const long long mine = nvec - (s_begin * 32 + lane);  // vectors of mine: u*32 < mine
+        const long long mine = nvec - (s_begin * 32 + lane);
         const long long by_data = mine <= 0 ? 0 : (mine + 31) / 32;
         const long long by_range = lane == 0 ? n_steps + 1 : n_steps;
         u_lim = (int)(by_data < by_range ? by_data : by_range);
     }
-    uint4 buf[kDepth];
+    auto issue = [&](int u) {  // copy step u into its ring stage
+        const bool full = u < u_lim;
+        cp_async16(ring + (u & (kRing - 1)) * 32, full ? vp + u * 32 : vp, full);
+        cp_async_commit();
+    };
 #pragma unroll
-    for (int d = 0; d < kDepth; ++d) buf[d] = d < u_lim ? __ldg(vp + d * 32) : make_uint4(0u, 0u, 0u, 0u);
+    for (int u = 0; u < kRing - 1; ++u) issue(u);
 
     // The record holding the first step: seq_offsets is input, so this runs
     // while the plan kernel (a programmatic predecessor) is still working.
-    long long rb;
-    int nv, ic;
+    const long long X0 = s_begin * kStep - q.head_pad;
+    RecState R;
     {
-        const long long X = s_begin * kStep - q.head_pad;
-        long long r = warp_rec_search_safe(q.so, q.n_seq, X > 0 ? X : 0, lane);
+        long long r = warp_rec_search_safe(q.so, q.n_seq, X0 > 0 ? X0 : 0, lane);
         if (r > q.n_seq - 1) r = q.n_seq - 1;
-        rb = r;
-        ic = 0;
-        const long long i = rb + lane;
+        R.rb = r;
+        R.ic = 0;
+        R.give_up = 0;
+        const long long i = r + lane;
         W.s[lane] = i <= q.n_seq ? __ldg(q.so + i) : q.n;
-        if (lane == 0) W.s[kWin] = rb + kWin <= q.n_seq ? __ldg(q.so + rb + kWin) : q.n;
-        nv = (q.n_seq - rb < kWin) ? (int)(q.n_seq - rb) : kWin;
+        if (lane == 0) W.s[kWin] = r + kWin <= q.n_seq ? __ldg(q.so + r + kWin) : q.n;
+        R.nv = (q.n_seq - r < kWin) ? (int)(q.n_seq - r) : kWin;
     }
     // id offsets come from the plan kernel: wait for it, then see whether it
     // rejected seq_offsets
     pdl_wait();
-    if (*(volatile const unsigned *)q.gate == q.epoch) return;
-    W.o[lane] = rb + lane < q.n_seq ? q.offsets_out[rb + lane] : 0;
-    __syncwarp();
-
-    auto win_fill = [&](long long nrb) {
-        __syncwarp();
-        const long long i = nrb + lane;
-        W.s[lane] = i <= q.n_seq ? __ldg(q.so + i) : q.n;
-        if (lane == 0) W.s[kWin] = nrb + kWin <= q.n_seq ? __ldg(q.so + nrb + kWin) : q.n;
-        W.o[lane] = i < q.n_seq ? q.offsets_out[i] : 0;
-        rb = nrb;
-        nv = (q.n_seq - nrb < kWin) ? (int)(q.n_seq - nrb) : kWin;
-        __syncwarp();
-    };
-
-    // warp-uniform state of the step to emit, which starts at X
-    long long X = s_begin * kStep - q.head_pad;
-    long long re;   // end of record ic
-    long long obJ;  // output index of the record's first k-mer starting at or after X
-    int ph;         // that k-mer's start - X (>= K only before the input's first byte)
-    {
-        const long long xc = X > 0 ? X : 0, rs = W.s[0];
-        const long long J = rec_tokens(q, xc - rs);  // ceil((xc - rs) / k)
-        ph = (int)(rs + J * K - X);
-        obJ = W.o[0] + J;
-        re = W.s[1];
+    if (*(volatile const unsigned *)q.gate == q.epoch) {
+        cp_async_wait<0>();
+        return;
     }
+    W.o[lane] = R.rb + lane < q.n_seq ? q.offsets_out[R.rb + lane] : 0;
+    __syncwarp();
+    {
+        const long long xc = X0 > 0 ? X0 : 0, rs = W.s[0];
+        const long long J = rec_tokens(q, xc - rs);  // ceil((xc - rs) / k)
+        R.ph = (int)(rs + J * K - X0);
+        R.obJ = W.o[0] + J;
+        R.re = W.s[1];
+    }
+
+    // Warp-uniform fast-path state, in 32-bit coordinates relative to X0: the
+    // step at Xr lies in one record (with 16 bytes to spare) iff Xr <= lim.
+    int Xr = 0, ph = R.ph;
+    int *obp = static_cast<int *>(q.out) + R.obJ;  // out + output index of the next k-mer
+    auto fast_lim = [&](long long re, long long X) -> int {
+        if (X < 0) return -1;  // the head pad: the slow path
+        const long long l = re - X0 - (kStep + 16);
+        return l > (1 << 30) ? (1 << 30) : (l < -1 ? -1 : (int)l);
+    };
+    int lim = fast_lim(R.re, X0);
     const int c_lane = 16 * lane + K - 1;
-    int *const out = static_cast<int *>(q.out);
+    const int m32l = -32 * lane;
 
     unsigned cw_p = 0u, nf_p = 0u;  // the previous step's codes and N flags
     bool sep = false, give_up = false;
-    for (int u0 = 0; u0 <= n_steps; u0 += kDepth) {
-#pragma unroll
-        for (int d = 0; d < kDepth; ++d) {
-            const int u = u0 + d;
-            if (u > n_steps) break;
-            const uint4 w = buf[d];
-            buf[d] = u + kDepth < u_lim ? __ldg(vp + (d + kDepth) * 32) : make_uint4(0u, 0u, 0u, 0u);
-            unsigned c0, c1, c2, c3;
-            const unsigned v0 = kv_word(w.x, c0), v1 = kv_word(w.y, c1);
-            const unsigned v2 = kv_word(w.z, c2), v3 = kv_word(w.w, c3);
-            const unsigned codes = kv_pack(c0, c1, c2, c3);
-            unsigned nf = 0u;
-            if ((v0 | v1 | v2 | v3) != 0u) {  // rare: something other than a base letter
-                nf = kv_nflags(v0, v1, v2, v3);
-                if (u < n_steps) {
-                    const unsigned low = dgather4(dlow4(w.x)) | (dgather4(dlow4(w.y)) << 4) |
-                                         (dgather4(dlow4(w.z)) << 8) | (dgather4(dlow4(w.w)) << 12);
-                    if (low & lane_mask16(16 * ((s_begin + u) * 32 + lane), lo, hi)) sep = true;
-                }
+    for (int u = 0; u <= n_steps; ++u) {
+        issue(u + kRing - 1);
+        cp_async_wait<kRing - 1>();  // step u has landed
+        const uint4 w = ring[(u & (kRing - 1)) * 32];
+        unsigned c0, c1, c2, c3;
+        const unsigned v0 = kv_word(w.x, c0), v1 = kv_word(w.y, c1);
+        const unsigned v2 = kv_word(w.z, c2), v3 = kv_word(w.w, c3);
+        const unsigned codes = kv_pack(c0, c1, c2, c3);
+        unsigned nf = 0u;
+        if ((v0 | v1 | v2 | v3) != 0u) {  // rare: something other than a base letter
+            nf = kv_nflags(v0, v1, v2, v3);
+            if ((dlow4(w.x) | dlow4(w.y) | dlow4(w.z) | dlow4(w.w)) != 0u && u < n_steps) {
+                const unsigned low = dgather4(dlow4(w.x)) | (dgather4(dlow4(w.y)) << 4) |
+                                     (dgather4(dlow4(w.z)) << 8) | (dgather4(dlow4(w.w)) << 12);
+                if (low & lane_mask16(16 * ((s_begin + u) * 32 + lane), lo, hi)) sep = true;
             }
-            if (u > 0) {
-                // emit step u - 1, whose codes are cw_p
-                const unsigned a = __shfl_down_sync(0xffffffffu, cw_p, 1);
-                const unsigned b = __shfl_sync(0xffffffffu, codes, 0);
-                const unsigned cw = cw_p, cw_nx = lane == 31 ? b : a;
-                const long long Xe = X + kStep;
-                // N flags only where the warp's step (or the next vector) has any
-                const bool anyN = __any_sync(0xffffffffu, (nf_p | (lane == 0 ? nf : 0u)) != 0u);
-                unsigned nwin = 0u;
-                if (anyN) {
-                    const unsigned na = __shfl_down_sync(0xffffffffu, nf_p, 1);
-                    const unsigned nb = __shfl_sync(0xffffffffu, nf, 0);
-                    nwin = nf_p | ((lane == 31 ? nb : na) << 16);
-                }
-                if (re >= Xe + 16 && X >= 0) {
-                    // the whole step (and 16 bytes past it) lies in one record
-                    const unsigned qd = div_k((unsigned)(c_lane - ph));
-                    const int o0 = ph + (int)qd * K - 16 * lane;  // first start, in [0, K)
-                    int *dst = out + (obJ + qd);
-#pragma unroll
-                    for (int t = 0; t < SLOTS; ++t) {
-                        const int o = o0 + t * K;
-                        if (t >= SURE && o >= 16) break;
-                        unsigned id = __umulhi(__funnelshift_l(cw_nx, cw, 2 * o), 1u << (2 * K));
-                        if (anyN && ((nwin >> o) & KMASK)) id = UNK;
-                        dst[t] = (int)id;
-                    }
-                    const unsigned qn = div_k((unsigned)(kStep - ph + K - 1));
-                    ph += (int)qn * K - kStep;
-                    obJ += qn;
-                } else {
-                    // record boundaries, a tail or the input's edges in this step
-                    if (!(rb + nv >= q.n_seq || W.s[nv] >= Xe)) {
-                        if (ic > 0) {
-                            win_fill(rb + ic);
-                            ic = 0;
-                        }
-                        if (!(rb + nv >= q.n_seq || W.s[nv] >= Xe)) {
-                            give_up = true;  // > kWin records in 512 bytes: the general path
-                            break;
-                        }
-                    }
-                    auto kmer_at = [&](int o) -> unsigned {  // k-mer starting at byte o of the vector
-                        const unsigned id = __funnelshift_l(cw_nx, cw, 2 * o) >> (32 - 2 * K);
-                        return ((nwin >> o) & KMASK) ? UNK : id;
-                    };
-                    const int x0r = 16 * lane;
-                    int i = ic;
-                    while (i + 1 < nv && W.s[i + 1] <= X + x0r) ++i;
-                    int p, rer;
-                    long long ob;
-                    if (i == ic) {
-                        const int qd = x0r > ph ? (int)div_k((unsigned)(x0r - ph + K - 1)) : 0;
-                        p = ph + qd * K;
-                        ob = obJ + qd;
-                    } else {
-                        const int rs = (int)(W.s[i] - X);
-                        const int qd = x0r > rs ? (int)div_k((unsigned)(x0r - rs + K - 1)) : 0;
-                        p = rs + qd * K;
-                        ob = W.o[i] + qd;
-                    }
-                    {
-                        const long long e = W.s[i + 1] - X;
-                        rer = e >= (1 << 30) ? (1 << 30) : (int)e;
-                    }
-                    while (true) {
-                        const int lim = rer < x0r + 16 ? rer : x0r + 16;
-                        int *dst = out + ob;
-                        for (int t = 0; p < lim; p += K, ++t) {
-                            const unsigned id = kmer_at(p - x0r);
-                            dst[t] = (int)(p + K > rer ? UNK : id);
-                        }
-                        if (rer >= x0r + 16 || i + 1 >= nv) break;
-                        ++i;  // the next record starts inside this vector
-                        p = rer;
-                        ob = W.o[i];
-                        const long long e = W.s[i + 1] - X;
-                        rer = e >= (1 << 30) ? (1 << 30) : (int)e;
-                    }
-                    if (u < n_steps) {
-                        // the record state for the next step, which starts at Xe
-                        int j = ic;
-                        bool moved = false;
-                        while (true) {
-                            while (j + 1 < nv && W.s[j + 1] <= Xe) ++j;
-                            if (j + 1 == nv && rb + nv < q.n_seq && W.s[nv] <= Xe) {
-                                win_fill(rb + nv);  // slide past the window
-                                j = 0;
-                                moved = true;
-                                continue;
-                            }
-                            break;
-                        }
-                        if (j == ic && !moved) {
-                            // same record: its next k-mer start at or after Xe
-                            const int dd = (int)(X + ph - Xe);  // start - Xe, > -kStep
-                            if (dd < 0) {
-                                const unsigned qn = div_k((unsigned)(-dd + K - 1));
-                                ph = dd + (int)qn * K;
-                                obJ += qn;
-                            } else {
-                                ph = dd;
-                            }
-                        } else {  // a record that starts in (X, Xe]
-                            ic = j;
-                            const unsigned qn = div_k((unsigned)(Xe - W.s[j]) + K - 1);
-                            ph = (int)(W.s[j] + (long long)qn * K - Xe);
-                            obJ = W.o[j] + qn;
-                        }
-                        re = W.s[ic + 1];
-                    }
-                }
-                X = Xe;
-            }
-            cw_p = codes;
-            nf_p = nf;
         }
-        if (give_up) break;
-        vp += kDepth * 32;  // vp points at step u0 of the next round
+        if (u > 0) {
+            // emit step u - 1, whose codes are cw_p
+            const unsigned a = __shfl_down_sync(0xffffffffu, cw_p, 1);
+            const unsigned b = __shfl_sync(0xffffffffu, codes, 0);
+            const unsigned cw = cw_p, cw_nx = lane == 31 ? b : a;
+            const bool anyN = __any_sync(0xffffffffu, (nf_p | (lane == 0 ? nf : 0u)) != 0u);
+            unsigned nwin = 0u;
+            if (anyN) {
+                const unsigned na = __shfl_down_sync(0xffffffffu, nf_p, 1);
+                const unsigned nb = __shfl_sync(0xffffffffu, nf, 0);
+                nwin = nf_p | ((lane == 31 ? nb : na) << 16);
+            }
+            if (Xr <= lim) {
+                // the whole step lies in one record: k-mers at offsets
+                // o0, o0 + K, ... of this lane's vector, o0 in [0, K)
+                const unsigned qd = C::div((unsigned)(c_lane - ph));
+                const int a0 = 2 * ph + m32l + (int)qd * (2 * K);  // 2 * o0
+                unsigned id[C::SLOTS];
+#pragma unroll
+                for (int t0 = 0; t0 < C::SLOTS; t0 += C::PERW) {
+                    const unsigned fw = __funnelshift_l(cw_nx, cw, a0 + t0 * 2 * K);
+#pragma unroll
+                    for (int t = t0; t < t0 + C::PERW && t < C::SLOTS; ++t)
+                        id[t] = __umulhi(fw << ((t - t0) * 2 * K), 1u << (2 * K));
+                }
+                if (anyN) {
+#pragma unroll
+                    for (int t = 0; t < C::SLOTS; ++t)
+                        if ((nwin >> ((a0 >> 1) + t * K)) & C::KMASK) id[t] = C::UNK;
+                }
+                int *dst = obp + qd;
+#pragma unroll
+                for (int t = 0; t < C::SLOTS; ++t)
+                    if (t < C::SURE || a0 + t * 2 * K < 32) dst[t] = (int)id[t];
+                const unsigned qn = C::div((unsigned)(kStep + K - 1 - ph));
+                ph += (int)qn * K - kStep;
+                obp += qn;
+            } else {
+                R.ph = ph;
+                R.obJ = obp - static_cast<int *>(q.out);
+                R = slow_step<K>(R, W, q, X0 + Xr, cw, cw_nx, nwin, u < n_steps);
+                if (R.give_up) {
+                    give_up = true;
+                    lim = -(1 << 30);  // every later step: slow_step, which returns at once
+                } else {
+                    ph = R.ph;
+                    obp = static_cast<int *>(q.out) + R.obJ;
+                    lim = fast_lim(R.re, X0 + Xr + kStep);
+                }
+            }
+            Xr += kStep;
+        }
+        cw_p = codes;
+        nf_p = nf;
     }
+    cp_async_wait<0>();
     if (give_up) {
         if (lane == 0) raise_gate(q);
         return;
