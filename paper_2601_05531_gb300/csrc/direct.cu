@@ -25,7 +25,8 @@ namespace dnatok {
 namespace {
 
 constexpr int kDThreads = 256;
-constexpr int kPlanThreads = 1024;
+constexpr int kPlanThreads = 256;
+constexpr int kPlanTile = 2048;  // records per pass of the plan kernel
 
 struct DirectParams {
     const uint8_t *base;       // bytes rounded down to 16
@@ -54,54 +55,67 @@ __device__ __forceinline__ void raise_gate(const DirectParams &q) {
 }
 
 // id offsets from the record lengths; any malformed offset sends the encode
-// to the general path (which reports it).
+// to the general path (which reports it).  One small block (it shares an SM
+// with the direct kernel's CTAs, which start while it runs): passes of
+// kPlanTile records, each loaded and stored coalesced through shared memory.
 __global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams q) {
+    constexpr int kPer = kPlanTile / kPlanThreads;
+    __shared__ long long s_v[kPlanTile + 1];
     __shared__ long long wsum[kPlanThreads / 32];
-    pdl_launch_dependents();  // the direct kernel may start loading its tiles now
+    pdl_launch_dependents();  // the direct kernel may start loading its input now
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = q.n_seq;
-    const long long per = (n + kPlanThreads - 1) / kPlanThreads;
-    const long long r0 = tid * per, r1 = (r0 + per < n) ? r0 + per : n;
-    long long sum = 0;
     bool bad = false;
-    constexpr int kBatch = 8;  // offsets loaded together, then used
-    for (long long rb = r0; rb < r1; rb += kBatch) {
-        long long v[kBatch + 1];
+    long long carry = 0;  // tokens of the records before this pass
+    for (long long r0 = 0; r0 < n; r0 += kPlanTile) {
+        const int cnt = (n - r0 < kPlanTile) ? (int)(n - r0) : kPlanTile;
+        for (int i = tid; i <= cnt; i += kPlanThreads) s_v[i] = __ldg(q.so + r0 + i);
+        __syncthreads();
+        long long t[kPer], sum = 0;
 #pragma unroll
-        for (int i = 0; i <= kBatch; ++i) v[i] = (rb + i <= r1) ? q.so[rb + i] : 0;
-#pragma unroll
-        for (int i = 0; i < kBatch; ++i) {
-            if (rb + i >= r1) break;
-            if (v[i + 1] < v[i]) bad = true;
-            sum += rec_tokens(q, v[i + 1] - v[i]);
+        for (int j = 0; j < kPer; ++j) {
+            const int i = tid * kPer + j;
+            t[j] = 0;
+            if (i < cnt) {
+                const long long L = s_v[i + 1] - s_v[i];
+                if (L < 0) bad = true;
+                t[j] = rec_tokens(q, L);
+                sum += t[j];
+            }
         }
+        long long x = sum;  // inclusive scan over the block
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();  // every s_v read above is done, wsum is complete
+        long long pre = carry, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kPlanThreads / 32; ++w) {
+            if (w < warp) pre += wsum[w];
+            tot += wsum[w];
+        }
+        long long run = pre + x - sum;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            s_v[tid * kPer + j] = run;
+            run += t[j];
+        }
+        __syncthreads();
+        for (int i = tid; i < cnt; i += kPlanThreads) q.offsets_out[r0 + i] = s_v[i];
+        carry += tot;
+        __syncthreads();  // s_v and wsum are reused by the next pass
     }
-    if (tid == 0 && (q.so[0] != 0 || q.so[n] != q.n)) bad = true;
+    if (tid == 0 && (__ldg(q.so) != 0 || __ldg(q.so + n) != q.n)) bad = true;
     if (__syncthreads_or(bad)) {
         if (tid == 0) raise_gate(q);
         return;
     }
-    long long x = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    long long pre = 0, total = 0;
-    for (int w = 0; w < kPlanThreads / 32; ++w) {
-        if (w < warp) pre += wsum[w];
-        total += wsum[w];
-    }
-    long long run = pre + x - sum;
-    for (long long r = r0; r < r1; ++r) {
-        q.offsets_out[r] = run;
-        run += rec_tokens(q, q.so[r + 1] - q.so[r]);
-    }
     if (tid == 0) {
-        q.offsets_out[n] = total;
+        q.offsets_out[n] = carry;
         if (q.totals_out) {
-            q.totals_out[0] = total;
+            q.totals_out[0] = carry;
             q.totals_out[1] = n;
         }
     }
@@ -286,6 +300,8 @@ struct KC {
     static constexpr int SLOTS = (16 + K - 1) / K;  // k-mer starts per vector, at most
     static constexpr int SURE = 16 / K;             // slots present whatever the phase
     static constexpr int PERW = 16 / K;             // k-mers per 16-base funnel window
+    static constexpr int D = kStep % K;             // phase shift of a lane's next vector
+    static constexpr int Q = kStep / K;             // k-mers it is ahead, less one on a wrap
     __device__ static __forceinline__ unsigned div(unsigned x) { return __umulhi(x, M32); }  // x < 2^17
 };
 
@@ -415,39 +431,74 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-constexpr int kRing = 8;  // warp steps in flight: a ring of 8 x 512 bytes per warp
+constexpr int kRing = 4;  // warp steps in flight: a ring of 4 x 1 KiB per warp
+constexpr int kV = 2;     // 512-byte slots per warp step (one vector per lane each)
+
+// Classification of one 16-byte vector: packed codes and N flags.
+struct KSlot {
+    unsigned codes, nf;
+};
+__device__ __forceinline__ KSlot k_classify(const uint4 &w, bool real, long long ab, long long lo,
+                                            long long hi, bool &sep) {
+    unsigned c0, c1, c2, c3;
+    const unsigned v0 = kv_word(w.x, c0), v1 = kv_word(w.y, c1);
+    const unsigned v2 = kv_word(w.z, c2), v3 = kv_word(w.w, c3);
+    KSlot r;
+    r.codes = kv_pack(c0, c1, c2, c3);
+    r.nf = 0u;
+    if ((v0 | v1 | v2 | v3) != 0u) {  // rare: something other than a base letter
+        r.nf = kv_nflags(v0, v1, v2, v3);
+        if ((dlow4(w.x) | dlow4(w.y) | dlow4(w.z) | dlow4(w.w)) != 0u && real) {
+            const unsigned low = dgather4(dlow4(w.x)) | (dgather4(dlow4(w.y)) << 4) |
+                                 (dgather4(dlow4(w.z)) << 8) | (dgather4(dlow4(w.w)) << 12);
+            if (low & lane_mask16(ab, lo, hi)) sep = true;
+        }
+    }
+    return r;
+}
 
 template <int K>
 __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams q) {
     static_assert(K >= 2 && K <= 15, "k-mer length");
     using C = KC<K>;
+    constexpr int kSpan = kV * kStep;  // bytes per warp step
     __shared__ RecWin wins[kSWarps];
-    __shared__ uint4 ring_s[kSWarps][kRing][32];
+    __shared__ uint4 ring_s[kSWarps][kRing][kV][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RecWin &W = wins[warp];
-    uint4 *const ring = &ring_s[warp][0][lane];  // this lane's slot of stage 0
+    uint4 *const ring = &ring_s[warp][0][0][lane];  // this lane's slot 0 of stage 0
     const long long lo = q.head_pad, hi = q.head_pad + q.n;  // valid aligned range
-    const long long S = (hi + kStep - 1) / kStep;
+    const long long S = (hi + kSpan - 1) / kSpan;
     const long long nw = (long long)gridDim.x * kSWarps;
     const long long gw = (long long)blockIdx.x * kSWarps + warp;
     const long long s_begin = gw * S / nw, s_end = (gw + 1) * S / nw;
     if (s_begin >= s_end) return;
     const int n_steps = (int)(s_end - s_begin);
 
-    // This lane's vectors: step u (relative to s_begin) holds vector
-    // (s_begin + u) * 32 + lane; step n_steps is the halo (lane 0 only).
-    const uint4 *const vp = reinterpret_cast<const uint4 *>(q.base) + s_begin * 32 + lane;
-    int u_lim;  // steps u < u_lim are read by this lane
-    {
+    // This lane's vectors: step u (relative to s_begin), slot v holds vector
+    // (s_begin + u) * 64 + v * 32 + lane; step n_steps is the halo (its slot
+    // 0, lane 0 only).
+    const uint4 *const vp = reinterpret_cast<const uint4 *>(q.base) + s_begin * (kV * 32) + lane;
+    int u_lim[kV];  // steps u < u_lim[v] are read by this lane in slot v
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
         const long long nvec = (hi + 15) / 16;  // vectors holding input bytes
-        const long long mine = nvec - (s_begin * 32 + lane);
-        const long long by_data = mine <= 0 ? 0 : (mine + 31) / 32;
-        const long long by_range = lane == 0 ? n_steps + 1 : n_steps;
-        u_lim = (int)(by_data < by_range ? by_data : by_range);
+        const long long mine = nvec - (s_begin * (kV * 32) + v * 32 + lane);
+        const long long by_data = mine <= 0 ? 0 : (mine + kV * 32 - 1) / (kV * 32);
+        const long long by_range = (v == 0 && lane == 0) ? n_steps + 1 : n_steps;
+        u_lim[v] = (int)(by_data < by_range ? by_data : by_range);
     }
+    const unsigned ring_sa = (unsigned)__cvta_generic_to_shared(ring);
     auto issue = [&](int u) {  // copy step u into its ring stage
-        const bool full = u < u_lim;
-        cp_async16(ring + (u & (kRing - 1)) * 32, full ? vp + u * 32 : vp, full);
+        const unsigned sa = ring_sa + (unsigned)(u & (kRing - 1)) * (kV * 32 * 16);
+        const uint4 *src = vp + (long long)u * (kV * 32);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            // nothing is read when the size is zero (the slot is zero-filled)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa + v * 32 * 16),
+                         "l"(src + v * 32), "r"(u < u_lim[v] ? 16 : 0)
+                         : "memory");
+        }
         cp_async_commit();
     };
 #pragma unroll
@@ -455,7 +506,7 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
 
     // The record holding the first step: seq_offsets is input, so this runs
     // while the plan kernel (a programmatic predecessor) is still working.
-    const long long X0 = s_begin * kStep - q.head_pad;
+    const long long X0 = s_begin * kSpan - q.head_pad;
     RecState R;
     {
         long long r = warp_rec_search_safe(q.so, q.n_seq, X0 > 0 ? X0 : 0, lane);
@@ -491,86 +542,123 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
     int *obp = static_cast<int *>(q.out) + R.obJ;  // out + output index of the next k-mer
     auto fast_lim = [&](long long re, long long X) -> int {
         if (X < 0) return -1;  // the head pad: the slow path
-        const long long l = re - X0 - (kStep + 16);
+        const long long l = re - X0 - (kSpan + 16);
         return l > (1 << 30) ? (1 << 30) : (l < -1 ? -1 : (int)l);
     };
     int lim = fast_lim(R.re, X0);
     const int c_lane = 16 * lane + K - 1;
     const int m32l = -32 * lane;
 
-    unsigned cw_p = 0u, nf_p = 0u;  // the previous step's codes and N flags
+    // Per-lane fast-path state: a2 = 2 x the offset in the lane's vector of
+    // its first k-mer start (in [0, 2K)), dp = that k-mer's output slot.
+    // Rebuilt from the warp-uniform (ph, obp) of a slot starting at X; lane
+    // 0's state is (2 ph, obp) again, which is how the slow path reads it.
+    int a2;
+    int *dp;
+    auto lane_state = [&]() {
+        const unsigned qd = C::div((unsigned)(c_lane - ph));
+        a2 = 2 * ph + m32l + (int)qd * (2 * K);
+        dp = obp + qd;
+    };
+    lane_state();
+    bool synced = true;  // (ph, obp) hold the state of the next step (else lane 0 does)
+    // k-mers of this lane's vector in a 512-byte slot inside a record; the
+    // state then moves to the lane's vector of the next slot (512 bytes on)
+    auto emit_fast = [&](unsigned cw, unsigned cw_nx, unsigned nwin, bool anyN) {
+        unsigned id[C::SLOTS];
+#pragma unroll
+        for (int t0 = 0; t0 < C::SLOTS; t0 += C::PERW) {
+            const unsigned fw = __funnelshift_l(cw_nx, cw, a2 + t0 * 2 * K);
+#pragma unroll
+            for (int t = t0; t < t0 + C::PERW && t < C::SLOTS; ++t)
+                id[t] = __umulhi(fw << ((t - t0) * 2 * K), 1u << (2 * K));
+        }
+        if (anyN) {
+#pragma unroll
+            for (int t = 0; t < C::SLOTS; ++t)
+                if ((nwin >> ((a2 >> 1) + t * K)) & C::KMASK) id[t] = C::UNK;
+        }
+#pragma unroll
+        for (int t = 0; t < C::SLOTS; ++t)
+            if (t < C::SURE || a2 + t * 2 * K < 32) dp[t] = (int)id[t];
+        if (C::D == 0) {
+            dp += C::Q;
+        } else {
+            const bool wrap = a2 < 2 * C::D;
+            a2 += wrap ? 2 * (K - C::D) : -2 * C::D;
+            dp += C::Q + (wrap ? 1 : 0);
+        }
+    };
+
+    KSlot p[kV] = {};  // the previous step's slots
     bool sep = false, give_up = false;
     for (int u = 0; u <= n_steps; ++u) {
         issue(u + kRing - 1);
         cp_async_wait<kRing - 1>();  // step u has landed
-        const uint4 w = ring[(u & (kRing - 1)) * 32];
-        unsigned c0, c1, c2, c3;
-        const unsigned v0 = kv_word(w.x, c0), v1 = kv_word(w.y, c1);
-        const unsigned v2 = kv_word(w.z, c2), v3 = kv_word(w.w, c3);
-        const unsigned codes = kv_pack(c0, c1, c2, c3);
-        unsigned nf = 0u;
-        if ((v0 | v1 | v2 | v3) != 0u) {  // rare: something other than a base letter
-            nf = kv_nflags(v0, v1, v2, v3);
-            if ((dlow4(w.x) | dlow4(w.y) | dlow4(w.z) | dlow4(w.w)) != 0u && u < n_steps) {
-                const unsigned low = dgather4(dlow4(w.x)) | (dgather4(dlow4(w.y)) << 4) |
-                                     (dgather4(dlow4(w.z)) << 8) | (dgather4(dlow4(w.w)) << 12);
-                if (low & lane_mask16(16 * ((s_begin + u) * 32 + lane), lo, hi)) sep = true;
-            }
+        const uint4 *st = ring + (u & (kRing - 1)) * (kV * 32);
+        KSlot c[kV];
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const long long ab = 16 * ((s_begin + u) * (kV * 32) + v * 32 + lane);
+            c[v] = (v == 0 || u < n_steps) ? k_classify(st[v * 32], u < n_steps, ab, lo, hi, sep)
+                                           : KSlot{0u, 0u};
         }
         if (u > 0) {
-            // emit step u - 1, whose codes are cw_p
-            const unsigned a = __shfl_down_sync(0xffffffffu, cw_p, 1);
-            const unsigned b = __shfl_sync(0xffffffffu, codes, 0);
-            const unsigned cw = cw_p, cw_nx = lane == 31 ? b : a;
-            const bool anyN = __any_sync(0xffffffffu, (nf_p | (lane == 0 ? nf : 0u)) != 0u);
-            unsigned nwin = 0u;
-            if (anyN) {
-                const unsigned na = __shfl_down_sync(0xffffffffu, nf_p, 1);
-                const unsigned nb = __shfl_sync(0xffffffffu, nf, 0);
-                nwin = nf_p | ((lane == 31 ? nb : na) << 16);
+            // emit step u - 1 (slots p[]); a slot's lane 31 takes the next
+            // slot's lane 0
+            unsigned nx[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const unsigned a = __shfl_down_sync(0xffffffffu, p[v].codes, 1);
+                const unsigned b = __shfl_sync(0xffffffffu, v + 1 < kV ? p[v + 1].codes : c[0].codes, 0);
+                nx[v] = lane == 31 ? b : a;
+            }
+            unsigned any = lane == 0 ? c[0].nf : 0u;
+#pragma unroll
+            for (int v = 0; v < kV; ++v) any |= p[v].nf;
+            const bool anyN = __any_sync(0xffffffffu, any != 0u);
+            unsigned nwin[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                nwin[v] = 0u;
+                if (anyN) {
+                    const unsigned a = __shfl_down_sync(0xffffffffu, p[v].nf, 1);
+                    const unsigned b = __shfl_sync(0xffffffffu, v + 1 < kV ? p[v + 1].nf : c[0].nf, 0);
+                    nwin[v] = p[v].nf | ((lane == 31 ? b : a) << 16);
+                }
             }
             if (Xr <= lim) {
-                // the whole step lies in one record: k-mers at offsets
-                // o0, o0 + K, ... of this lane's vector, o0 in [0, K)
-                const unsigned qd = C::div((unsigned)(c_lane - ph));
-                const int a0 = 2 * ph + m32l + (int)qd * (2 * K);  // 2 * o0
-                unsigned id[C::SLOTS];
 #pragma unroll
-                for (int t0 = 0; t0 < C::SLOTS; t0 += C::PERW) {
-                    const unsigned fw = __funnelshift_l(cw_nx, cw, a0 + t0 * 2 * K);
-#pragma unroll
-                    for (int t = t0; t < t0 + C::PERW && t < C::SLOTS; ++t)
-                        id[t] = __umulhi(fw << ((t - t0) * 2 * K), 1u << (2 * K));
-                }
-                if (anyN) {
-#pragma unroll
-                    for (int t = 0; t < C::SLOTS; ++t)
-                        if ((nwin >> ((a0 >> 1) + t * K)) & C::KMASK) id[t] = C::UNK;
-                }
-                int *dst = obp + qd;
-#pragma unroll
-                for (int t = 0; t < C::SLOTS; ++t)
-                    if (t < C::SURE || a0 + t * 2 * K < 32) dst[t] = (int)id[t];
-                const unsigned qn = C::div((unsigned)(kStep + K - 1 - ph));
-                ph += (int)qn * K - kStep;
-                obp += qn;
+                for (int v = 0; v < kV; ++v) emit_fast(p[v].codes, nx[v], nwin[v], anyN);
+                synced = false;
             } else {
-                R.ph = ph;
-                R.obJ = obp - static_cast<int *>(q.out);
-                R = slow_step<K>(R, W, q, X0 + Xr, cw, cw_nx, nwin, u < n_steps);
+                if (!synced) {  // the fast steps left the state in the lanes
+                    ph = __shfl_sync(0xffffffffu, a2, 0) >> 1;
+                    obp = reinterpret_cast<int *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dp), 0));
+                    synced = true;
+                }
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    R.ph = ph;
+                    R.obJ = obp - static_cast<int *>(q.out);
+                    R = slow_step<K>(R, W, q, X0 + Xr + v * kStep, p[v].codes, nx[v], nwin[v],
+                                     v + 1 < kV || u < n_steps);
+                    ph = R.ph;
+                    obp = static_cast<int *>(q.out) + R.obJ;
+                }
                 if (R.give_up) {
                     give_up = true;
                     lim = -(1 << 30);  // every later step: slow_step, which returns at once
                 } else {
-                    ph = R.ph;
-                    obp = static_cast<int *>(q.out) + R.obJ;
-                    lim = fast_lim(R.re, X0 + Xr + kStep);
+                    lim = fast_lim(R.re, X0 + Xr + kSpan);
+                    lane_state();
                 }
             }
-            Xr += kStep;
+            Xr += kSpan;
         }
-        cw_p = codes;
-        nf_p = nf;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) p[v] = c[v];
     }
     cp_async_wait<0>();
     if (give_up) {
@@ -709,7 +797,7 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                     o = 1;
                 occ = o;
             }
-            const long long steps = (q.head_pad + n + kStep - 1) / kStep;
+            const long long steps = (q.head_pad + n + kV * kStep - 1) / (kV * kStep);
             long long grid = (long long)sm_count * occ;
             const long long need = (steps + kSWarps - 1) / kSWarps;
             if (grid > need) grid = need;
