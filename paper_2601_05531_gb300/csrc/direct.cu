@@ -371,19 +371,47 @@ __device__ __forceinline__ RecState slow_step(RecState R, RecWin &W, const Direc
         const long long e = W.s[i + 1] - X;
         rer = e >= (1 << 30) ? (1 << 30) : (int)e;
     }
-    while (true) {
-        const int lim = rer < x0r + 16 ? rer : x0r + 16;
-        int *dst = out + ob;
-        for (int t = 0; p < lim; p += K, ++t) {
-            const unsigned id = kmer_at(p - x0r);
-            dst[t] = (int)(p + K > rer ? C::UNK : id);
+    {
+        // the lane's record: k-mers at offsets o, o + K, ... below lim, the
+        // same funnel windows as the fast path, tails to UNK
+        const int o = p - x0r;  // >= 0
+        const int lim = rer - x0r < 16 ? rer - x0r : 16;
+        const int tail = rer - x0r - K;  // a k-mer at offset > tail runs past the record
+        unsigned id[C::SLOTS];
+#pragma unroll
+        for (int t0 = 0; t0 < C::SLOTS; t0 += C::PERW) {
+            const unsigned fw = __funnelshift_l(cw_nx, cw, 2 * (o + t0 * K));
+#pragma unroll
+            for (int t = t0; t < t0 + C::PERW && t < C::SLOTS; ++t)
+                id[t] = __umulhi(fw << ((t - t0) * 2 * K), 1u << (2 * K));
         }
-        if (rer >= x0r + 16 || i + 1 >= R.nv) break;
-        ++i;  // the next record starts inside this vector
-        p = rer;
-        ob = W.o[i];
-        const long long e = W.s[i + 1] - X;
-        rer = e >= (1 << 30) ? (1 << 30) : (int)e;
+        int *dst = out + ob;
+#pragma unroll
+        for (int t = 0; t < C::SLOTS; ++t) {
+            const int ot = o + t * K;
+            if (ot < lim) {
+                unsigned v = id[t];
+                if (ot > tail || ((nwin >> ot) & C::KMASK)) v = C::UNK;
+                dst[t] = (int)v;
+            }
+        }
+    }
+    if (rer < x0r + 16 && i + 1 < R.nv) {
+        // rare: further records start inside this vector
+        while (true) {
+            ++i;
+            p = rer;
+            ob = W.o[i];
+            const long long e = W.s[i + 1] - X;
+            rer = e >= (1 << 30) ? (1 << 30) : (int)e;
+            const int lim = rer < x0r + 16 ? rer : x0r + 16;
+            int *dst = out + ob;
+            for (int t = 0; p < lim; p += K, ++t) {
+                const unsigned id = kmer_at(p - x0r);
+                dst[t] = (int)(p + K > rer ? C::UNK : id);
+            }
+            if (rer >= x0r + 16 || i + 1 >= R.nv) break;
+        }
     }
     if (!advance) return R;
     // the record state for the next step, which starts at Xe
