@@ -565,12 +565,13 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
     }
 
     // Warp-uniform fast-path state, in 32-bit coordinates relative to X0: the
-    // step at Xr lies in one record (with 16 bytes to spare) iff Xr <= lim.
+    // 512-byte slot at Xr lies in one record (with 16 bytes to spare) iff
+    // Xr <= lim.
     int Xr = 0, ph = R.ph;
     int *obp = static_cast<int *>(q.out) + R.obJ;  // out + output index of the next k-mer
     auto fast_lim = [&](long long re, long long X) -> int {
         if (X < 0) return -1;  // the head pad: the slow path
-        const long long l = re - X0 - (kSpan + 16);
+        const long long l = re - X0 - (kStep + 16);
         return l > (1 << 30) ? (1 << 30) : (l < -1 ? -1 : (int)l);
     };
     int lim = fast_lim(R.re, X0);
@@ -655,35 +656,35 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
                     nwin[v] = p[v].nf | ((lane == 31 ? b : a) << 16);
                 }
             }
-            if (Xr <= lim) {
 #pragma unroll
-                for (int v = 0; v < kV; ++v) emit_fast(p[v].codes, nx[v], nwin[v], anyN);
-                synced = false;
-            } else {
-                if (!synced) {  // the fast steps left the state in the lanes
-                    ph = __shfl_sync(0xffffffffu, a2, 0) >> 1;
-                    obp = reinterpret_cast<int *>(
-                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dp), 0));
-                    synced = true;
-                }
-#pragma unroll
-                for (int v = 0; v < kV; ++v) {
+            for (int v = 0; v < kV; ++v) {
+                if (Xr <= lim) {
+                    emit_fast(p[v].codes, nx[v], nwin[v], anyN);
+                    synced = false;
+                } else {
+                    // record boundaries, a tail or the input's edge in this slot
+                    if (!synced) {  // the fast slots left the state in the lanes
+                        ph = __shfl_sync(0xffffffffu, a2, 0) >> 1;
+                        obp = reinterpret_cast<int *>(
+                            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dp), 0));
+                    }
                     R.ph = ph;
                     R.obJ = obp - static_cast<int *>(q.out);
-                    R = slow_step<K>(R, W, q, X0 + Xr + v * kStep, p[v].codes, nx[v], nwin[v],
+                    R = slow_step<K>(R, W, q, X0 + Xr, p[v].codes, nx[v], nwin[v],
                                      v + 1 < kV || u < n_steps);
                     ph = R.ph;
                     obp = static_cast<int *>(q.out) + R.obJ;
+                    synced = true;
+                    if (R.give_up) {
+                        give_up = true;
+                        lim = -(1 << 30);  // every later slot: slow_step, which returns at once
+                    } else {
+                        lim = fast_lim(R.re, X0 + Xr + kStep);
+                        lane_state();
+                    }
                 }
-                if (R.give_up) {
-                    give_up = true;
-                    lim = -(1 << 30);  // every later step: slow_step, which returns at once
-                } else {
-                    lim = fast_lim(R.re, X0 + Xr + kSpan);
-                    lane_state();
-                }
+                Xr += kStep;
             }
-            Xr += kSpan;
         }
 #pragma unroll
         for (int v = 0; v < kV; ++v) p[v] = c[v];
