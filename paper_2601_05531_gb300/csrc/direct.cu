@@ -702,12 +702,25 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
 template <int MODE>
 __global__ void __launch_bounds__(kDThreads) direct_byte_kernel(DirectParams q) {
     __shared__ int lut_s[256];
-    __shared__ int s_stop;
     const int tid = threadIdx.x;
-    pdl_wait();
-    if (tid == 0) s_stop = (*(volatile const unsigned *)q.gate == q.epoch) ? 1 : 0;
-    __syncthreads();
-    if (s_stop) return;
+    // one output per byte: the id offsets are seq_offsets itself, so this
+    // kernel needs no plan -- it copies and validates them on the way (a
+    // malformed list raises the flag; the general kernel then reports it)
+    {
+        bool bad = false;
+        for (long long r = blockIdx.x * (long long)kDThreads + tid; r <= q.n_seq;
+             r += (long long)gridDim.x * kDThreads) {
+            const long long v = __ldg(q.so + r);
+            q.offsets_out[r] = v;
+            if (r < q.n_seq && __ldg(q.so + r + 1) < v) bad = true;
+            if ((r == 0 && v != 0) || (r == q.n_seq && v != q.n)) bad = true;
+        }
+        if (bad) raise_gate(q);
+        if (blockIdx.x == 0 && tid == 0 && q.totals_out) {
+            q.totals_out[0] = q.n;
+            q.totals_out[1] = q.n_seq;
+        }
+    }
     if (MODE == MODE_CHAR) {
         for (int i = tid; i < 256; i += kDThreads) lut_s[i] = q.lut[i];
         __syncthreads();
@@ -805,6 +818,22 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
     q.kinv = k > 1 ? ~0ull / (unsigned long long)k + 1ull : 0ull;
     q.lut = lut;
     q.n_tiles = 0;
+    const bool kmer = mode == MODE_KMER && k >= 2;
+    if (!kmer) {
+        // single-nucleotide ids, symbols, and 1-mers (the default table maps
+        // A/C/G/T to 0..3 and every other kept byte to 4 = UNK): one kernel,
+        // no plan
+        long long g2 = ((q.head_pad + n + 15) / 16 + kDThreads - 1) / kDThreads;
+        const long long g3 = (n_seq + 1 + kDThreads - 1) / kDThreads;
+        if (g2 < g3) g2 = g3;
+        if (g2 > (long long)sm_count * 8) g2 = (long long)sm_count * 8;
+        if (g2 < 1) g2 = 1;
+        if (mode != MODE_SYM)
+            direct_byte_kernel<MODE_CHAR><<<(unsigned)g2, kDThreads, 0, s>>>(q);
+        else
+            direct_byte_kernel<MODE_SYM><<<(unsigned)g2, kDThreads, 0, s>>>(q);
+        return cudaGetLastError();
+    }
     direct_plan_kernel<<<1, kPlanThreads, 0, s>>>(q);
     if (n > 0) {
         // programmatic dependent launch: it starts while the plan runs
@@ -816,7 +845,7 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
         attr.val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
-        if (mode == MODE_KMER && k >= 2) {
+        {
             // one wave of resident CTAs, every warp with at least one step
             static int occ = 0;
             if (occ == 0) {
@@ -834,13 +863,6 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
             cfg.gridDim = dim3((unsigned)grid);
             return launch_kmer_k(k, cfg, q);
         }
-        // single-nucleotide ids, symbols, and 1-mers (the default table maps
-        // A/C/G/T to 0..3 and every other kept byte to 4 = UNK)
-        long long g2 = ((q.head_pad + n + 15) / 16 + kDThreads - 1) / kDThreads;
-        if (g2 > (long long)sm_count * 8) g2 = (long long)sm_count * 8;
-        cfg.gridDim = dim3((unsigned)g2);
-        if (mode != MODE_SYM) return cudaLaunchKernelEx(&cfg, direct_byte_kernel<MODE_CHAR>, q);
-        return cudaLaunchKernelEx(&cfg, direct_byte_kernel<MODE_SYM>, q);
     }
     return cudaGetLastError();
 }
