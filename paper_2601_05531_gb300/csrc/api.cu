@@ -133,22 +133,22 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
         unsigned ep = 0;
         st = next_epoch(h, s, &ep);
         if (st != DNATOK_OK) return st;
-        if (capturing) {  // replays must not see an earlier replay's switch
-            e = cudaMemsetAsync(h->d_gate, 0, sizeof(unsigned), s);
-            if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(gate)");
-        }
+        // under stream capture the epochs are baked into the graph: a replay
+        // whose general kernel ran clears the switch and its descriptors at
+        // its end (clear_gate), so the next replay starts clean
         e = launch_direct(mode, bytes, n_bytes, seq_offsets, n_bnd - 1, out, offsets_out,
                           totals_out, h->d_gate, ep, k, h->d_lut, h->sm_count, s);
         if (e != cudaSuccess) return fail_cuda(h, e, "direct kernel launch");
         p.gate = h->d_gate;
         p.gate_epoch = ep;
+        if (capturing) p.clear_gate = h->d_gate;
     }
     st = next_epoch(h, s, &p.epoch);
     if (st != DNATOK_OK) return st;
     {
         // Under stream capture the epoch is baked into the graph and every
         // replay reuses it, so the graph clears the descriptors it uses first.
-        if (capturing) {
+        if (capturing && !p.gate) {
             e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * (size_t)p.n_chunks, s);
             if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
         }

@@ -73,6 +73,9 @@ struct TileParams {
     int lut_keeps_bases;           // MODE_CHAR: the table keeps all of A C G T a c g t
     const unsigned *gate;          // non-null: run only if *gate == gate_epoch
     unsigned gate_epoch;
+    unsigned *clear_gate;          // non-null (captured launches behind the direct path):
+                                   // after a run, the last CTA clears *clear_gate and the
+                                   // chunk descriptors, so the next replay starts clean
 };
 
 constexpr int kMaxB = 256;     // segments per emission round
@@ -1159,15 +1162,27 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
         }
     }
     // The last CTA out resets the chunk counters for the next launch.
+    __shared__ int s_last;
     __syncthreads();
     if (tid == 0) {
         bulk_wait_all();
         __threadfence();
         const unsigned long long done = atomicAdd(&p.tile_counter[1], 1ull);
-        if (done == gridDim.x - 1) {
+        s_last = done == gridDim.x - 1;
+        if (s_last) {
             p.tile_counter[0] = 0ull;
             p.tile_counter[1] = 0ull;
             __threadfence();
+        }
+    }
+    if (p.clear_gate) {
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            uint4 *d = reinterpret_cast<uint4 *>(p.desc);
+            const long long nw = p.n_chunks * (long long)(sizeof(TileDesc) / sizeof(uint4));
+            for (long long i = tid; i < nw; i += NT) d[i] = make_uint4(0u, 0u, 0u, 0u);
+            if (tid == 0) *(volatile unsigned *)p.clear_gate = 0u;
         }
     }
 }
