@@ -607,21 +607,17 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                     const int v = warp * 32 * VPT + q * 32 + lane;
                     unsigned s0 = HS_LS, s1 = HS_HD, s2 = HS_SQ;
                     const uint4 w4 = *reinterpret_cast<const uint4 *>(tb + 16 * v);
-                    const unsigned nb0 = nonbase4(w4.x, codes4(w4.x)) | nonbase4(w4.y, codes4(w4.y)) |
-                                         nonbase4(w4.z, codes4(w4.z)) | nonbase4(w4.w, codes4(w4.w));
                     const bool full = (16 * v >= vlo) && (16 * v + 16 <= vhi);
-                    if (full && !nb0) {
-                        m[q] = HS_SQ | (HS_HD << 2) | (HS_SQ << 4);  // only bases
-                    } else if (full && !has_byte16(w4, 0x3E3E3E3Eu)) {
-                        // no '>': a newline decides the state after it, alone
-                        const unsigned nl = gather4(zero4(w4.x ^ 0x0A0A0A0Au)) |
-                                            (gather4(zero4(w4.y ^ 0x0A0A0A0Au)) << 4) |
-                                            (gather4(zero4(w4.z ^ 0x0A0A0A0Au)) << 8) |
-                                            (gather4(zero4(w4.w ^ 0x0A0A0A0Au)) << 12);
-                        if (!nl) {
+                    // Only '\n' and '>' move the line state.  Without a '>',
+                    // a vector with no newline maps LS -> SQ (its first byte
+                    // starts a sequence line) and keeps HD and SQ; with one, the
+                    // state after its last newline is LS if that newline is the
+                    // vector's last byte, else SQ.
+                    if (full && !has_byte16(w4, 0x3E3E3E3Eu)) {
+                        if (!has_byte16(w4, 0x0A0A0A0Au)) {
                             m[q] = HS_SQ | (HS_HD << 2) | (HS_SQ << 4);
                         } else {
-                            const unsigned e = (nl & 0x8000u) ? HS_LS : HS_SQ;
+                            const unsigned e = (w4.w >> 24) == 0x0Au ? HS_LS : HS_SQ;
                             m[q] = e | (e << 2) | (e << 4);
                         }
                     } else {
