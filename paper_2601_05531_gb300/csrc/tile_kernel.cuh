@@ -686,6 +686,19 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
                 sepm[q] = 0u;
                 if (MODE == MODE_CHAR && !p.lut_keeps_bases) {
                     s = true;
+                } else if (BSRC == BSRC_FASTA && PACKED && !full_pass) {
+                    // pass 1 of FASTA input needs kept counts only: outside
+                    // header lines every byte but a separator is kept (the
+                    // scan element's trailing codes are read from the bytes)
+                    const unsigned sm = sepmask16(w4);
+                    const bool gt = has_byte16(w4, 0x3E3E3E3Eu);
+                    if (sm || gt) {
+                        s = true;
+                        if (full && !gt && hin[q] != HS_HD) {
+                            md = true;
+                            sepm[q] = sm;
+                        }
+                    }
                 } else if (full_pass || BSRC == BSRC_FASTA || MODE == MODE_CHAR) {
                     const unsigned c0 = codes4(w4.x), c1 = codes4(w4.y);
                     const unsigned c2 = codes4(w4.z), c3 = codes4(w4.w);
