@@ -607,6 +607,48 @@ def run_gpu(args):
     return 0
 
 
+def run_fasta_chunk(args):
+    """Device-resident 6-mer encode of one FASTA chunk (the first
+    `--fasta-chunk-mib` MiB of the seeded config-4 stream), the unit of work
+    the host-streamed encode gives the general kernel: prints one JSON line
+    with the per-encode time (CUDA events, median of --steps)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    import paper_2601_05531_gb300 as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = int(args.fasta_chunk_mib) << 20
+    host = np.empty(n, dtype=np.uint8)
+    synth.fasta_stream(n, seed=47, out=host)
+    d = torch.from_numpy(host).to(dev)
+    with P.Tokenizer(P.KMER, k=6, fmt=P.FASTA) as tok:
+        ids, o, tot = tok.alloc_outputs(n, 1, device=dev)
+        s = torch.cuda.current_stream()
+        for _ in range(max(args.warmup, 3)):
+            tok.encode(d, None, ids, o, tot, stream=s)
+        tok.sync()
+        evs = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            tok.encode(d, None, ids, o, tot, stream=s)
+            b.record(s)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        tok.sync()
+        us = sorted(1e3 * a.elapsed_time(b) for a, b in evs)
+        med = us[len(us) // 2]
+        print(json.dumps({"workload": "6-mer ids of a %d MiB FASTA chunk (device-resident)"
+                                      % args.fasta_chunk_mib,
+                          "median_us": med, "gb_per_s": n / (med * 1e-6) / 1e9,
+                          "tokens": int(tot[0])}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -621,7 +663,11 @@ def main():
                     help="skip the batched / serving measurements")
     ap.add_argument("--stream-gib", type=float, default=8.0,
                     help="size of the host-streamed FASTA measurement (0 = skip)")
+    ap.add_argument("--fasta-chunk-mib", type=int, default=0,
+                    help="time only the device-resident encode of one FASTA chunk of this size")
     args = ap.parse_args()
+    if args.fasta_chunk_mib > 0:
+        return run_fasta_chunk(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
