@@ -25,8 +25,8 @@ namespace dnatok {
 namespace {
 
 constexpr int kDThreads = 256;
-constexpr int kPlanThreads = 256;
-constexpr int kPlanTile = 2048;  // records per pass of the plan kernel
+constexpr int kPlanThreads = 1024;
+constexpr int kPlanTile = 4096;  // records per pass of the plan kernel
 
 struct DirectParams {
     const uint8_t *base;       // bytes rounded down to 16
@@ -55,9 +55,9 @@ __device__ __forceinline__ void raise_gate(const DirectParams &q) {
 }
 
 // id offsets from the record lengths; any malformed offset sends the encode
-// to the general path (which reports it).  One small block (it shares an SM
-// with the direct kernel's CTAs, which start while it runs): passes of
-// kPlanTile records, each loaded and stored coalesced through shared memory.
+// to the general path (which reports it).  One block (the direct kernel's
+// CTAs start while it runs): passes of kPlanTile records, each loaded and
+// stored coalesced through shared memory, one pass for up to 4096 records.
 __global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams q) {
     constexpr int kPer = kPlanTile / kPlanThreads;
     __shared__ long long s_v[kPlanTile + 1];
