@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "dnatok_oracle.c")
 _LIB = os.path.join(_HERE, "_liboracle.so")
 _lib = None
 
-CHAR, KMER, BPE = 0, 1, 2
+CHAR, KMER, BPE, KMER_OVERLAP = 0, 1, 2, 3
 RAW, FASTA = 0, 1
 
 

@@ -17,7 +17,10 @@
  *     (MapKmer in Algorithm 2) -- here the closed form
  *     id = sum_i 4^(k-1-i) * code(b_i);
  *   - BPE with a fixed, rank-ordered merge table whose segmentation and
- *     IDs must match the source tokenizer (Sec. 1.1, Sec. 4.3).
+ *     IDs must match the source tokenizer (Sec. 1.1, Sec. 4.3);
+ *   - overlapping k-mers with stride 1: every substring of k bases is a
+ *     token, adjacent tokens share k-1 bases, and an input of L bases gives
+ *     L-k+1 tokens (Sec. 1.1, Table 1).
  *
  * Readings where the paper is silent (each one is a test in tests/):
  *   C1  case-insensitive: a/c/g/t/n behave like A/C/G/T/N (Algorithm 1).
@@ -42,12 +45,15 @@
  *       smallest (left, right); stop when the best count is below 2; each
  *       merge is applied left to right without overlap.
  *   C10 ids are int32, record offsets int64.
+ *   C15 overlapping k-mers: per record over kept bases (as C6), one token for
+ *       every start j <= L - k with the C6 ids (any N-class base: UNK = 4^k);
+ *       a record with L < k bases has no token.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_CHAR = 0, OR_KMER = 1, OR_BPE = 2 };
+enum { OR_CHAR = 0, OR_KMER = 1, OR_BPE = 2, OR_KMER_OVL = 3 };
 enum { OR_RAW = 0, OR_FASTA = 1 };
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_CAPACITY = -3, OR_ERR_NOMEM = -8 };
 
@@ -262,7 +268,8 @@ int64_t oracle_bpe_word(const int32_t *merges, int32_t n_merges, const int32_t *
 /* -------------------------------------------------------------- encode */
 
 /*
- * Encode a byte stream.  mode: 0 single-nucleotide, 1 k-mer, 2 BPE.
+ * Encode a byte stream.  mode: 0 single-nucleotide, 1 k-mer, 2 BPE,
+ * 3 overlapping (stride-1) k-mer.
  * fmt: 0 RAW (records given by seq_offsets[0..n_seq]), 1 FASTA (records
  * found from header lines).  lut: 256 ids for mode 0 (NULL = default C5).
  * Outputs: ids (capacity ids_cap), offsets (capacity offs_cap >= n_rec + 1),
@@ -272,8 +279,8 @@ int oracle_encode(int mode, int k, const int32_t *lut_in, const int32_t *merges,
                   int32_t n_merges, int fmt, const uint8_t *bytes, int64_t n,
                   const int64_t *seq_offsets, int64_t n_seq, int32_t *ids, int64_t ids_cap,
                   int64_t *offsets, int64_t offs_cap, int64_t *n_ids_out, int64_t *n_rec_out) {
-    if (mode < 0 || mode > 2 || fmt < 0 || fmt > 1 || n < 0) return OR_ERR_ARG;
-    if (mode == OR_KMER && (k < 1 || k > 15)) return OR_ERR_ARG;
+    if (mode < 0 || mode > 3 || fmt < 0 || fmt > 1 || n < 0) return OR_ERR_ARG;
+    if ((mode == OR_KMER || mode == OR_KMER_OVL) && (k < 1 || k > 15)) return OR_ERR_ARG;
     if (fmt == OR_RAW) {
         if (n_seq < 0 || !seq_offsets || seq_offsets[0] != 0 || seq_offsets[n_seq] != n)
             return OR_ERR_ARG;
@@ -331,6 +338,20 @@ int oracle_encode(int mode, int k, const int32_t *lut_in, const int32_t *merges,
                         if (c < 0) { id = unk; break; }
                         id = id * 4 + c;
                     }
+                }
+                ids[w++] = (int32_t)id;
+            }
+        } else if (mode == OR_KMER_OVL) {
+            /* C15: a token at every start j with j + k <= L */
+            int64_t unk = (int64_t)1 << (2 * k);
+            int64_t n_tok = L >= k ? L - k + 1 : 0;
+            if (w + n_tok > ids_cap) { status = OR_ERR_CAPACITY; goto out; }
+            for (int64_t j = 0; j < n_tok; ++j) {
+                int64_t id = 0;
+                for (int i = 0; i < k; ++i) {
+                    int32_t c = sym[j + i];
+                    if (c < 0) { id = unk; break; }
+                    id = id * 4 + c;
                 }
                 ids[w++] = (int32_t)id;
             }
@@ -435,7 +456,9 @@ static int64_t bpe_token_text(const int32_t *merges, int32_t m, int32_t id, char
 
 /* Decode ids back to text: mode 0 uses the default table's inverse (A C G T
  * N), mode 1 writes k bases per k-mer id and '?' for UNK, mode 2 expands
- * merges.  Returns the text length or -1. */
+ * merges, mode 3 (one record of overlapping k-mers) writes the first k-mer's
+ * k bases and then the last base of each next one.  Returns the text length
+ * or -1. */
 int64_t oracle_decode(int mode, int k, const int32_t *merges, int32_t n_merges,
                       const int32_t *ids, int64_t n_ids, char *out, int64_t cap) {
     int64_t w = 0;
@@ -444,7 +467,11 @@ int64_t oracle_decode(int mode, int k, const int32_t *merges, int32_t n_merges,
         if (mode == OR_CHAR) {
             if (w + 1 > cap || id < 0 || id > 4) return -1;
             out[w++] = "ACGTN"[id];
-        } else if (mode == OR_KMER) {
+        } else if (mode == OR_KMER_OVL && t > 0) {
+            int64_t unk = (int64_t)1 << (2 * k);
+            if (w + 1 > cap || id < 0 || id > unk) return -1;
+            out[w++] = id == unk ? '?' : "ACGT"[id & 3];
+        } else if (mode == OR_KMER || mode == OR_KMER_OVL) {
             int64_t unk = (int64_t)1 << (2 * k);
             if (id == unk) {
                 if (w + 1 > cap) return -1;

@@ -108,3 +108,21 @@ def bpe_ids(symbols, merges):
 
 def char_ids(body: bytes, lut):
     return [int(lut[b]) for b in body if int(lut[b]) >= 0]
+
+
+def kmer_overlap(data: bytes, k: int):
+    """Overlapping k-mers of one record, stride 1 (reading C15): drop the
+    separators, then for every start j with j + k <= L take bases j..j+k-1;
+    the id is their base-4 number, or 4^k when any is not a base letter."""
+    kept = [b for b in data if b not in SEPARATORS]
+    out = []
+    for j in range(len(kept) - k + 1):
+        window = kept[j:j + k]
+        if all(b in BASES for b in window):
+            v = 0
+            for b in window:
+                v = 4 * v + BASES[b]
+            out.append(v)
+        else:
+            out.append(4 ** k)
+    return out

@@ -84,7 +84,7 @@ def test_k1_equals_default_char():
 
 
 @pytest.mark.parametrize("mode,k", [(oracle.CHAR, 1), (oracle.KMER, 6), (oracle.KMER, 4),
-                                    (oracle.BPE, 1)])
+                                    (oracle.BPE, 1), (oracle.KMER_OVERLAP, 6)])
 def test_separator_insertion_is_invariant(mode, k):
     rng = np.random.default_rng(11)
     merges = [(0, 0), (1, 2), (4, 3), (2, 2), (5, 0)]
@@ -98,7 +98,75 @@ def test_separator_insertion_is_invariant(mode, k):
         assert got.tolist() == ref.tolist()
 
 
+# ------------------------------------------------------ overlapping k-mers
+
+def test_kmer_overlap_hand_examples():
+    n = 0
+    for k, text, want in G.rows("kmer_overlap_examples.txt"):
+        ids, offs = oracle.encode(G.unescape(text), oracle.KMER_OVERLAP, k=int(k))
+        assert ids.tolist() == G.ints(want), (k, text)
+        assert offs.tolist() == [0, len(G.ints(want))]
+        n += 1
+    assert n >= 11
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 6, 9, 15])
+def test_kmer_overlap_matches_literal_definition(k):
+    data = synth.iid_sequence(2500, seed=200 + k, n_fraction=0.03, lower_fraction=0.2)
+    rng = np.random.default_rng(k)
+    pos = np.sort(rng.choice(len(data) + 1, size=40))
+    data = np.insert(data, pos, rng.choice(np.frombuffer(b"\n\r \t", np.uint8), size=40))
+    ids, _ = oracle.encode(data, oracle.KMER_OVERLAP, k=k)
+    assert ids.tolist() == literal.kmer_overlap(bytes(data), k)
+
+
+def test_kmer_overlap_counts_per_record():
+    # L - k + 1 tokens per record (none when L < k), records independent
+    rng = np.random.default_rng(3)
+    lens = [0, 1, 5, 6, 7, 40, 3, 6]
+    data, offs = synth.markov_batch(lens, 0.4, seed=3)
+    for k in (1, 6, 7):
+        ids, o = oracle.encode(data, oracle.KMER_OVERLAP, k=k, seq_offsets=offs)
+        assert np.diff(o).tolist() == [max(0, L - k + 1) for L in lens]
+        for r, L in enumerate(lens):
+            rec = bytes(data[offs[r]:offs[r + 1]])
+            assert ids[o[r]:o[r + 1]].tolist() == literal.kmer_overlap(rec, k)
+
+
+@pytest.mark.parametrize("k", [2, 4, 6, 11])
+def test_kmer_overlap_every_kth_window_is_the_blocked_kmer(k):
+    data = synth.iid_sequence(30 * k + 7, seed=k, n_fraction=0.02, lower_fraction=0.1)
+    ovl, _ = oracle.encode(data, oracle.KMER_OVERLAP, k=k)
+    blk, _ = oracle.encode(data, oracle.KMER, k=k)
+    full = len(data) // k  # blocks without the UNK tail
+    assert ovl[::k][:full].tolist() == blk[:full].tolist()
+
+
+def test_kmer_overlap_k1_equals_default_char():
+    data = synth.random_bytes(3000, seed=8)
+    a, oa = oracle.encode(data, oracle.KMER_OVERLAP, k=1)
+    b, ob = oracle.encode(data, oracle.CHAR)
+    assert a.tolist() == b.tolist() and oa.tolist() == ob.tolist()
+
+
+def test_kmer_overlap_fasta_matches_records():
+    text = synth.fuzz_fasta(5, n_records=6, max_len=300)
+    ids, offs = oracle.encode(text, oracle.KMER_OVERLAP, k=5, fmt=oracle.FASTA)
+    recs = literal.fasta_records(bytes(text))
+    assert len(offs) == len(recs) + 1
+    for r, body in enumerate(recs):
+        assert ids[offs[r]:offs[r + 1]].tolist() == literal.kmer_overlap(body, 5)
+
+
 # --------------------------------------------------------------------- decode
+
+def test_decode_roundtrip_kmer_overlap():
+    for k in (1, 3, 6, 15):
+        data = synth.iid_sequence(500 + k, seed=40 + k, n_fraction=0.0, lower_fraction=0.3)
+        ids, _ = oracle.encode(data, oracle.KMER_OVERLAP, k=k)
+        assert len(ids) == len(data) - k + 1
+        assert oracle.decode(ids, oracle.KMER_OVERLAP, k=k) == bytes(data).upper()
+
 
 def test_decode_roundtrip_kmer():
     for k in (1, 2, 6, 11, 15):
