@@ -15,7 +15,12 @@
  *   DNATOK_KMER  non-overlapping k-mers, id = sum_i 4^(k-1-i) * code(b_i),
  *                A0 C1 G2 T3, UNK = 4^k (MapKmer, Algorithm 2);
  *   DNATOK_BPE   greedy rank-ordered BPE merges of a fixed table
- *                (segmentation identical to the table's tokenizer, Sec. 4.3).
+ *                (segmentation identical to the table's tokenizer, Sec. 4.3);
+ *   DNATOK_KMER_OVERLAP  overlapping k-mers with stride 1: a token at every
+ *                kept base j with j + k <= L of a record of L kept bases
+ *                (L - k + 1 tokens, none when L < k; Sec. 1.1, Table 1), same
+ *                ids and UNK as DNATOK_KMER.  One-shot encodes only (no
+ *                host streams, no serving loop).
  *
  * Conventions for what the paper leaves open (identical in the CPU oracle):
  *   - case-insensitive; '\n' '\r' ' ' '\t' are dropped (they emit nothing and
@@ -75,7 +80,12 @@ typedef enum {
     DNATOK_ERR_DEVICE_DATA = -10  /* device-side input (seq_offsets) malformed */
 } dnatok_status;
 
-typedef enum { DNATOK_CHAR = 0, DNATOK_KMER = 1, DNATOK_BPE = 2 } dnatok_mode;
+typedef enum {
+    DNATOK_CHAR = 0,
+    DNATOK_KMER = 1,
+    DNATOK_BPE = 2,
+    DNATOK_KMER_OVERLAP = 3
+} dnatok_mode;
 typedef enum { DNATOK_RAW = 0, DNATOK_FASTA = 1 } dnatok_format;
 
 /* Same type as cudaStream_t (NULL = the legacy default stream). */
@@ -100,7 +110,8 @@ typedef struct {
 #define DNATOK_MAX_MERGES 16384
 
 /* Create a tokenizer on the current CUDA device.  mode/k/tables as above (k
- * is ignored unless mode == DNATOK_KMER; 1 <= k <= 15).  fmt selects how
+ * is ignored unless mode is DNATOK_KMER or DNATOK_KMER_OVERLAP;
+ * 1 <= k <= 15).  fmt selects how
  * records are found by dnatok_encode and the stream API.  Tables are
  * validated and copied to device memory.  On success *out owns its device
  * tables and workspace; release it with dnatok_destroy. */

@@ -8,10 +8,10 @@ tokenization runs in the library's CUDA kernels).
 from __future__ import annotations
 
 from . import binding
-from .binding import (BPE, CHAR, END_OF_STREAM, FASTA, HOST_PINNED, KMER, NEW_RECORD, RAW,
+from .binding import (BPE, CHAR, END_OF_STREAM, FASTA, HOST_PINNED, KMER, KMER_OVERLAP, NEW_RECORD, RAW,
                       DnatokError)
 
-__all__ = ["binding", "Tokenizer", "CHAR", "KMER", "BPE", "RAW", "FASTA", "DnatokError",
+__all__ = ["binding", "Tokenizer", "CHAR", "KMER", "KMER_OVERLAP", "BPE", "RAW", "FASTA", "DnatokError",
            "END_OF_STREAM", "NEW_RECORD", "HOST_PINNED", "build"]
 
 

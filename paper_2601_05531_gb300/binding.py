@@ -13,7 +13,7 @@ import os
 
 from . import _build
 
-CHAR, KMER, BPE = 0, 1, 2
+CHAR, KMER, BPE, KMER_OVERLAP = 0, 1, 2, 3  # dnatok_mode
 RAW, FASTA = 0, 1
 
 OK, PENDING = 0, 1

@@ -168,16 +168,17 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
                             const dnatok_tables *tables, dnatok_format fmt) {
     if (!out) return fail(nullptr, DNATOK_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (mode != DNATOK_CHAR && mode != DNATOK_KMER && mode != DNATOK_BPE)
+    if (mode != DNATOK_CHAR && mode != DNATOK_KMER && mode != DNATOK_BPE &&
+        mode != DNATOK_KMER_OVERLAP)
         return fail(nullptr, DNATOK_ERR_ARG, "unknown mode");
     if (fmt != DNATOK_RAW && fmt != DNATOK_FASTA)
         return fail(nullptr, DNATOK_ERR_ARG, "unknown format");
-    if (mode == DNATOK_KMER && (k < 1 || k > DNATOK_MAX_K))
+    if ((mode == DNATOK_KMER || mode == DNATOK_KMER_OVERLAP) && (k < 1 || k > DNATOK_MAX_K))
         return fail(nullptr, DNATOK_ERR_ARG, "k must be in [1, 15]");
     dnatok_handle *h = new (std::nothrow) dnatok_handle();
     if (!h) return fail(nullptr, DNATOK_ERR_NOMEM, "host allocation failed");
     h->mode = mode;
-    h->k = (mode == DNATOK_KMER) ? k : 1;
+    h->k = (mode == DNATOK_KMER || mode == DNATOK_KMER_OVERLAP) ? k : 1;
     h->fmt = fmt;
     if (mode == DNATOK_CHAR && tables && tables->ascii_lut256) {
         for (int b = 0; b < 256; ++b) {
@@ -228,6 +229,7 @@ void dnatok_destroy(dnatok_handle *h) {
     cudaDeviceSynchronize();
     stream_destroy(h);
     bpe_destroy(h);
+    ovl_destroy(h);
     cudaFree(h->d_lut);
     cudaFree(h->d_desc);
     cudaFree(h->d_tile_rec);
@@ -258,6 +260,8 @@ dnatok_status dnatok_reserve(dnatok_handle *h, int64_t max_bytes, int64_t max_se
     dnatok_status st = ensure_workspace(h, max_bytes, max_seq + 1, h->shape, 0);
     if (st != DNATOK_OK) return st;
     if (h->mode == DNATOK_BPE) return bpe_reserve(h, max_bytes);
+    if (h->mode == DNATOK_KMER_OVERLAP)
+        return ovl_reserve(h, max_bytes, h->fmt == DNATOK_RAW ? max_seq + 1 : max_bytes + 2, 0);
     return DNATOK_OK;
 }
 
@@ -290,6 +294,9 @@ dnatok_status dnatok_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (h->mode == DNATOK_BPE)
         return bpe_encode(h, bytes_d, n_bytes, seq_offsets_d, n_seq, ids_out_d, ids_capacity,
+                          id_offsets_d, offsets_capacity, totals_d, s);
+    if (h->mode == DNATOK_KMER_OVERLAP)
+        return ovl_encode(h, bytes_d, n_bytes, seq_offsets_d, n_seq, ids_out_d, ids_capacity,
                           id_offsets_d, offsets_capacity, totals_d, s);
     const int mode = (h->mode == DNATOK_CHAR) ? MODE_CHAR : MODE_KMER;
     if (h->fmt == DNATOK_RAW)

@@ -12,6 +12,7 @@
 
 struct StreamState;  // host-streamed pipeline (stream.cu)
 struct BpeState;     // BPE tables and workspace (bpe.cu)
+struct OvlState;     // overlapping k-mer workspace (ovl.cu)
 
 struct dnatok_handle {
     int mode = 0;
@@ -47,6 +48,7 @@ struct dnatok_handle {
 
     StreamState *stream = nullptr;
     BpeState *bpe = nullptr;
+    OvlState *ovl = nullptr;
 
     std::string last_error;
 };
@@ -89,6 +91,15 @@ dnatok_status bpe_reserve(dnatok_handle *h, long long max_bytes);
 dnatok_status bpe_set_launch(dnatok_handle *h, int seg_symbols, int halo);
 dnatok_status bpe_get_launch(const dnatok_handle *h, int *seg_symbols, int *halo);
 dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
+                         const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
+                         int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
+                         int64_t *totals_d, cudaStream_t s);
+
+// overlapping k-mers (ovl.cu)
+void ovl_destroy(dnatok_handle *h);
+dnatok_status ovl_reserve(dnatok_handle *h, long long max_bytes, long long max_offsets,
+                          cudaStream_t s);
+dnatok_status ovl_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
                          const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
                          int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
                          int64_t *totals_d, cudaStream_t s);
