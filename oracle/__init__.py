@@ -5,11 +5,13 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 and shares no code with it.
 
 ``dnatok_oracle.c`` is the plain single-threaded statement of the method
-(record split, byte classes, single-nucleotide / k-mer / BPE tokenization,
-offsets, the BPE trainer and a decoder); ``literal.py`` holds even simpler
+(record split, byte classes, single-nucleotide / k-mer / BPE / overlapping
+and table-driven k-mer tokenization, offsets, the BPE trainer, decoders and
+the reverse complement); ``feed`` below is the fixed-shape model feed in
+plain numpy; ``literal.py`` holds even simpler
 pure-Python definitions used to brute-force check the C oracle on tiny
-inputs.  The conventions the paper leaves open (C1-C10) are listed at the
-top of ``dnatok_oracle.c``.
+inputs.  The conventions the paper leaves open (C1-C18) are listed at the
+top of ``dnatok_oracle.c``; C19 (the feed) is stated at ``feed``.
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ _SRC = os.path.join(_HERE, "dnatok_oracle.c")
 _LIB = os.path.join(_HERE, "_liboracle.so")
 _lib = None
 
-CHAR, KMER, BPE, KMER_OVERLAP = 0, 1, 2, 3
+CHAR, KMER, BPE, KMER_OVERLAP, KMER_TABLE = 0, 1, 2, 3, 4
 RAW, FASTA = 0, 1
 
 
@@ -58,6 +60,15 @@ def _load():
         lib.oracle_decode.restype = i64
         lib.oracle_default_lut.argtypes = [i32p]
         lib.oracle_default_lut.restype = None
+        lib.oracle_encode_ktab.argtypes = [cint, i32p, i32p, cint, u8p, i64, i64p, i64, i32p,
+                                           i64, i64p, i64, i64p, i64p]
+        lib.oracle_encode_ktab.restype = cint
+        lib.oracle_revcomp.argtypes = [u8p, i64, i64p, i64, u8p]
+        lib.oracle_revcomp.restype = cint
+        lib.oracle_decode_lut.argtypes = [i32p, i32p, i64, ctypes.c_char_p, i64]
+        lib.oracle_decode_lut.restype = i64
+        lib.oracle_decode_ktab.argtypes = [cint, i32p, i32p, i32p, i64, ctypes.c_char_p, i64]
+        lib.oracle_decode_ktab.restype = i64
         _lib = lib
     return _lib
 
@@ -161,4 +172,93 @@ def codes_of(text) -> np.ndarray:
         table[c] = v
     out = table[a]
     assert (out < 4).all(), "codes_of expects uppercase ACGT only"
+    return out
+
+
+def _records(data, seq_offsets):
+    if isinstance(data, (bytes, bytearray)):
+        data = np.frombuffer(bytes(data), dtype=np.uint8)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    if seq_offsets is None:
+        seq_offsets = np.array([0, data.size], dtype=np.int64)
+    return data, np.ascontiguousarray(seq_offsets, dtype=np.int64)
+
+
+def encode_ktab(data, k: int, kmer_lut, base_ids, seq_offsets=None, fmt: int = RAW):
+    """Table-driven k-mers (reading C16).  Returns (ids int32, offsets int64)."""
+    data, so = _records(data, seq_offsets)
+    n = data.size
+    kl = np.ascontiguousarray(kmer_lut, dtype=np.int32)
+    bi = np.ascontiguousarray(base_ids, dtype=np.int32)
+    assert kl.size == 5 ** k and bi.size == 5
+    if fmt == RAW:
+        n_seq, offs_cap, sop = so.size - 1, so.size, _p(so, ctypes.c_int64)
+    else:
+        n_seq, offs_cap, sop = 0, n + 2, None
+    ids = np.empty(max(n, 1), dtype=np.int32)
+    offs = np.empty(offs_cap, dtype=np.int64)
+    n_ids, n_rec = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = _load().oracle_encode_ktab(k, _p(kl, ctypes.c_int32), _p(bi, ctypes.c_int32), fmt,
+                                    _p(data, ctypes.c_uint8), n, sop, n_seq,
+                                    _p(ids, ctypes.c_int32), n, _p(offs, ctypes.c_int64),
+                                    offs_cap, ctypes.byref(n_ids), ctypes.byref(n_rec))
+    if st != 0:
+        raise RuntimeError("oracle_encode_ktab failed with status %d" % st)
+    return ids[: n_ids.value].copy(), offs[: n_rec.value + 1].copy()
+
+
+def revcomp(data, seq_offsets=None) -> np.ndarray:
+    """Reverse complement of every record (reading C18)."""
+    data, so = _records(data, seq_offsets)
+    out = np.empty(max(data.size, 1), dtype=np.uint8)
+    st = _load().oracle_revcomp(_p(data, ctypes.c_uint8), data.size, _p(so, ctypes.c_int64),
+                                so.size - 1, _p(out, ctypes.c_uint8))
+    if st != 0:
+        raise RuntimeError("oracle_revcomp failed with status %d" % st)
+    return out[: data.size].copy()
+
+
+def decode_lut(ids, lut) -> bytes:
+    """Single-nucleotide ids through the inverse of ``lut`` (reading C17)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    lut = np.ascontiguousarray(lut, dtype=np.int32)
+    buf = ctypes.create_string_buffer(max(ids.size, 1))
+    n = _load().oracle_decode_lut(_p(lut, ctypes.c_int32), _p(ids, ctypes.c_int32), ids.size,
+                                  buf, ids.size)
+    if n < 0:
+        raise RuntimeError("oracle_decode_lut: an id has no inverse")
+    return buf.raw[:n]
+
+
+def decode_ktab(ids, k: int, kmer_lut, base_ids) -> bytes:
+    """Table-driven k-mer ids back to text (reading C17)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    kl = np.ascontiguousarray(kmer_lut, dtype=np.int32)
+    bi = np.ascontiguousarray(base_ids, dtype=np.int32)
+    cap = max(ids.size * k, 1)
+    buf = ctypes.create_string_buffer(cap)
+    n = _load().oracle_decode_ktab(k, _p(kl, ctypes.c_int32), _p(bi, ctypes.c_int32),
+                                   _p(ids, ctypes.c_int32), ids.size, buf, cap)
+    if n < 0:
+        raise RuntimeError("oracle_decode_ktab: an id has no inverse")
+    return buf.raw[:n]
+
+
+def feed(ids, id_offsets, token_len: int, id_pad: int, row_begin: int = 0, n_rows=None,
+         dtype=np.int64) -> np.ndarray:
+    """Fixed-shape model feed (reading C19 of Algorithm 2's left padding):
+    row i holds record row_begin + i; a record of m <= token_len tokens is
+    right-aligned after token_len - m copies of id_pad; a longer record keeps
+    its first token_len tokens.  Plain per-row loop."""
+    ids = np.asarray(ids)
+    offs = np.asarray(id_offsets, dtype=np.int64)
+    if n_rows is None:
+        n_rows = offs.size - 1 - row_begin
+    out = np.empty((n_rows, token_len), dtype=dtype)
+    for i in range(n_rows):
+        r = row_begin + i
+        toks = ids[offs[r]:offs[r + 1]][:token_len]
+        pad = token_len - toks.size
+        out[i, :pad] = id_pad
+        out[i, pad:] = toks
     return out

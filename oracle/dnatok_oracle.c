@@ -48,12 +48,29 @@
  *   C15 overlapping k-mers: per record over kept bases (as C6), one token for
  *       every start j <= L - k with the C6 ids (any N-class base: UNK = 4^k);
  *       a record with L < k bases has no token.
+ *   C16 table-driven k-mers (Algorithm 1 builds kmer_lut[0..5^k-1] and a
+ *       byte -> base-5 digit table; Algorithm 2 applies MapKmer): digits A0
+ *       C1 G2 T3, every N-class byte 4 (C1-C3); the record's kept symbols are
+ *       cut into windows of k from its start (as C6); a whole window with
+ *       index sum_i 5^(k-1-i) d_i emits kmer_lut[index] when that entry is
+ *       >= 0, else each of its k symbols as base_ids[d]; a tail of L mod k
+ *       symbols emits base_ids[d] for each one.  1 <= k <= 10.
+ *   C17 decode (Sec. 4, "Decode Operations": an inverse vocabulary table):
+ *       single-nucleotide ids through the inverse of the handle's 256-entry
+ *       table -- for id v the first byte b in the order "ACGTN", then 'A'..'Z',
+ *       'a'..'z', then 0..255, with lut[b] == v; table-driven k-mer ids
+ *       through the smallest index with kmer_lut[index] == v (its k digits
+ *       written as "ACGTN"), else the smallest digit with base_ids[d] == v.
+ *       An id with no inverse is an error.
+ *   C18 reverse complement (Sec. 4, "Integration with Data Augmentation"):
+ *       per record, out[s + e - 1 - i] = comp(in[i]); comp swaps A/T, C/G,
+ *       R/Y, K/M, B/V, D/H in either case, keeps S W N and every other byte.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_CHAR = 0, OR_KMER = 1, OR_BPE = 2, OR_KMER_OVL = 3 };
+enum { OR_CHAR = 0, OR_KMER = 1, OR_BPE = 2, OR_KMER_OVL = 3, OR_KMER_TABLE = 4 };
 enum { OR_RAW = 0, OR_FASTA = 1 };
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_CAPACITY = -3, OR_ERR_NOMEM = -8 };
 
@@ -432,6 +449,89 @@ done:
     return r;
 }
 
+/* ------------------------------------------------- table-driven k-mers */
+
+/* C16: tokens of every record through kmer_lut (5^k entries, -1 = no entry)
+ * and base_ids (5 entries for the digits A C G T N).  Arguments and results
+ * as oracle_encode. */
+int oracle_encode_ktab(int k, const int32_t *kmer_lut, const int32_t *base_ids, int fmt,
+                       const uint8_t *bytes, int64_t n, const int64_t *seq_offsets,
+                       int64_t n_seq, int32_t *ids, int64_t ids_cap, int64_t *offsets,
+                       int64_t offs_cap, int64_t *n_ids_out, int64_t *n_rec_out) {
+    if (k < 1 || k > 10 || !kmer_lut || !base_ids || fmt < 0 || fmt > 1 || n < 0)
+        return OR_ERR_ARG;
+    if (fmt == OR_RAW) {
+        if (n_seq < 0 || !seq_offsets || seq_offsets[0] != 0 || seq_offsets[n_seq] != n)
+            return OR_ERR_ARG;
+        for (int64_t r = 0; r < n_seq; ++r)
+            if (seq_offsets[r + 1] < seq_offsets[r]) return OR_ERR_ARG;
+    }
+    int64_t *rs = NULL;
+    uint8_t *hdr = NULL;
+    int64_t n_rec = split_records(fmt, bytes, n, seq_offsets, n_seq, &rs, &hdr);
+    if (n_rec < 0) return OR_ERR_NOMEM;
+    int32_t *digit = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int status = OR_OK;
+    int64_t w = 0;
+    if (!digit) { status = OR_ERR_NOMEM; goto out; }
+    if (n_rec + 1 > offs_cap) { status = OR_ERR_CAPACITY; goto out; }
+    for (int64_t r = 0; r < n_rec; ++r) {
+        offsets[r] = w;
+        int64_t L = 0;
+        for (int64_t i = rs[r]; i < rs[r + 1]; ++i) {
+            if (hdr[i]) continue;
+            int code = 0, c = classify(bytes[i], &code);
+            if (c == K_BASE) digit[L++] = code;
+            else if (c == K_NCLASS) digit[L++] = 4;
+        }
+        int64_t t = 0;
+        for (; t + k <= L; t += k) {  /* whole windows */
+            int64_t index = 0;
+            for (int i = 0; i < k; ++i) index = index * 5 + digit[t + i];
+            if (kmer_lut[index] >= 0) {
+                if (w + 1 > ids_cap) { status = OR_ERR_CAPACITY; goto out; }
+                ids[w++] = kmer_lut[index];
+            } else {
+                if (w + k > ids_cap) { status = OR_ERR_CAPACITY; goto out; }
+                for (int i = 0; i < k; ++i) ids[w++] = base_ids[digit[t + i]];
+            }
+        }
+        for (; t < L; ++t) {  /* the tail */
+            if (w + 1 > ids_cap) { status = OR_ERR_CAPACITY; goto out; }
+            ids[w++] = base_ids[digit[t]];
+        }
+    }
+    offsets[n_rec] = w;
+    *n_ids_out = w;
+    *n_rec_out = n_rec;
+out:
+    free(digit); free(rs); free(hdr);
+    return status;
+}
+
+/* ---------------------------------------------------- reverse complement */
+
+static uint8_t complement(uint8_t b) {
+    static const char from[] = "ACGTRYKMBVDHacgtrykmbvdh";
+    static const char to[] = "TGCAYRMKVBHDtgcayrmkvbhd";
+    for (int i = 0; from[i]; ++i)
+        if ((uint8_t)from[i] == b) return (uint8_t)to[i];
+    return b;
+}
+
+/* C18: reverse complement of every record [seq_offsets[r], seq_offsets[r+1]). */
+int oracle_revcomp(const uint8_t *in, int64_t n, const int64_t *seq_offsets, int64_t n_seq,
+                   uint8_t *out) {
+    if (n < 0 || n_seq < 0 || !seq_offsets || seq_offsets[0] != 0 || seq_offsets[n_seq] != n)
+        return OR_ERR_ARG;
+    for (int64_t r = 0; r < n_seq; ++r) {
+        const int64_t s = seq_offsets[r], e = seq_offsets[r + 1];
+        if (e < s) return OR_ERR_ARG;
+        for (int64_t i = s; i < e; ++i) out[s + e - 1 - i] = complement(in[i]);
+    }
+    return OR_OK;
+}
+
 /* -------------------------------------------------------------- decode */
 
 /* Write the bases a BPE token stands for (recursively through the merge
@@ -486,6 +586,56 @@ int64_t oracle_decode(int mode, int k, const int32_t *merges, int32_t n_merges,
             if (m < 0) return -1;
             w += m;
         }
+    }
+    return w;
+}
+
+/* C17: single-nucleotide ids through the inverse of a 256-entry table. */
+int64_t oracle_decode_lut(const int32_t *lut, const int32_t *ids, int64_t n_ids, char *out,
+                          int64_t cap) {
+    int order[256 + 62 + 5], n_order = 0;
+    const char *first = "ACGTN";
+    for (int i = 0; first[i]; ++i) order[n_order++] = (uint8_t)first[i];
+    for (int c = 'A'; c <= 'Z'; ++c) order[n_order++] = c;
+    for (int c = 'a'; c <= 'z'; ++c) order[n_order++] = c;
+    for (int c = 0; c < 256; ++c) order[n_order++] = c;
+    if (n_ids > cap) return -1;
+    for (int64_t t = 0; t < n_ids; ++t) {
+        int found = -1;
+        for (int i = 0; i < n_order && found < 0; ++i)
+            if (lut[order[i]] == ids[t]) found = order[i];
+        if (found < 0 || ids[t] < 0) return -1;
+        out[t] = (char)found;
+    }
+    return n_ids;
+}
+
+/* C17: table-driven k-mer ids back to text. */
+int64_t oracle_decode_ktab(int k, const int32_t *kmer_lut, const int32_t *base_ids,
+                           const int32_t *ids, int64_t n_ids, char *out, int64_t cap) {
+    if (k < 1 || k > 10) return -1;
+    int64_t n_index = 1;
+    for (int i = 0; i < k; ++i) n_index *= 5;
+    int64_t w = 0;
+    for (int64_t t = 0; t < n_ids; ++t) {
+        const int32_t v = ids[t];
+        int64_t index = -1;
+        for (int64_t x = 0; x < n_index && index < 0 && v >= 0; ++x)
+            if (kmer_lut[x] == v) index = x;
+        if (index >= 0) {
+            if (w + k > cap) return -1;
+            for (int i = k - 1; i >= 0; --i) {
+                out[w + i] = "ACGTN"[index % 5];
+                index /= 5;
+            }
+            w += k;
+            continue;
+        }
+        int d = -1;
+        for (int x = 0; x < 5 && d < 0; ++x)
+            if (base_ids[x] == v && v >= 0) d = x;
+        if (d < 0 || w + 1 > cap) return -1;
+        out[w++] = "ACGTN"[d];
     }
     return w;
 }

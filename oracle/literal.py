@@ -126,3 +126,33 @@ def kmer_overlap(data: bytes, k: int):
         else:
             out.append(4 ** k)
     return out
+
+
+def kmer_table(symbols, k, kmer_lut, base_ids):
+    """Reading C16 on one record's kept symbols (0..3, None for N-class):
+    whole windows of k go through kmer_lut[sum 5^(k-1-i) d_i] when that entry
+    is >= 0, else symbol by symbol through base_ids; a tail goes symbol by
+    symbol."""
+    digits = [4 if s is None else s for s in symbols]
+    out = []
+    n_whole = len(digits) // k
+    for t in range(n_whole):
+        win = digits[t * k:(t + 1) * k]
+        index = 0
+        for d in win:
+            index = 5 * index + d
+        if kmer_lut[index] >= 0:
+            out.append(int(kmer_lut[index]))
+        else:
+            out.extend(int(base_ids[d]) for d in win)
+    out.extend(int(base_ids[d]) for d in digits[n_whole * k:])
+    return out
+
+
+COMPLEMENT = dict(zip(b"ACGTRYKMBVDHSWNacgtrykmbvdhswn", b"TGCAYRMKVBHDSWNtgcayrmkvbhdswn"))
+
+
+def reverse_complement(body: bytes) -> bytes:
+    """Reading C18 on one record: reversed, each byte complemented (bytes
+    outside the IUPAC letters kept)."""
+    return bytes(COMPLEMENT.get(b, b) for b in reversed(body))

@@ -190,6 +190,27 @@ def random_bytes(n: int, seed: int) -> np.ndarray:
     return out
 
 
+def kmer_vocab(k: int, seed: int, n_specials: int = 5):
+    """A vocabulary laid out like a blocked k-mer model's: every k-mer of
+    A/C/G/T gets its own id (a seeded permutation after ``n_specials``
+    special ids), windows holding the fifth digit (N) have no entry (-1), and
+    the five single symbols A C G T N get the ids after the k-mers.  Returns
+    (kmer_lut over the 5^k base-5 window indices, base_ids[5]).  Input data
+    only: which windows hold the digit 4 is read off their base-5 index."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    idx = np.arange(5 ** k)
+    has_n = np.zeros(5 ** k, dtype=bool)
+    x = idx.copy()
+    for _ in range(k):
+        has_n |= (x % 5) == 4
+        x //= 5
+    lut = np.full(5 ** k, -1, dtype=np.int32)
+    n_free = int((~has_n).sum())
+    lut[~has_n] = (rng.permutation(n_free) + n_specials).astype(np.int32)
+    base = np.arange(5, dtype=np.int32) + n_specials + n_free
+    return lut, base
+
+
 # ------------------------------------------------------------- named workloads
 
 def single_sequence_1mb(seed: int = 43, n: int = 1_000_000):

@@ -400,3 +400,226 @@ def test_trainer_first_merge_is_most_frequent_pair():
             counts[(int(a), int(b))] = counts.get((int(a), int(b)), 0) + 1
         best = max(counts.items(), key=lambda kv: (kv[1], (-kv[0][0], -kv[0][1])))[0]
         assert tuple(oracle.bpe_train(s, 1)[0].tolist()) == best
+
+
+# ------------------------------------------------- table-driven k-mers (C16)
+
+def _closed4(digits):
+    v = 0
+    for d in digits:
+        v = 4 * v + d
+    return v
+
+
+def _digits5(index, k):
+    out = []
+    for _ in range(k):
+        out.append(index % 5)
+        index //= 5
+    return out[::-1]
+
+
+def ktab_named(name):
+    """The tables the hand-worked fixture names, built from their stated rules."""
+    if name == "T1":
+        return 1, np.array([7, 8, 9, 10, -1], np.int32), np.array([0, 1, 2, 3, 4], np.int32)
+    if name == "T2":
+        lut = np.array([10 + i if 4 not in _digits5(i, 2) else -1 for i in range(25)], np.int32)
+        return 2, lut, np.array([0, 1, 2, 3, 4], np.int32)
+    if name == "T3":
+        lut = np.array([100 + _closed4(_digits5(i, 3)) if 4 not in _digits5(i, 3) else -1
+                        for i in range(125)], np.int32)
+        return 3, lut, np.array([1, 2, 3, 4, 0], np.int32)
+    raise KeyError(name)
+
+
+def random_ktab(rng, k, hole_p=0.3):
+    lut = rng.integers(0, 50000, size=5 ** k).astype(np.int32)
+    lut[rng.random(5 ** k) < hole_p] = -1
+    return lut, rng.integers(0, 50000, size=5).astype(np.int32)
+
+
+def test_ktab_hand_examples():
+    n = 0
+    for name, text, want in G.rows("kmer_table_examples.txt"):
+        k, lut, base = ktab_named(name)
+        ids, offs = oracle.encode_ktab(G.unescape(text), k, lut, base)
+        assert ids.tolist() == G.ints(want), (name, text)
+        assert offs.tolist() == [0, len(G.ints(want))]
+        n += 1
+    assert n >= 14
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6])
+def test_ktab_matches_literal_definition(k):
+    rng = np.random.default_rng(300 + k)
+    lut, base = random_ktab(rng, k)
+    lens = [0, 1, k - 1, k, k + 1, 3 * k, 97, 400]
+    data, offs = synth.markov_batch(lens, 0.4, seed=300 + k)
+    ids, o = oracle.encode_ktab(data, k, lut, base, seq_offsets=offs)
+    for r in range(len(lens)):
+        syms = literal.kept_symbols(bytes(data[offs[r]:offs[r + 1]]))
+        assert ids[o[r]:o[r + 1]].tolist() == literal.kmer_table(syms, k, lut, base)
+
+
+def test_ktab_counts():
+    # floor(L/k) windows, k - 1 more tokens per window without an entry, plus
+    # the L mod k tail symbols
+    rng = np.random.default_rng(7)
+    for k in (2, 5, 6):
+        lut, base = random_ktab(rng, k, hole_p=0.5)
+        data = synth.iid_sequence(1000 + k, seed=k, n_fraction=0.05, lower_fraction=0.2)
+        ids, _ = oracle.encode_ktab(data, k, lut, base)
+        syms = literal.kept_symbols(bytes(data))
+        L = len(syms)
+        holes = 0
+        for t in range(L // k):
+            idx = 0
+            for s in syms[t * k:(t + 1) * k]:
+                idx = 5 * idx + (4 if s is None else s)
+            holes += lut[idx] < 0
+        assert len(ids) == L // k + (k - 1) * holes + L % k
+
+
+@pytest.mark.parametrize("k", [1, 3, 6, 10])
+def test_ktab_with_the_closed_form_table_is_the_kmer_mode(k):
+    # entries = base-4 closed form for windows without N, 4^k (UNK) with N:
+    # on records whose length is a multiple of k (no tail) this is DNATOK_KMER
+    lut = np.empty(5 ** k, np.int32)
+    for i in range(5 ** k):
+        d = _digits5(i, k)
+        lut[i] = (1 << (2 * k)) if 4 in d else _closed4(d)
+    lens = [k * m for m in (0, 1, 2, 17, 150)]
+    data, offs = synth.markov_batch(lens, 0.4, seed=k)
+    a, oa = oracle.encode_ktab(data, k, lut, np.arange(5, dtype=np.int32), seq_offsets=offs)
+    b, ob = oracle.encode(data, oracle.KMER, k=k, seq_offsets=offs)
+    assert a.tolist() == b.tolist() and oa.tolist() == ob.tolist()
+
+
+def test_ktab_k1_identity_table_is_default_char():
+    data = synth.random_bytes(3000, seed=11)
+    a, oa = oracle.encode_ktab(data, 1, np.arange(5, dtype=np.int32), np.arange(5, dtype=np.int32))
+    b, ob = oracle.encode(data, oracle.CHAR)
+    assert a.tolist() == b.tolist() and oa.tolist() == ob.tolist()
+
+
+def test_ktab_fasta_matches_records():
+    rng = np.random.default_rng(5)
+    lut, base = random_ktab(rng, 3)
+    text = synth.fuzz_fasta(6, n_records=6, max_len=300)
+    ids, offs = oracle.encode_ktab(text, 3, lut, base, fmt=oracle.FASTA)
+    recs = literal.fasta_records(bytes(text))
+    assert len(offs) == len(recs) + 1
+    for r, body in enumerate(recs):
+        assert ids[offs[r]:offs[r + 1]].tolist() == literal.kmer_table(
+            literal.kept_symbols(body), 3, lut, base)
+
+
+def test_ktab_decode_roundtrip():
+    # an injective table whose ids differ from the base ids decodes back to
+    # the kept symbols (bases upper-cased, N-class as N), whatever its holes
+    rng = np.random.default_rng(9)
+    for k in (1, 2, 6):
+        lut = (rng.permutation(5 ** k) + 10).astype(np.int32)
+        lut[rng.random(5 ** k) < 0.4] = -1
+        base = np.array([0, 1, 2, 3, 4], np.int32)
+        data = synth.iid_sequence(700 + k, seed=k, n_fraction=0.05, lower_fraction=0.3)
+        ids, _ = oracle.encode_ktab(data, k, lut, base)
+        want = bytes(b"ACGTN"[4 if s is None else s] for s in literal.kept_symbols(bytes(data)))
+        assert oracle.decode_ktab(ids, k, lut, base) == want
+
+
+# ------------------------------------------------------------ decode (C17)
+
+def test_decode_lut_paper_fallback_table():
+    # Algorithm 1's fixed DNA table: A1 C2 G3 T4, N and every other byte 0
+    ids, _ = oracle.encode(b"ACGTNacgtn", oracle.CHAR, lut=PAPER_FALLBACK)
+    assert ids.tolist() == [1, 2, 3, 4, 0, 1, 2, 3, 4, 0]
+    assert oracle.decode_lut(ids, PAPER_FALLBACK) == b"ACGTNACGTN"
+
+
+def test_decode_lut_default_table_is_the_char_decoder():
+    data = synth.random_bytes(2000, seed=4)
+    ids, _ = oracle.encode(data, oracle.CHAR)
+    assert oracle.decode_lut(ids, oracle.default_lut()) == oracle.decode(ids, oracle.CHAR)
+
+
+def test_decode_lut_preference_order():
+    lut = np.full(256, -1, np.int32)
+    lut[ord("x")] = 5
+    lut[ord("Q")] = 5    # upper case before lower case
+    lut[ord("b")] = 6
+    lut[0x07] = 7        # only a control byte
+    assert oracle.decode_lut([5, 6, 7], lut) == b"Qb\x07"
+    with pytest.raises(RuntimeError):
+        oracle.decode_lut([8], lut)
+
+
+# ------------------------------------------------ reverse complement (C18)
+
+def test_revcomp_hand_examples():
+    n = 0
+    for text, want in G.rows("revcomp_examples.txt"):
+        assert oracle.revcomp(G.unescape(text)).tobytes() == G.unescape(want), text
+        n += 1
+    assert n >= 7
+
+
+def test_revcomp_is_an_involution_and_matches_literal():
+    data = synth.random_bytes(5000, seed=12)
+    offs = np.array([0, 1, 10, 10, 999, 4000, 5000], np.int64)
+    rc = oracle.revcomp(data, offs)
+    for r in range(len(offs) - 1):
+        body = bytes(data[offs[r]:offs[r + 1]])
+        assert rc[offs[r]:offs[r + 1]].tobytes() == literal.reverse_complement(body)
+    assert oracle.revcomp(rc, offs).tobytes() == bytes(data)
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_revcomp_kmer_ids_are_reversed_and_complemented(k):
+    # for ACGT records with L mod k = 0, the k-mer ids of the reverse
+    # complement are the reversed list of each id's reverse complement in
+    # base 4: digit i -> 3 - digit(k-1-i)
+    lens = [k * m for m in (1, 5, 60)]
+    data, offs = synth.markov_batch(lens, 0.4, seed=k, n_runs=False)
+    ids, o = oracle.encode(data, oracle.KMER, k=k, seq_offsets=offs)
+    rids, ro = oracle.encode(oracle.revcomp(data, offs), oracle.KMER, k=k, seq_offsets=offs)
+    assert o.tolist() == ro.tolist()
+    for r in range(len(lens)):
+        fw = ids[o[r]:o[r + 1]].tolist()
+        want = []
+        for v in reversed(fw):
+            d = [(v >> (2 * (k - 1 - i))) & 3 for i in range(k)]
+            want.append(_closed4([3 - x for x in reversed(d)]))
+        assert rids[ro[r]:ro[r + 1]].tolist() == want
+
+
+# -------------------------------------------------- fixed-shape feed (C19)
+
+def test_feed_hand_examples():
+    n = 0
+    for tl, pad, toks, row in G.rows("feed_examples.txt"):
+        t = G.ints(toks)
+        out = oracle.feed(np.array(t, np.int32), [0, len(t)], int(tl), int(pad))
+        assert out.shape == (1, int(tl))
+        assert out[0].tolist() == G.ints(row), (tl, pad, toks)
+        n += 1
+    assert n >= 6
+
+
+def test_feed_equal_length_rows_are_numpy_left_pad():
+    # Algorithm 2's B x T case: every row has T tokens; token_len > T pads
+    # each on the left
+    rng = np.random.default_rng(1)
+    B, T, TL = 7, 13, 20
+    ids = rng.integers(0, 4097, size=B * T).astype(np.int32)
+    out = oracle.feed(ids, np.arange(B + 1) * T, TL, 4098)
+    want = np.pad(ids.reshape(B, T), ((0, 0), (TL - T, 0)), constant_values=4098)
+    assert np.array_equal(out, want) and out.dtype == np.int64
+
+
+def test_feed_row_window():
+    ids = np.arange(10, dtype=np.int32)
+    offs = [0, 2, 2, 7, 10]
+    out = oracle.feed(ids, offs, 4, -1, row_begin=1, n_rows=2, dtype=np.int32)
+    assert out.tolist() == [[-1, -1, -1, -1], [2, 3, 4, 5]]
