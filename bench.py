@@ -351,6 +351,131 @@ def _overlap(torch, P, dev, d_bytes, d_offs, n, n_seq, flush_l2, steps: int = 10
                                      "offsets and emit kernels)"}}
 
 
+def _time_median(torch, fn, flush_l2, steps: int = 10, warm: int = 3):
+    """Median CUDA-event time (ms) of fn() on the current stream, L2 flushed
+    before each run (outside the events)."""
+    s = torch.cuda.current_stream()
+    for i in range(warm):
+        flush_l2(i)
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for i in range(steps):
+        flush_l2(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in evs)
+    return ms[len(ms) // 2]
+
+
+def _hbm(alg, ms, what):
+    peak, kind = _peaks()
+    ach = alg / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": kind, "algorithmic_bytes_per_step": alg, "duration": what}
+
+
+def _ktab(torch, P, dev, d_bytes, d_offs, n, n_seq, flush_l2):
+    """The 4096-sequence batch through a 5^6-entry k-mer table laid out like a
+    blocked 6-mer model's vocabulary (windows with N fall back to single
+    symbols): symbol pass, window offsets, count, scan and emit."""
+    import synth
+    lut, base = synth.kmer_vocab(6, seed=49)
+    s = torch.cuda.current_stream()
+    with P.Tokenizer(P.KMER_TABLE, k=6, kmer_lut=lut, base_ids=base) as tok:
+        ids, o, tot = tok.alloc_outputs(n, n_seq, device=dev)
+        ms = _time_median(torch, lambda: tok.encode(d_bytes, d_offs, ids, o, tot, stream=s), flush_l2)
+        tok.sync()
+        n_ids = int(tot[0].item())
+    alg = n + 4 * n_ids + 16 * (n_seq + 1)
+    return {"workload": "table-driven 6-mers (5^6 table, single-symbol fallback) of the same "
+                        "4096 sequences", "tokens": n_ids, "ms": ms,
+            "tokens_per_s": n_ids / (ms / 1e3),
+            "roofline": _hbm(alg, ms, "CUDA events around the whole encode (five launches)"),
+            "gpu_launches_per_step": 6}
+
+
+def _decode_rc_feed(torch, P, dev, d_bytes, d_offs, n, n_seq, flush_l2):
+    """Decode of the batch's 6-mer ids back to text, reverse complement of
+    its bytes, and the fixed-shape int64 feed of its ids (rows of 2048, the
+    micro-batched two-stream form with an embedding lookup as consumer)."""
+    s = torch.cuda.current_stream()
+    out = {}
+    with P.Tokenizer(P.KMER, k=6) as tok:
+        ids, o, tot = tok.alloc_outputs(n, n_seq, device=dev)
+        tok.encode(d_bytes, d_offs, ids, o, tot, stream=s)
+        tok.sync()
+        n_ids = int(tot[0].item())
+        ids = ids[:max(n_ids, 1)]
+        cap = P.binding.dnatok_max_decoded_bytes(tok.h, n_ids, n_seq)
+        text = torch.empty(cap, dtype=torch.uint8, device=dev)
+        bo = torch.empty(n_seq + 1, dtype=torch.int64, device=dev)
+        dt = torch.zeros(2, dtype=torch.int64, device=dev)
+        ms = _time_median(torch, lambda: tok.decode(ids, o, n_ids=n_ids, out=text, byte_offsets=bo,
+                                                    totals=dt, stream=s), flush_l2)
+        tok.sync()
+        n_text = int(dt[0].item())
+        alg = 4 * n_ids + n_text + 16 * (n_seq + 1)
+        out["decode_kmer6_4096seq"] = {
+            "workload": "6-mer ids of the 4096 sequences back to text", "ids": n_ids,
+            "bytes_out": n_text, "ms": ms, "ids_per_s": n_ids / (ms / 1e3),
+            "roofline": _hbm(alg, ms, "CUDA events around the decode (count, scan, emit)")}
+
+        rc = torch.empty(n, dtype=torch.uint8, device=dev)
+        ms = _time_median(torch, lambda: P.reverse_complement(d_bytes, d_offs, out=rc, stream=s),
+                          flush_l2)
+        alg = 2 * n + 8 * (n_seq + 1)
+        out["reverse_complement_4096seq"] = {
+            "workload": "reverse complement of every record of the 4096 sequences",
+            "bytes": n, "ms": ms, "bytes_per_s": n / (ms / 1e3),
+            "roofline": _hbm(alg, ms, "CUDA events around the one launch")}
+
+        T = 2048
+        fo = torch.empty((n_seq, T), dtype=torch.int64, device=dev)
+        ms = _time_median(torch, lambda: P.feed(ids, o, T, 4097, out=fo, stream=s), flush_l2)
+        lens = (o[1:] - o[:-1]).clamp(max=T)
+        kept = int(lens.sum().item())
+        alg = 4 * kept + 8 * n_seq * T + 16 * (n_seq + 1)
+        out["feed_int64_4096x2048"] = {
+            "workload": "left-padded int64 feed of the 6-mer ids, 4096 rows of 2048",
+            "elements": n_seq * T, "ms": ms, "elements_per_s": n_seq * T / (ms / 1e3),
+            "roofline": _hbm(alg, ms, "CUDA events around the one launch")}
+
+        # micro-batched feed into an embedding lookup (d = 256, bf16 table):
+        # two streams with ping-pong buffers vs the same work on one stream
+        rows = P.microbatch_rows(256, 1 << 18, T)
+        emb = torch.randn(4099, 256, device=dev, dtype=torch.bfloat16)
+        sink = torch.empty((rows, T, 256), device=dev, dtype=torch.bfloat16)
+
+        def consumer(row_begin, batch, stream):
+            with torch.cuda.stream(stream):
+                torch.index_select(emb, 0, batch.reshape(-1), out=sink[:batch.shape[0]].view(-1, 256))
+
+        fs, cs = torch.cuda.Stream(), torch.cuda.Stream()
+        res = {}
+        for name, feed_s in (("pipelined", fs), ("one_stream", cs)):
+            for rep in range(2):
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(cs)
+                fs.wait_event(a)
+                P.feed_pipeline(ids, o, T, 4097, rows, consumer, feed_stream=feed_s,
+                                consumer_stream=cs)
+                b.record(cs)
+                torch.cuda.synchronize()
+                res[name] = a.elapsed_time(b)
+        out["feed_pipeline_embedding"] = {
+            "workload": "4096 rows of 2048 int64 ids in micro-batches of %d rows into an "
+                        "embedding lookup (4099 x 256 bf16)" % rows,
+            "rows_per_batch": rows, "ms_pipelined": res["pipelined"],
+            "ms_one_stream": res["one_stream"]}
+    return out
+
+
 def _serving(torch, P, dev, seconds: float):
     """Config-5 request trace (Poisson 2000/s, 200 B-1 MB, 30% single-
     nucleotide / 50% 6-mer / 20% BPE with the 4096-merge table) replayed in
@@ -639,6 +764,9 @@ def run_gpu(args):
             line["batched"] = _batched(torch, P, dev, data, offs, d_bytes, d_offs)
             line["kmer6_overlap_4096seq"] = _overlap(torch, P, dev, d_bytes, d_offs, n_bytes,
                                                      n_seq, flush_l2)
+            line["kmer6_table_4096seq"] = _ktab(torch, P, dev, d_bytes, d_offs, n_bytes, n_seq,
+                                                flush_l2)
+            line.update(_decode_rc_feed(torch, P, dev, d_bytes, d_offs, n_bytes, n_seq, flush_l2))
             if args.serve_seconds > 0:
                 line["serving"] = _serving(torch, P, dev, args.serve_seconds)
         if args.stream_gib > 0:

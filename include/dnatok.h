@@ -21,6 +21,13 @@
  *                (L - k + 1 tokens, none when L < k; Sec. 1.1, Table 1), same
  *                ids and UNK as DNATOK_KMER.  One-shot encodes only (no
  *                host streams, no serving loop).
+ *   DNATOK_KMER_TABLE  table-driven non-overlapping k-mers (Algorithm 1
+ *                builds kmer_lut[0..5^k-1] over base-5 digits A0 C1 G2 T3
+ *                N4 and Algorithm 2 applies it as MapKmer): each whole window
+ *                of k kept symbols emits kmer_lut[sum_i 5^(k-1-i) d_i] when
+ *                that entry is >= 0, otherwise its k symbols one by one as
+ *                base_ids[d]; a tail of L mod k symbols emits base_ids[d]
+ *                for each.  1 <= k <= 10.  One-shot encodes only.
  *
  * Conventions for what the paper leaves open (identical in the CPU oracle):
  *   - case-insensitive; '\n' '\r' ' ' '\t' are dropped (they emit nothing and
@@ -84,7 +91,8 @@ typedef enum {
     DNATOK_CHAR = 0,
     DNATOK_KMER = 1,
     DNATOK_BPE = 2,
-    DNATOK_KMER_OVERLAP = 3
+    DNATOK_KMER_OVERLAP = 3,
+    DNATOK_KMER_TABLE = 4
 } dnatok_mode;
 typedef enum { DNATOK_RAW = 0, DNATOK_FASTA = 1 } dnatok_format;
 
@@ -99,19 +107,27 @@ typedef struct dnatok_handle dnatok_handle;
  *                 Algorithm 1 (e.g. its fixed DNA fallback A1 C2 G3 T4 N0).
  *   merges:       BPE only; n_merges host (left, right) int32 pairs in rank
  *                 order.  Valid iff for every rank r both ids are < 4 + r and
- *                 no pair repeats.  n_merges <= DNATOK_MAX_MERGES. */
+ *                 no pair repeats.  n_merges <= DNATOK_MAX_MERGES.
+ *   kmer_lut:     DNATOK_KMER_TABLE only; 5^k host int32 ids indexed by
+ *                 sum_i 5^(k-1-i) d_i (digits A0 C1 G2 T3, N-class 4), each
+ *                 >= -1; -1 = no entry (the window falls back to base_ids).
+ *   base_ids:     DNATOK_KMER_TABLE only; 5 host int32 ids >= 0 for the
+ *                 single symbols A C G T N. */
 typedef struct {
     const int32_t *ascii_lut256;
     const int32_t *merges;
     int32_t n_merges;
+    const int32_t *kmer_lut;
+    const int32_t *base_ids;
 } dnatok_tables;
 
 #define DNATOK_MAX_K 15
+#define DNATOK_MAX_K_TABLE 10
 #define DNATOK_MAX_MERGES 16384
 
 /* Create a tokenizer on the current CUDA device.  mode/k/tables as above (k
- * is ignored unless mode is DNATOK_KMER or DNATOK_KMER_OVERLAP;
- * 1 <= k <= 15).  fmt selects how
+ * is ignored unless mode is DNATOK_KMER, DNATOK_KMER_OVERLAP (1 <= k <= 15)
+ * or DNATOK_KMER_TABLE (1 <= k <= 10)).  fmt selects how
  * records are found by dnatok_encode and the stream API.  Tables are
  * validated and copied to device memory.  On success *out owns its device
  * tables and workspace; release it with dnatok_destroy. */
@@ -306,6 +322,108 @@ DNATOK_API dnatok_status dnatok_server_release(dnatok_server *s, uint64_t req_id
 DNATOK_API dnatok_status dnatok_server_stats(dnatok_server *s, dnatok_server_counters *out);
 /* Stop the worker, wait for the device, free everything. */
 DNATOK_API void dnatok_server_destroy(dnatok_server *s);
+
+/* ---------------------------------------------------------------- decode */
+
+/*
+ * Token ids back to text on the device (Sec. 4, "Decode Operations": an
+ * inverse vocabulary table maps each id to its character span).  Per mode:
+ *   DNATOK_CHAR   id v -> the first byte b with lut[b] == v in the order
+ *                 "ACGTN", 'A'..'Z', 'a'..'z', then 0..255;
+ *   DNATOK_KMER   id < 4^k -> its k bases (A C G T); UNK = 4^k -> one '?';
+ *   DNATOK_KMER_OVERLAP  per record: the first token as DNATOK_KMER, every
+ *                 later one its last base ('?' for UNK);
+ *   DNATOK_BPE    the bases the merge table expands the id to; N_ID -> 'N';
+ *   DNATOK_KMER_TABLE  the k digits ("ACGTN") of the smallest window index
+ *                 whose kmer_lut entry is the id, else the symbol of the
+ *                 smallest digit d with base_ids[d] == id.
+ * An id with no inverse (out of range, PAD, a table gap) writes nothing and
+ * is counted in totals_d[1].
+ *   ids_d          n_ids int32 (DEVICE).
+ *   id_offsets_d   n_seq + 1 non-decreasing int64 (DEVICE) with [0] = 0 and
+ *                  [n_seq] = n_ids, as written by dnatok_encode; a malformed
+ *                  array gives wrong record offsets but no access outside
+ *                  the buffers.
+ *   bytes_out_d    bytes_capacity >= dnatok_max_decoded_bytes (DEVICE;
+ *                  checked here, DNATOK_ERR_CAPACITY).
+ *   byte_offsets_d n_seq + 1 int64 (DEVICE): record r's text is
+ *                  bytes_out[byte_offsets[r] .. byte_offsets[r+1]).
+ *   totals_d       NULL or 2 int64 (DEVICE): {bytes written, ids without an
+ *                  inverse}.
+ * Asynchronous on `stream`.  The handle builds its inverse table at the
+ * first call (synchronous upload); DNATOK_ERR_TABLE if it would exceed 2^24
+ * ids or 256 MB of text.
+ */
+DNATOK_API dnatok_status dnatok_max_decoded_bytes(dnatok_handle *h, int64_t n_ids, int64_t n_seq,
+                                                  int64_t *cap);
+DNATOK_API dnatok_status dnatok_decode(dnatok_handle *h, const int32_t *ids_d, int64_t n_ids,
+                                       const int64_t *id_offsets_d, int64_t n_seq,
+                                       uint8_t *bytes_out_d, int64_t bytes_capacity,
+                                       int64_t *byte_offsets_d, int64_t *totals_d,
+                                       dnatok_cuda_stream stream);
+
+/* ------------------------------------------------------ reverse complement */
+
+/*
+ * Reverse complement of every record (Sec. 4, "Integration with Data
+ * Augmentation": the augmentation the paper leaves to future GPU work):
+ * out[s + e - 1 - i] = comp(in[i]) for i in [s, e) = [seq_offsets[r],
+ * seq_offsets[r+1]); comp swaps A/T, C/G, R/Y, K/M, B/V, D/H in either case
+ * and keeps every other byte (S, W, N, separators, ...).  Needs no handle.
+ *   bytes_d, out_d  n_bytes each (DEVICE); out must not overlap the input.
+ *   seq_offsets_d   n_seq + 1 non-decreasing int64 (DEVICE), [0] = 0,
+ *                   [n_seq] = n_bytes; positions a malformed array would map
+ *                   outside [0, n_bytes) are left unwritten.
+ * Asynchronous on `stream`; DNATOK_ERR_ARG for bad arguments.
+ */
+DNATOK_API dnatok_status dnatok_reverse_complement(const uint8_t *bytes_d, int64_t n_bytes,
+                                                   const int64_t *seq_offsets_d, int64_t n_seq,
+                                                   uint8_t *out_d, dnatok_cuda_stream stream);
+
+/* ------------------------------------------------------- fixed-shape feed */
+
+/*
+ * Fixed-shape model feed (Algorithm 2: rows left-padded with id_pad to
+ * token_len so each row's own tokens stay right-aligned; Sec. 2.2, int32
+ * staging promoted on the device to the int64 an embedding call takes).
+ * Row i of out (n_rows x token_len, row-major) is record row_begin + i of
+ * (ids_d, id_offsets_d): a record of m <= token_len ids is written after
+ * token_len - m copies of id_pad; a longer record keeps its first token_len
+ * ids.  out_bytes is 4 (int32) or 8 (int64).  Needs no handle.  All
+ * pointers DEVICE; asynchronous on `stream`; DNATOK_ERR_ARG for bad
+ * arguments (id_pad must fit the output type).
+ */
+DNATOK_API dnatok_status dnatok_feed(const int32_t *ids_d, const int64_t *id_offsets_d,
+                                     int64_t row_begin, int64_t n_rows, int64_t token_len,
+                                     int64_t id_pad, void *out_d, int32_t out_bytes,
+                                     dnatok_cuda_stream stream);
+
+/* Algorithm 2's micro-batch size: min(emb_batch_cap, max(1, floor(
+ * tokens_per_call / token_len))) rows. */
+DNATOK_API dnatok_status dnatok_microbatch_rows(int64_t emb_batch_cap, int64_t tokens_per_call,
+                                                int64_t token_len, int64_t *rows);
+
+/*
+ * Micro-batched feed on two streams (Sec. 2.2, "Pipelined streaming": ping-
+ * pong device buffers so that preparing micro-batch n+1 overlaps the
+ * embedding compute of micro-batch n).  For each micro-batch of up to
+ * rows_per_batch rows, dnatok_feed writes it into buf[i % 2] on
+ * feed_stream; consumer_stream then waits for it and `consumer` is called
+ * (on this host thread) to enqueue its work on consumer_stream; feed_stream
+ * waits for that work before it reuses the buffer.  Each buffer holds
+ * rows_per_batch x token_len elements of out_bytes.  Returns once
+ * everything is enqueued; a nonzero return from `consumer` stops the loop
+ * with DNATOK_ERR_STATE.
+ */
+typedef int (*dnatok_feed_consumer)(void *user, int64_t row_begin, int64_t n_rows, void *batch_d,
+                                    dnatok_cuda_stream consumer_stream);
+DNATOK_API dnatok_status dnatok_feed_pipeline(const int32_t *ids_d, const int64_t *id_offsets_d,
+                                              int64_t n_rows, int64_t token_len, int64_t id_pad,
+                                              int32_t out_bytes, int64_t rows_per_batch,
+                                              void *buf0_d, void *buf1_d,
+                                              dnatok_cuda_stream feed_stream,
+                                              dnatok_cuda_stream consumer_stream,
+                                              dnatok_feed_consumer consumer, void *user);
 
 /* ------------------------------------------------------ no allocation */
 

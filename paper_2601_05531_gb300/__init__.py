@@ -8,11 +8,12 @@ tokenization runs in the library's CUDA kernels).
 from __future__ import annotations
 
 from . import binding
-from .binding import (BPE, CHAR, END_OF_STREAM, FASTA, HOST_PINNED, KMER, KMER_OVERLAP, NEW_RECORD, RAW,
-                      DnatokError)
+from .binding import (BPE, CHAR, END_OF_STREAM, FASTA, HOST_PINNED, KMER, KMER_OVERLAP, KMER_TABLE,
+                      NEW_RECORD, RAW, DnatokError)
 
-__all__ = ["binding", "Tokenizer", "CHAR", "KMER", "KMER_OVERLAP", "BPE", "RAW", "FASTA", "DnatokError",
-           "END_OF_STREAM", "NEW_RECORD", "HOST_PINNED", "build"]
+__all__ = ["binding", "Tokenizer", "CHAR", "KMER", "KMER_OVERLAP", "KMER_TABLE", "BPE", "RAW", "FASTA",
+           "DnatokError", "END_OF_STREAM", "NEW_RECORD", "HOST_PINNED", "build", "reverse_complement",
+           "feed", "microbatch_rows", "feed_pipeline"]
 
 
 def build(force: bool = False) -> str:
@@ -28,14 +29,17 @@ def _stream_ptr(stream) -> int:
 
 
 class Tokenizer:
-    """One library handle.  mode: CHAR / KMER / BPE; fmt: RAW / FASTA."""
+    """One library handle.  mode: CHAR / KMER / KMER_OVERLAP / KMER_TABLE /
+    BPE; fmt: RAW / FASTA."""
 
-    def __init__(self, mode: int, k: int = 1, lut=None, merges=None, fmt: int = RAW):
+    def __init__(self, mode: int, k: int = 1, lut=None, merges=None, fmt: int = RAW,
+                 kmer_lut=None, base_ids=None):
         import torch  # noqa: F401  (initializes the CUDA context the library uses)
         torch.cuda.init()
         self.mode, self.k, self.fmt = mode, k, fmt
         self.n_merges = 0 if merges is None else len(merges)
-        self.h = binding.dnatok_create(mode, k, lut=lut, merges=merges, fmt=fmt)
+        self.h = binding.dnatok_create(mode, k, lut=lut, merges=merges, fmt=fmt,
+                                       kmer_lut=kmer_lut, base_ids=base_ids)
 
     def close(self):
         if getattr(self, "h", None):
@@ -95,6 +99,26 @@ class Tokenizer:
     def sync(self, stream=None):
         binding.dnatok_sync(self.h, _stream_ptr(stream))
 
+    def decode(self, ids, id_offsets, n_ids: int | None = None, out=None, byte_offsets=None,
+               totals=None, stream=None):
+        """Asynchronous decode of CUDA int32 ids with their record offsets
+        (CUDA int64, n_seq + 1).  Returns (bytes, byte_offsets, totals) with
+        totals = [bytes written, ids without text] once the stream gets there."""
+        import torch
+        n_ids = int(ids.numel()) if n_ids is None else n_ids
+        n_seq = int(id_offsets.numel()) - 1
+        if out is None:
+            cap = binding.dnatok_max_decoded_bytes(self.h, n_ids, n_seq)
+            out = torch.empty(max(cap, 1), dtype=torch.uint8, device=ids.device)
+        if byte_offsets is None:
+            byte_offsets = torch.empty(n_seq + 1, dtype=torch.int64, device=ids.device)
+        if totals is None:
+            totals = torch.zeros(2, dtype=torch.int64, device=ids.device)
+        binding.dnatok_decode(self.h, ids.data_ptr() if n_ids else 0, n_ids, id_offsets.data_ptr(),
+                              n_seq, out.data_ptr(), out.numel(), byte_offsets.data_ptr(),
+                              totals.data_ptr(), _stream_ptr(stream))
+        return out, byte_offsets, totals
+
     # ---------------------------------------------------------------- streams
     def stream_open(self, ids, offsets, chunk_bytes: int = 0, n_slots: int = 0,
                     overlap: bool = True):
@@ -140,3 +164,62 @@ class Tokenizer:
         self.sync()
         n_ids, n_rec = (int(x) for x in tot.cpu().tolist())
         return ids[:n_ids].cpu().numpy(), offs[: n_rec + 1].cpu().numpy()
+
+
+def reverse_complement(data, seq_offsets, out=None, stream=None):
+    """Reverse complement of every record of a CUDA uint8 tensor (records by
+    seq_offsets, CUDA int64).  Asynchronous; returns the output tensor."""
+    import torch
+    n = int(data.numel())
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.uint8, device=data.device)
+    binding.dnatok_reverse_complement(data.data_ptr() if n else 0, n, seq_offsets.data_ptr(),
+                                      int(seq_offsets.numel()) - 1, out.data_ptr(),
+                                      _stream_ptr(stream))
+    return out[:n] if n else out[:0]
+
+
+def feed(ids, id_offsets, token_len: int, id_pad: int, dtype=None, row_begin: int = 0,
+         n_rows: int | None = None, out=None, stream=None):
+    """Fixed-shape (n_rows, token_len) feed of records row_begin.. of (ids,
+    id_offsets): left-padded with id_pad, longer records cut to their first
+    token_len ids; dtype torch.int64 (default) or torch.int32."""
+    import torch
+    dtype = torch.int64 if dtype is None else dtype
+    if n_rows is None:
+        n_rows = int(id_offsets.numel()) - 1 - row_begin
+    if out is None:
+        out = torch.empty((n_rows, token_len), dtype=dtype, device=ids.device)
+    binding.dnatok_feed(ids.data_ptr(), id_offsets.data_ptr(), row_begin, n_rows, token_len,
+                        id_pad, out.data_ptr(), out.element_size(), _stream_ptr(stream))
+    return out
+
+
+def microbatch_rows(emb_batch_cap: int, tokens_per_call: int, token_len: int) -> int:
+    return binding.dnatok_microbatch_rows(emb_batch_cap, tokens_per_call, token_len)
+
+
+def feed_pipeline(ids, id_offsets, token_len: int, id_pad: int, rows_per_batch: int, consumer,
+                  dtype=None, feed_stream=None, consumer_stream=None):
+    """Micro-batched feed on two streams with ping-pong buffers.  For every
+    micro-batch consumer(row_begin, batch, stream) is called with a
+    (rows, token_len) tensor view and the torch stream it must enqueue its
+    work on (e.g. an embedding lookup); the buffer is reused only after that
+    work.  Returns once everything is enqueued."""
+    import torch
+    dtype = torch.int64 if dtype is None else dtype
+    n_rows = int(id_offsets.numel()) - 1
+    bufs = [torch.empty((rows_per_batch, token_len), dtype=dtype, device=ids.device)
+            for _ in range(2)]
+    fs = feed_stream or torch.cuda.Stream(device=ids.device)
+    cs = consumer_stream or torch.cuda.current_stream(ids.device)
+    by_addr = {b.data_ptr(): b for b in bufs}
+
+    def _consume(row_begin, n, addr, _stream):
+        consumer(row_begin, by_addr[addr][:n], cs)
+
+    binding.dnatok_feed_pipeline(ids.data_ptr(), id_offsets.data_ptr(), n_rows, token_len, id_pad,
+                                 bufs[0].element_size(), rows_per_batch, bufs[0].data_ptr(),
+                                 bufs[1].data_ptr(), int(fs.cuda_stream), int(cs.cuda_stream),
+                                 _consume)
+    return bufs, fs

@@ -13,7 +13,7 @@ import os
 
 from . import _build
 
-CHAR, KMER, BPE, KMER_OVERLAP = 0, 1, 2, 3  # dnatok_mode
+CHAR, KMER, BPE, KMER_OVERLAP, KMER_TABLE = 0, 1, 2, 3, 4  # dnatok_mode
 RAW, FASTA = 0, 1
 
 OK, PENDING = 0, 1
@@ -68,7 +68,14 @@ class LaunchCfg(ctypes.Structure):
 
 class Tables(ctypes.Structure):
     _fields_ = [("ascii_lut256", ctypes.POINTER(ctypes.c_int32)),
-                ("merges", ctypes.POINTER(ctypes.c_int32)), ("n_merges", ctypes.c_int32)]
+                ("merges", ctypes.POINTER(ctypes.c_int32)), ("n_merges", ctypes.c_int32),
+                ("kmer_lut", ctypes.POINTER(ctypes.c_int32)),
+                ("base_ids", ctypes.POINTER(ctypes.c_int32))]
+
+
+# int consumer(void *user, int64 row_begin, int64 n_rows, void *batch_d, cudaStream_t stream)
+FEED_CONSUMER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                 ctypes.c_void_p, ctypes.c_void_p)
 
 
 _lib = None
@@ -128,6 +135,13 @@ def lib():
             "dnatok_server_destroy": (None, [_P]),
             "dnatok_encode_kmer_noalloc": (_ST, [ctypes.c_int, _P, _I64, _P, _I64, _P, _I64, _P,
                                                  _I64, _P, _P]),
+            "dnatok_max_decoded_bytes": (_ST, [_P, _I64, _I64, ctypes.POINTER(_I64)]),
+            "dnatok_decode": (_ST, [_P, _P, _I64, _P, _I64, _P, _I64, _P, _P, _P]),
+            "dnatok_reverse_complement": (_ST, [_P, _I64, _P, _I64, _P, _P]),
+            "dnatok_feed": (_ST, [_P, _P, _I64, _I64, _I64, _I64, _P, ctypes.c_int32, _P]),
+            "dnatok_microbatch_rows": (_ST, [_I64, _I64, _I64, ctypes.POINTER(_I64)]),
+            "dnatok_feed_pipeline": (_ST, [_P, _P, _I64, _I64, _I64, ctypes.c_int32, _I64, _P, _P,
+                                           _P, _P, FEED_CONSUMER, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -151,12 +165,19 @@ def check(st: int, h=None) -> int:
 
 # ------------------------------------------------------------------ wrappers
 
-def dnatok_create(mode: int, k: int = 1, lut=None, merges=None, fmt: int = RAW):
+def dnatok_create(mode: int, k: int = 1, lut=None, merges=None, fmt: int = RAW, kmer_lut=None,
+                  base_ids=None):
     """Returns the handle (an opaque address).  lut: 256 ints or None;
-    merges: (M, 2) ints or None."""
+    merges: (M, 2) ints or None; kmer_lut (5^k ints) and base_ids (5 ints):
+    KMER_TABLE only."""
     import numpy as np
     t = Tables()
     keep = []
+    for name, arr in (("kmer_lut", kmer_lut), ("base_ids", base_ids)):
+        if arr is not None:
+            a = np.ascontiguousarray(np.asarray(arr, dtype=np.int32).reshape(-1))
+            keep.append(a)
+            setattr(t, name, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     if lut is not None:
         a = np.ascontiguousarray(np.asarray(lut, dtype=np.int32).reshape(256))
         keep.append(a)
@@ -384,3 +405,51 @@ def dnatok_encode_kmer_noalloc(k: int, bytes_d: int, n_bytes: int, seq_offsets_d
                % NOALLOC_MAX_BYTES, -4: "CUDA call failed"}.get(st, "error")
         raise DnatokError(st, "dnatok_encode_kmer_noalloc: " + why)
     return st
+
+
+def dnatok_max_decoded_bytes(h, n_ids: int, n_seq: int) -> int:
+    c = _I64()
+    check(lib().dnatok_max_decoded_bytes(h, n_ids, n_seq, ctypes.byref(c)), h)
+    return c.value
+
+
+def dnatok_decode(h, ids_d: int, n_ids: int, id_offsets_d: int, n_seq: int, bytes_out_d: int,
+                  bytes_capacity: int, byte_offsets_d: int, totals_d: int, stream: int) -> int:
+    return check(lib().dnatok_decode(h, ids_d, n_ids, id_offsets_d, n_seq, bytes_out_d,
+                                     bytes_capacity, byte_offsets_d, totals_d, stream), h)
+
+
+def dnatok_reverse_complement(bytes_d: int, n_bytes: int, seq_offsets_d: int, n_seq: int,
+                              out_d: int, stream: int) -> int:
+    return check(lib().dnatok_reverse_complement(bytes_d, n_bytes, seq_offsets_d, n_seq, out_d,
+                                                 stream))
+
+
+def dnatok_feed(ids_d: int, id_offsets_d: int, row_begin: int, n_rows: int, token_len: int,
+                id_pad: int, out_d: int, out_bytes: int, stream: int) -> int:
+    return check(lib().dnatok_feed(ids_d, id_offsets_d, row_begin, n_rows, token_len, id_pad,
+                                   out_d, out_bytes, stream))
+
+
+def dnatok_microbatch_rows(emb_batch_cap: int, tokens_per_call: int, token_len: int) -> int:
+    r = _I64()
+    check(lib().dnatok_microbatch_rows(emb_batch_cap, tokens_per_call, token_len,
+                                       ctypes.byref(r)))
+    return r.value
+
+
+def dnatok_feed_pipeline(ids_d: int, id_offsets_d: int, n_rows: int, token_len: int, id_pad: int,
+                         out_bytes: int, rows_per_batch: int, buf0_d: int, buf1_d: int,
+                         feed_stream: int, consumer_stream: int, consumer) -> int:
+    """consumer(row_begin, n_rows, batch_address, consumer_stream) -> None;
+    an exception stops the pipeline (ERR_STATE)."""
+    def _cb(user, row_begin, n, batch, stream):
+        try:
+            consumer(int(row_begin), int(n), int(batch or 0), int(stream or 0))
+            return 0
+        except Exception:  # reported as ERR_STATE by the library
+            return 1
+    cb = FEED_CONSUMER(_cb)
+    return check(lib().dnatok_feed_pipeline(ids_d, id_offsets_d, n_rows, token_len, id_pad,
+                                            out_bytes, rows_per_batch, buf0_d, buf1_d,
+                                            feed_stream, consumer_stream, cb, None))

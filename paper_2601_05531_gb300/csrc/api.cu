@@ -169,16 +169,37 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
     if (!out) return fail(nullptr, DNATOK_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (mode != DNATOK_CHAR && mode != DNATOK_KMER && mode != DNATOK_BPE &&
-        mode != DNATOK_KMER_OVERLAP)
+        mode != DNATOK_KMER_OVERLAP && mode != DNATOK_KMER_TABLE)
         return fail(nullptr, DNATOK_ERR_ARG, "unknown mode");
     if (fmt != DNATOK_RAW && fmt != DNATOK_FASTA)
         return fail(nullptr, DNATOK_ERR_ARG, "unknown format");
     if ((mode == DNATOK_KMER || mode == DNATOK_KMER_OVERLAP) && (k < 1 || k > DNATOK_MAX_K))
         return fail(nullptr, DNATOK_ERR_ARG, "k must be in [1, 15]");
+    long long n_index = 0;
+    if (mode == DNATOK_KMER_TABLE) {
+        if (k < 1 || k > DNATOK_MAX_K_TABLE)
+            return fail(nullptr, DNATOK_ERR_ARG, "k must be in [1, 10] for DNATOK_KMER_TABLE");
+        if (!tables || !tables->kmer_lut || !tables->base_ids)
+            return fail(nullptr, DNATOK_ERR_TABLE, "DNATOK_KMER_TABLE needs kmer_lut and base_ids");
+        n_index = 1;
+        for (int i = 0; i < k; ++i) n_index *= 5;
+        for (long long i = 0; i < n_index; ++i)
+            if (tables->kmer_lut[i] < -1)
+                return fail(nullptr, DNATOK_ERR_TABLE, "kmer_lut ids must be >= -1");
+        for (int d = 0; d < 5; ++d)
+            if (tables->base_ids[d] < 0)
+                return fail(nullptr, DNATOK_ERR_TABLE, "base_ids must be >= 0");
+    }
     dnatok_handle *h = new (std::nothrow) dnatok_handle();
     if (!h) return fail(nullptr, DNATOK_ERR_NOMEM, "host allocation failed");
     h->mode = mode;
-    h->k = (mode == DNATOK_KMER || mode == DNATOK_KMER_OVERLAP) ? k : 1;
+    h->k = (mode == DNATOK_KMER || mode == DNATOK_KMER_OVERLAP || mode == DNATOK_KMER_TABLE) ? k : 1;
+    if (mode == DNATOK_KMER_TABLE) {
+        h->klut_host.assign(tables->kmer_lut, tables->kmer_lut + n_index);
+        for (int d = 0; d < 5; ++d) h->base_ids[d] = tables->base_ids[d];
+    }
+    if (mode == DNATOK_BPE && tables && tables->merges && tables->n_merges > 0)
+        h->merges_host.assign(tables->merges, tables->merges + 2 * (size_t)tables->n_merges);
     h->fmt = fmt;
     if (mode == DNATOK_CHAR && tables && tables->ascii_lut256) {
         for (int b = 0; b < 256; ++b) {
@@ -203,6 +224,12 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_gate, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(h->d_gate, 0, sizeof(unsigned));
+    if (e == cudaSuccess && mode == DNATOK_KMER_TABLE) {
+        e = cudaMalloc(&h->d_klut, sizeof(int32_t) * (size_t)n_index);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->d_klut, h->klut_host.data(), sizeof(int32_t) * (size_t)n_index,
+                           cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         std::string m = std::string("CUDA setup failed: ") + cudaGetErrorString(e);
         dnatok_destroy(h);
@@ -230,6 +257,8 @@ void dnatok_destroy(dnatok_handle *h) {
     stream_destroy(h);
     bpe_destroy(h);
     ovl_destroy(h);
+    dec_destroy(h);
+    cudaFree(h->d_klut);
     cudaFree(h->d_lut);
     cudaFree(h->d_desc);
     cudaFree(h->d_tile_rec);
@@ -260,7 +289,7 @@ dnatok_status dnatok_reserve(dnatok_handle *h, int64_t max_bytes, int64_t max_se
     dnatok_status st = ensure_workspace(h, max_bytes, max_seq + 1, h->shape, 0);
     if (st != DNATOK_OK) return st;
     if (h->mode == DNATOK_BPE) return bpe_reserve(h, max_bytes);
-    if (h->mode == DNATOK_KMER_OVERLAP)
+    if (h->mode == DNATOK_KMER_OVERLAP || h->mode == DNATOK_KMER_TABLE)
         return ovl_reserve(h, max_bytes, h->fmt == DNATOK_RAW ? max_seq + 1 : max_bytes + 2, 0);
     return DNATOK_OK;
 }
@@ -298,6 +327,9 @@ dnatok_status dnatok_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_
     if (h->mode == DNATOK_KMER_OVERLAP)
         return ovl_encode(h, bytes_d, n_bytes, seq_offsets_d, n_seq, ids_out_d, ids_capacity,
                           id_offsets_d, offsets_capacity, totals_d, s);
+    if (h->mode == DNATOK_KMER_TABLE)
+        return ktab_encode(h, bytes_d, n_bytes, seq_offsets_d, n_seq, ids_out_d, ids_capacity,
+                           id_offsets_d, offsets_capacity, totals_d, s);
     const int mode = (h->mode == DNATOK_CHAR) ? MODE_CHAR : MODE_KMER;
     if (h->fmt == DNATOK_RAW)
         return run_tile_encode(h, mode, h->k, BSRC_LIST, bytes_d, n_bytes,

@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(256) bpe_emit_kernel(BpeTables G, bool smem, B
                 m &= m - 1;
                 const long long j = s + 32ll * w + b;
                 const unsigned id = (W.sym[j] >= 4) ? (unsigned)T.V : token_at(T, W.sym, j, W.len[j]);
-                if (pos < W.out_cap) W.out[pos] = (int)id;
+                if (pos >= 0 && pos < W.out_cap) W.out[pos] = (int)id;
                 ++pos;
             }
             out += __shfl_sync(0xffffffffu, x, 31);
@@ -1074,6 +1074,9 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     bpe_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, s>>>(W);
     bpe_scan_top<<<1, kScanThreads, 0, s>>>(W, nblk);
     bpe_scan_down<<<(unsigned)nblk, kScanThreads, 0, s>>>(W);
+    // the emit takes its positions from the scans: launch it only if they launched
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(h, e, "BPE kernel launch");
     bpe_emit_kernel<<<g256, 256, dyn, s>>>(T, use_smem, W);
     const long long nrec_bound = raw ? n_seq + 1 : offsets_capacity;
     long long og = (nrec_bound + 255) / 256;

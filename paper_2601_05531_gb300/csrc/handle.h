@@ -50,6 +50,23 @@ struct dnatok_handle {
     BpeState *bpe = nullptr;
     OvlState *ovl = nullptr;
 
+    // table-driven k-mers: kmer_lut (5^k ids) on the device, the single-symbol ids
+    int32_t *d_klut = nullptr;
+    std::vector<int32_t> klut_host;
+    int32_t base_ids[5] = {0, 1, 2, 3, 4};
+    std::vector<int32_t> merges_host;  // BPE table, kept for the decode table
+
+    // decode: inverse vocabulary (text of id v = text[off[v] .. off[v+1])),
+    // built at the first dnatok_decode; dec_v < 0 until then
+    int32_t *d_dec_off = nullptr;
+    uint8_t *d_dec_text = nullptr;
+    long long dec_v = -1;
+    int dec_max_len = 0;
+    // per-tile sums of the decode passes
+    long long *d_dsum = nullptr;
+    long long *d_dinv = nullptr;
+    long long dsum_cap = 0;
+
     std::string last_error;
 };
 
@@ -95,7 +112,7 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
                          int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
                          int64_t *totals_d, cudaStream_t s);
 
-// overlapping k-mers (ovl.cu)
+// overlapping and table-driven k-mers on the symbol pass (ovl.cu)
 void ovl_destroy(dnatok_handle *h);
 dnatok_status ovl_reserve(dnatok_handle *h, long long max_bytes, long long max_offsets,
                           cudaStream_t s);
@@ -103,6 +120,28 @@ dnatok_status ovl_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
                          const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
                          int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
                          int64_t *totals_d, cudaStream_t s);
+dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
+                          const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
+                          int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
+                          int64_t *totals_d, cudaStream_t s);
+
+// Exclusive scan of per-tile sums in place, one block of kTileScanThreads
+// (ovl.cu).  n_items items in tiles of items_per_tile; keys (n_rec + 1
+// non-decreasing item offsets of the records) give the records with no item
+// left (keys[r] >= n_items), whose rec_out entries get the total.
+// totals_out (NULL or 2): {total, sum of tinv (NULL: n_rec)}.  n_rec comes
+// from n_rec_dev when not NULL; n_items from n_items_dev when not NULL, else
+// n_items_host when >= 0, else keys[n_rec].  Does nothing once the device
+// status word holds an error.
+__global__ void tile_scan_kernel(long long *tsum, const long long *tinv, const long long *keys,
+                                 const long long *n_rec_dev, long long n_rec_host,
+                                 const long long *n_items_dev, long long n_items_host,
+                                 int items_per_tile, long long *rec_out, long long *totals_out,
+                                 const int *status);
+constexpr int kTileScanThreads = 1024;
+
+// decode tables (decode.cu)
+void dec_destroy(dnatok_handle *h);
 
 // host-streamed pipeline (stream.cu)
 void stream_destroy(dnatok_handle *h);

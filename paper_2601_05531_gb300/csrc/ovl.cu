@@ -1,21 +1,37 @@
-// ovl.cu -- overlapping k-mers with stride 1: every window of k consecutive
-// kept bases of a record is a token, adjacent tokens share k - 1 bases, and a
-// record of L kept bases gives max(0, L - k + 1) tokens (Sec. 1.1 and
-// Table 1: "overlapping k-mer tokenization with stride 1" yields L - k + 1
-// tokens).  Ids are the closed form of the non-overlapping mode,
-// sum_i 4^(k-1-i) * code(b_i) with A0 C1 G2 T3, and UNK = 4^k for a window
-// holding an N-class base.
+// ovl.cu -- the modes built on the symbol pass: overlapping k-mers with
+// stride 1 and table-driven k-mers.
 //
-// Three launches per encode:
+// Overlapping k-mers: every window of k consecutive kept bases of a record is
+// a token, adjacent tokens share k - 1 bases, and a record of L kept bases
+// gives max(0, L - k + 1) tokens (Sec. 1.1 and Table 1: overlapping k-mer
+// tokenization with stride 1 yields L - k + 1 tokens).  Ids are the closed
+// form of the non-overlapping mode, sum_i 4^(k-1-i) * code(b_i) with A0 C1 G2
+// T3, and UNK = 4^k for a window holding an N-class base.  Three launches:
 //   1. the symbol pass (the tile kernel in MODE_SYM, or its direct path): one
 //      byte per kept base (0..3, 4 for N-class) and the record starts in
 //      symbols, written to the caller's id_offsets (FASTA headers and
 //      separators already removed);
-//   2. ovl_offsets_kernel (one block): copies those starts to the handle's
-//      workspace and rewrites id_offsets in place with the token offsets;
+//   2. offsets_kernel<kOffsetsTokens> (one block): copies those starts to the
+//      handle's workspace and rewrites id_offsets in place with the token
+//      offsets;
 //   3. ovl_emit_kernel: each CTA walks a contiguous run of 4096-symbol tiles,
 //      staging the tile's symbols (plus k - 1) and a window of its records
 //      in shared memory; consecutive threads write consecutive ids.
+//
+// Table-driven k-mers (Algorithm 1 builds kmer_lut[0..5^k-1] over base-5
+// digits, Algorithm 2 applies it as MapKmer): the symbols of a record are cut
+// into windows of k from its start; a whole window emits kmer_lut[index] or,
+// when that entry is -1, its k symbols through base_ids; a tail of L mod k
+// symbols goes through base_ids.  A window's token count (1, k or the tail
+// length) depends on the table, so the positions need a scan:
+//   1. the symbol pass, as above;
+//   2. offsets_kernel<kOffsetsWindows>: record starts to the workspace and
+//      the window offsets wpre[r] = sum of ceil(L / k) over earlier records;
+//   3. ktab_tile_kernel<K, false>: per tile of 1024 windows, its token count;
+//   4. tile_scan_kernel (one block): exclusive scan of the tile counts, the
+//      totals and the offsets of records with no window left;
+//   5. ktab_tile_kernel<K, true>: recounts, scans inside the block and writes
+//      the ids and the record offsets.
 #include <cstring>
 
 #include "handle.h"
@@ -25,11 +41,16 @@ struct OvlState {
     uint8_t *d_sym = nullptr;   // one symbol per kept base
     long long cap_sym = 0;
     long long *d_srec = nullptr;  // record starts in symbols (n_rec + 1)
+    long long *d_wpre = nullptr;  // table-driven k-mers: window offsets (n_rec + 1)
     long long cap_srec = 0;
     long long *d_tot = nullptr;   // {symbols, records} of the symbol pass
+    long long *d_tsum = nullptr;  // table-driven k-mers: per-tile token counts
+    long long cap_tsum = 0;
 };
 
 namespace {
+
+using namespace dnatok;
 
 constexpr int kOT = 4096;          // symbols per emit tile
 constexpr int kOThreads = 256;
@@ -50,20 +71,43 @@ __device__ long long ovl_find(const long long *srec, long long n_rec, long long 
     return lo;
 }
 
-// Token offsets from the symbol pass's record starts, in place.
-__global__ void __launch_bounds__(kOPlanThreads) ovl_offsets_kernel(long long *offs, long long *srec,
-                                                                    const long long *tot, int k,
-                                                                    long long *totals_out) {
+enum { kOffsetsTokens = 0, kOffsetsWindows = 1 };
+
+// From the symbol pass's record starts (offs, n_rec + 1 entries): copy them
+// to srec and write, for every record, the running sum of f(L) over earlier
+// records -- f(L) = max(0, L - k + 1) tokens in place into offs
+// (kOffsetsTokens), or ceil(L / k) windows into wpre (kOffsetsWindows).  If
+// the records found do not fit offs_cap entries the pass records
+// DEV_CAPACITY, zeroes the symbol pass's record count (so the later kernels
+// do nothing) and reports {0, n_rec} in totals_out.
+template <int KIND>
+__global__ void __launch_bounds__(kOPlanThreads) offsets_kernel(long long *offs, long long *srec,
+                                                                long long *wpre, long long *tot,
+                                                                int k, long long offs_cap,
+                                                                long long *totals_out, int *status) {
     constexpr int kPer = kOPlanTile / kOPlanThreads;
     __shared__ long long s_v[kOPlanTile + 1];
     __shared__ long long wsum[kOPlanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = tot[1];  // records
+    if (n + 1 > offs_cap) {
+        __syncthreads();  // every thread has read tot[1]
+        if (tid == 0) {
+            tot[1] = 0;
+            set_dev_status(status, DEV_CAPACITY);
+            if (totals_out) {
+                totals_out[0] = 0;
+                totals_out[1] = n;
+            }
+        }
+        return;
+    }
+    long long *dst = KIND == kOffsetsTokens ? offs : wpre;
     long long carry = 0;
     for (long long r0 = 0; r0 < n; r0 += kOPlanTile) {
         const int cnt = (n - r0 < kOPlanTile) ? (int)(n - r0) : kOPlanTile;
         // read this pass's starts (and the next pass's first) before any is
-        // overwritten; keep a copy for the emit kernel
+        // overwritten; keep a copy for the later kernels
         for (int i = tid; i <= cnt; i += kOPlanThreads) {
             const long long v = offs[r0 + i];
             s_v[i] = v;
@@ -74,8 +118,13 @@ __global__ void __launch_bounds__(kOPlanThreads) ovl_offsets_kernel(long long *o
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             const int i = tid * kPer + j;
-            t[j] = i < cnt ? ovl_tokens(s_v[i + 1] - s_v[i], k) : 0;
-            sum += t[j];
+            long long f = 0;
+            if (i < cnt) {
+                const long long L = s_v[i + 1] - s_v[i];
+                f = KIND == kOffsetsTokens ? ovl_tokens(L, k) : (L + k - 1) / k;
+            }
+            t[j] = f;
+            sum += f;
         }
         long long x = sum;
         for (int o = 1; o < 32; o <<= 1) {
@@ -97,14 +146,14 @@ __global__ void __launch_bounds__(kOPlanThreads) ovl_offsets_kernel(long long *o
             run += t[j];
         }
         __syncthreads();
-        for (int i = tid; i < cnt; i += kOPlanThreads) offs[r0 + i] = s_v[i];
+        for (int i = tid; i < cnt; i += kOPlanThreads) dst[r0 + i] = s_v[i];
         carry += tt;
         __syncthreads();
     }
     if (tid == 0) {
         srec[n] = offs[n];  // the symbol count (not overwritten above)
-        offs[n] = carry;
-        if (totals_out) {
+        dst[n] = carry;
+        if (KIND == kOffsetsTokens && totals_out) {
             totals_out[0] = carry;
             totals_out[1] = n;
         }
@@ -199,14 +248,197 @@ cudaError_t launch_emit(int k, unsigned grid, const uint8_t *sym, const long lon
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ table-driven k-mers
+
+constexpr int kKW = 1024;       // windows per tile
+constexpr int kKThreads = 256;  // four consecutive windows per thread
+constexpr int kKPer = kKW / kKThreads;
+constexpr int kKRW = 64;        // records of a tile kept in shared memory
+
+struct KtabIds {
+    int b[5];  // ids of the single symbols A C G T N
+};
+
+// One tile of windows [w0, w1): count (EMIT = false: the tile's token count
+// to tsum[tile]) or emit (EMIT = true: ids from tsum[tile], now the tile's
+// exclusive token offset, and the record offsets of records whose first
+// window is here).
+template <int K, bool EMIT>
+__global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
+    const uint8_t *sym, const long long *srec, const long long *wpre, const long long *tot,
+    const int *klut, KtabIds base, long long *tsum, int *out, long long ids_cap,
+    long long *id_offsets) {
+    __shared__ uint8_t s_sym[kKW * K + 16];
+    __shared__ long long s_wp[kKRW + 1], s_sr[kKRW + 1];
+    __shared__ long long s_rb, s_jlo, s_jhi;
+    __shared__ int s_nw;
+    __shared__ long long s_wsum[kKThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long n_rec = tot[1];
+    if (n_rec < 1) return;
+    const long long n_win = wpre[n_rec];
+    const long long n_tiles = (n_win + kKW - 1) / kKW;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const long long w0 = tile * kKW;
+        const long long w1 = (w0 + kKW < n_win) ? w0 + kKW : n_win;
+        if (tid == 0) {
+            const long long rb = ovl_find(wpre, n_rec, w0);
+            s_rb = rb;
+            s_nw = (n_rec - rb < kKRW) ? (int)(n_rec - rb) : kKRW;
+            s_jlo = srec[rb] + (w0 - wpre[rb]) * K;
+            if (w1 >= n_win) {
+                s_jhi = srec[n_rec];
+            } else {
+                const long long r1 = ovl_find(wpre, n_rec, w1);
+                s_jhi = srec[r1] + (w1 - wpre[r1]) * K;
+            }
+        }
+        __syncthreads();
+        const long long rb = s_rb, jlo = s_jlo;
+        const int nw = s_nw;
+        long long nsym = s_jhi - jlo;
+        if (nsym > (long long)kKW * K) nsym = (long long)kKW * K;  // (malformed input)
+        if (nsym < 0) nsym = 0;
+        for (int l = tid; l <= nw; l += kKThreads) {
+            s_wp[l] = wpre[rb + l];
+            s_sr[l] = srec[rb + l];
+        }
+        for (long long i = tid; i < nsym; i += kKThreads) s_sym[i] = sym[jlo + i];
+        __syncthreads();
+
+        // this thread's windows: counts and, for whole windows, the table entry
+        int cnt[kKPer], ent[kKPer];
+        long long jw[kKPer], rr[kKPer], tw[kKPer];
+        int sum = 0;
+#pragma unroll
+        for (int q = 0; q < kKPer; ++q) {
+            const long long w = w0 + (long long)tid * kKPer + q;
+            cnt[q] = 0;
+            ent[q] = -1;
+            jw[q] = 0;
+            rr[q] = -1;
+            tw[q] = 0;
+            if (w >= w1) continue;
+            long long r, wp, sr, sr1;
+            if (w >= s_wp[nw] && rb + nw < n_rec) {
+                // more records start in this tile than the window holds
+                r = ovl_find(wpre, n_rec, w);
+                wp = wpre[r];
+                sr = srec[r];
+                sr1 = srec[r + 1];
+            } else {
+                int lo = 0, hi = nw - 1;  // largest i with s_wp[i] <= w
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_wp[mid] <= w) lo = mid; else hi = mid - 1;
+                }
+                r = rb + lo;
+                wp = s_wp[lo];
+                sr = s_sr[lo];
+                sr1 = s_sr[lo + 1];
+            }
+            const long long t = w - wp;
+            const long long j = sr + t * K - jlo;  // in s_sym
+            const long long rem = (sr1 - sr) - t * K;
+            const int n_s = rem >= K ? K : (int)rem;
+            if (j < 0 || n_s < 1 || j + n_s > nsym) continue;  // (malformed input)
+            rr[q] = r;
+            tw[q] = t;
+            jw[q] = j;
+            if (n_s == K) {
+                int index = 0;
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const int d = s_sym[j + i];
+                    index = index * 5 + (d < 5 ? d : 4);
+                }
+                ent[q] = __ldg(klut + index);
+                cnt[q] = ent[q] >= 0 ? 1 : K;
+            } else {
+                cnt[q] = n_s;
+            }
+            sum += cnt[q];
+        }
+        // block scan of the per-thread counts
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        __syncthreads();
+        if (!EMIT) {
+            if (tid == 0) {
+                long long tt = 0;
+                for (int w = 0; w < kKThreads / 32; ++w) tt += s_wsum[w];
+                tsum[tile] = tt;
+            }
+        } else {
+            long long pos = tsum[tile] + x - sum;
+            for (int w = 0; w < warp; ++w) pos += s_wsum[w];
+#pragma unroll
+            for (int q = 0; q < kKPer; ++q) {
+                if (rr[q] < 0) continue;
+                const long long w = w0 + (long long)tid * kKPer + q;
+                if (tw[q] == 0) {
+                    // the record's first window: its offset, and that of the
+                    // empty records just before it
+                    long long r = rr[q];
+                    id_offsets[r] = pos;
+                    while (r > 0 && wpre[r - 1] == w) id_offsets[--r] = pos;
+                }
+                if (cnt[q] == 1 && ent[q] >= 0) {
+                    if (pos < ids_cap) out[pos] = ent[q];
+                } else {
+                    for (int i = 0; i < cnt[q]; ++i) {
+                        const int d = s_sym[jw[q] + i];
+                        if (pos + i < ids_cap) out[pos + i] = base.b[d < 5 ? d : 4];
+                    }
+                }
+                pos += cnt[q];
+            }
+        }
+        __syncthreads();  // shared memory is reused by the next tile
+    }
+}
+
+cudaError_t launch_ktab(int k, bool emit, unsigned grid, const uint8_t *sym, const long long *srec,
+                        const long long *wpre, const long long *tot, const int *klut,
+                        KtabIds base, long long *tsum, int *out, long long cap,
+                        long long *id_offsets, cudaStream_t s) {
+    switch (k) {
+#define DNATOK_KT_K(KK)                                                                        \
+    case KK:                                                                                   \
+        if (emit)                                                                              \
+            ktab_tile_kernel<KK, true><<<grid, kKThreads, 0, s>>>(sym, srec, wpre, tot, klut,  \
+                                                                  base, tsum, out, cap,        \
+                                                                  id_offsets);                 \
+        else                                                                                   \
+            ktab_tile_kernel<KK, false><<<grid, kKThreads, 0, s>>>(sym, srec, wpre, tot, klut, \
+                                                                   base, tsum, out, cap,       \
+                                                                   id_offsets);                \
+        break;
+        DNATOK_KT_K(1) DNATOK_KT_K(2) DNATOK_KT_K(3) DNATOK_KT_K(4) DNATOK_KT_K(5)
+        DNATOK_KT_K(6) DNATOK_KT_K(7) DNATOK_KT_K(8) DNATOK_KT_K(9) DNATOK_KT_K(10)
+#undef DNATOK_KT_K
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 void free_ovl(OvlState *o) {
     cudaFree(o->d_sym);
     cudaFree(o->d_srec);
+    cudaFree(o->d_wpre);
     cudaFree(o->d_tot);
+    cudaFree(o->d_tsum);
     o->d_sym = nullptr;
     o->d_srec = nullptr;
+    o->d_wpre = nullptr;
     o->d_tot = nullptr;
-    o->cap_sym = o->cap_srec = 0;
+    o->d_tsum = nullptr;
+    o->cap_sym = o->cap_srec = o->cap_tsum = 0;
 }
 
 }  // namespace
@@ -237,8 +469,13 @@ dnatok_status ovl_reserve(dnatok_handle *h, long long max_bytes, long long max_o
     const long long cs_ = max_bytes > o->cap_sym ? max_bytes + max_bytes / 8 + 4096 : o->cap_sym;
     const long long cr = max_offsets > o->cap_srec ? max_offsets + max_offsets / 8 + 64 : o->cap_srec;
     free_ovl(o);
+    const long long ct = cs_ / kKW + 2;  // tiles of windows (at most one window per symbol)
     e = cudaMalloc(&o->d_sym, (size_t)cs_ + 16);
     if (e == cudaSuccess) e = cudaMalloc(&o->d_srec, sizeof(long long) * (size_t)(cr + 1));
+    if (e == cudaSuccess && h->mode == DNATOK_KMER_TABLE)
+        e = cudaMalloc(&o->d_wpre, sizeof(long long) * (size_t)(cr + 1));
+    if (e == cudaSuccess && h->mode == DNATOK_KMER_TABLE)
+        e = cudaMalloc(&o->d_tsum, sizeof(long long) * (size_t)ct);
     if (e == cudaSuccess) e = cudaMalloc(&o->d_tot, 2 * sizeof(long long));
     if (e != cudaSuccess) {
         free_ovl(o);
@@ -246,6 +483,7 @@ dnatok_status ovl_reserve(dnatok_handle *h, long long max_bytes, long long max_o
     }
     o->cap_sym = cs_;
     o->cap_srec = cr;
+    o->cap_tsum = h->mode == DNATOK_KMER_TABLE ? ct : 0;
     return DNATOK_OK;
 }
 
@@ -264,9 +502,9 @@ dnatok_status ovl_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
                          offsets_capacity, o->d_tot, nullptr, nullptr, raw ? 0 : 1, raw ? 0 : 1, s);
     if (st != DNATOK_OK) return st;
     // 2. token offsets
-    ovl_offsets_kernel<<<1, kOPlanThreads, 0, s>>>(reinterpret_cast<long long *>(id_offsets_d),
-                                                    o->d_srec, o->d_tot, h->k,
-                                                    reinterpret_cast<long long *>(totals_d));
+    offsets_kernel<kOffsetsTokens><<<1, kOPlanThreads, 0, s>>>(
+        reinterpret_cast<long long *>(id_offsets_d), o->d_srec, nullptr, o->d_tot, h->k,
+        offsets_capacity, reinterpret_cast<long long *>(totals_d), h->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "overlap offsets launch");
     // 3. ids
@@ -278,6 +516,116 @@ dnatok_status ovl_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
                     reinterpret_cast<const long long *>(id_offsets_d), o->d_tot, ids_out_d,
                     ids_capacity, s);
     if (e != cudaSuccess) return fail_cuda(h, e, "overlap emit launch");
+    return DNATOK_OK;
+}
+
+__global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
+    long long *tsum, const long long *tinv, const long long *keys, const long long *n_rec_dev,
+    long long n_rec_host, const long long *n_items_dev, long long n_items_host, int items_per_tile,
+    long long *rec_out, long long *totals_out, const int *status) {
+    constexpr int kPer = 4;
+    __shared__ long long wsum[kTileScanThreads / 32], winv[kTileScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (dev_failed(status)) return;  // an earlier pass failed: its counts are not valid
+    const long long n_rec = n_rec_dev ? *n_rec_dev : n_rec_host;
+    if (n_rec < 0) return;
+    const long long n_items = n_items_dev ? *n_items_dev : (n_items_host >= 0 ? n_items_host : keys[n_rec]);
+    if (n_items < 0) return;
+    const long long n_tiles = (n_items + items_per_tile - 1) / items_per_tile;
+    long long carry = 0, inv = 0;
+    for (long long b0 = 0; b0 < n_tiles; b0 += (long long)kTileScanThreads * kPer) {
+        long long v[kPer], sum = 0, isum = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const long long i = b0 + (long long)tid * kPer + j;
+            v[j] = i < n_tiles ? tsum[i] : 0;
+            if (tinv && i < n_tiles) isum += tinv[i];
+            sum += v[j];
+        }
+        long long x = sum, y = isum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long a = __shfl_up_sync(0xffffffffu, x, o);
+            const long long c = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) {
+                x += a;
+                y += c;
+            }
+        }
+        if (lane == 31) {
+            wsum[warp] = x;
+            winv[warp] = y;
+        }
+        __syncthreads();
+        long long pre = carry, tt = 0, ti = 0;
+        for (int w = 0; w < kTileScanThreads / 32; ++w) {
+            if (w < warp) pre += wsum[w];
+            tt += wsum[w];
+            ti += winv[w];
+        }
+        long long run = pre + x - sum;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const long long i = b0 + (long long)tid * kPer + j;
+            if (i < n_tiles) tsum[i] = run;
+            run += v[j];
+        }
+        carry += tt;
+        inv += ti;
+        __syncthreads();  // wsum is rewritten by the next pass
+    }
+    // records with no item left start at the total: the first r with
+    // keys[r] >= n_items, then every later one
+    long long lo = 0, hi = n_rec;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (keys[mid] >= n_items) hi = mid; else lo = mid + 1;
+    }
+    for (long long r = lo + tid; r <= n_rec; r += kTileScanThreads) rec_out[r] = carry;
+    if (tid == 0 && totals_out) {
+        totals_out[0] = carry;
+        totals_out[1] = tinv ? inv : n_rec;
+    }
+}
+
+dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
+                          const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
+                          int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
+                          int64_t *totals_d, cudaStream_t s) {
+    dnatok_status st = ovl_reserve(h, n_bytes, offsets_capacity, s);
+    if (st != DNATOK_OK) return st;
+    OvlState *o = h->ovl;
+    const bool raw = (h->fmt == DNATOK_RAW);
+    long long *offs = reinterpret_cast<long long *>(id_offsets_d);
+    // 1. symbols and record starts (in symbols)
+    st = run_tile_encode(h, MODE_SYM, 1, raw ? BSRC_LIST : BSRC_FASTA, bytes_d, n_bytes,
+                         reinterpret_cast<const long long *>(seq_offsets_d), raw ? n_seq + 1 : 0,
+                         o->d_sym, o->cap_sym, offs, offsets_capacity, o->d_tot, nullptr, nullptr,
+                         raw ? 0 : 1, raw ? 0 : 1, s);
+    if (st != DNATOK_OK) return st;
+    // 2. window offsets
+    offsets_kernel<kOffsetsWindows><<<1, kOPlanThreads, 0, s>>>(
+        offs, o->d_srec, o->d_wpre, o->d_tot, h->k, offsets_capacity,
+        reinterpret_cast<long long *>(totals_d), h->d_status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(h, e, "window offsets launch");
+    // 3-5. count, scan, emit
+    long long tiles = n_bytes / kKW + 1;
+    long long grid = (long long)h->sm_count * 8;
+    if (grid > tiles) grid = tiles;
+    KtabIds base;
+    for (int d = 0; d < 5; ++d) base.b[d] = h->base_ids[d];
+    e = launch_ktab(h->k, false, (unsigned)grid, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,
+                    h->d_klut, base, o->d_tsum, ids_out_d, ids_capacity, offs, s);
+    if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer count launch");
+    tile_scan_kernel<<<1, kTileScanThreads, 0, s>>>(o->d_tsum, nullptr, o->d_wpre, o->d_tot + 1, 0,
+                                                nullptr, -1, kKW, offs,
+                                                reinterpret_cast<long long *>(totals_d),
+                                                h->d_status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer scan launch");
+    e = launch_ktab(h->k, true, (unsigned)grid, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,
+                    h->d_klut, base, o->d_tsum, ids_out_d, ids_capacity, offs, s);
+    if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer emit launch");
     return DNATOK_OK;
 }
 

@@ -319,8 +319,8 @@ dnatok_status dnatok_server_create(const dnatok_server_cfg *cfg, dnatok_server *
     if (!S) return DNATOK_ERR_NOMEM;
     S->cfg = *cfg;
     S->n_slots = cfg->n_slots;
-    dnatok_tables none{nullptr, nullptr, 0};
-    dnatok_tables bpe{nullptr, cfg->merges, cfg->n_merges};
+    dnatok_tables none{nullptr, nullptr, 0, nullptr, nullptr};
+    dnatok_tables bpe{nullptr, cfg->merges, cfg->n_merges, nullptr, nullptr};
     for (int slot = 0; slot < S->n_slots; ++slot) {
         for (int mode = 0; mode < 3; ++mode) {
             dnatok_handle *h = nullptr;

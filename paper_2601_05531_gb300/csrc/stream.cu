@@ -163,7 +163,7 @@ dnatok_status dnatok_stream_open(dnatok_handle *h, const dnatok_stream_cfg *cfg,
                                  int64_t offsets_capacity) {
     if (!h) return DNATOK_ERR_ARG;
     if (h->stream) return fail(h, DNATOK_ERR_STATE, "a stream is already open on this handle");
-    if (h->mode == DNATOK_BPE || h->mode == DNATOK_KMER_OVERLAP)
+    if (h->mode == DNATOK_BPE || h->mode == DNATOK_KMER_OVERLAP || h->mode == DNATOK_KMER_TABLE)
         return fail(h, DNATOK_ERR_STATE, "streams take CHAR or KMER handles");
     if (ids_capacity < 0 || (ids_capacity > 0 && !ids_out_d) || offsets_capacity < 0 ||
         (offsets_capacity > 0 && !id_offsets_d))
