@@ -20,11 +20,15 @@
 // count and its count of ids without text), tile_scan_kernel (exclusive scan
 // of the tile counts, totals), dec_tile_kernel<true> (recount, scan inside the
 // block, write the bytes and the record offsets of records starting here).
+// The emit assembles a tile's text in shared memory when it fits (16 KB: up
+// to 8 bases per id on average) and writes it out in aligned 16-byte stores;
+// larger tiles write byte by byte.
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "handle.h"
+#include "search.cuh"
 
 namespace {
 
@@ -32,6 +36,7 @@ using namespace dnatok;
 
 constexpr int kDT = 2048;       // ids per tile
 constexpr int kDThreads = 256;  // eight consecutive ids per thread
+constexpr int kDOut = 16384;    // text bytes of a tile staged in shared memory
 constexpr int kDPer = kDT / kDThreads;
 
 enum { DEC_TABLE = 0, DEC_KMER = 1, DEC_OVL = 2 };
@@ -51,15 +56,8 @@ struct DecArgs {
     long long *rec_out;
 };
 
-// first r in [0, n] with keys[r] >= x (keys non-decreasing)
-__device__ long long lower_bound_keys(const long long *keys, long long n, long long x) {
-    long long lo = 0, hi = n;
-    while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        if (keys[mid] >= x) hi = mid; else lo = mid + 1;
-    }
-    return lo;
-}
+// "ACGT"[c] for c in 0..3
+__device__ __forceinline__ uint8_t base_char(int c) { return (uint8_t)(0x54474341u >> (8 * c)); }
 
 template <int MODE>
 __device__ __forceinline__ int dec_len(const DecArgs &a, int v, bool first) {
@@ -74,6 +72,7 @@ template <int MODE, bool EMIT>
 __global__ void __launch_bounds__(kDThreads) dec_tile_kernel(DecArgs a) {
     __shared__ uint8_t s_first[kDT];
     __shared__ int s_pos[kDT];
+    __shared__ __align__(16) uint8_t s_out[kDOut + 32];
     __shared__ long long s_ra, s_rb;
     __shared__ int s_wsum[kDThreads / 32], s_winv[kDThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -83,9 +82,13 @@ __global__ void __launch_bounds__(kDThreads) dec_tile_kernel(DecArgs a) {
         const long long t1 = (t0 + kDT < a.n_ids) ? t0 + kDT : a.n_ids;
         const bool need_rec = (MODE == DEC_OVL) || EMIT;
         if (need_rec) {
-            if (tid == 0) {
-                s_ra = lower_bound_keys(a.keys, a.n_rec, t0);
-                s_rb = lower_bound_keys(a.keys, a.n_rec, t1);
+            // the records starting in [t0, t1): one warp searches each end
+            if (warp == 0) {
+                const long long r = warp_first_ge(a.keys, a.n_rec, t0);
+                if (lane == 0) s_ra = r < a.n_rec ? r : a.n_rec;
+            } else if (warp == 1) {
+                const long long r = warp_first_ge(a.keys, a.n_rec, t1);
+                if (lane == 0) s_rb = r < a.n_rec + 1 ? r : a.n_rec + 1;
             }
             if (MODE == DEC_OVL)
                 for (int i = tid; i < kDT; i += kDThreads) s_first[i] = 0;
@@ -135,28 +138,50 @@ __global__ void __launch_bounds__(kDThreads) dec_tile_kernel(DecArgs a) {
                 a.tinv[tile] = ti;
             }
         } else {
-            int local = x - sum;
-            for (int w = 0; w < warp; ++w) local += s_wsum[w];
+            int local = x - sum, total = 0;
+            for (int w = 0; w < kDThreads / 32; ++w) {
+                if (w < warp) local += s_wsum[w];
+                total += s_wsum[w];
+            }
             const long long base = a.tsum[tile];
+            // staged: the text goes to s_out[shift + local], shift being the
+            // misalignment of its global start, then out in aligned chunks
+            const int shift = (int)(reinterpret_cast<uintptr_t>(a.out + base) & 15u);
+            const bool staged = total + shift <= kDOut;
 #pragma unroll
             for (int q = 0; q < kDPer; ++q) {
                 s_pos[tid * kDPer + q] = local;
                 const long long p = base + local;
-                if (len[q] > 0 && p + len[q] <= a.cap) {
+                uint8_t *dst = staged ? s_out + shift + local : a.out + p;
+                if (len[q] > 0 && (staged || p + len[q] <= a.cap)) {
                     if (MODE == DEC_TABLE) {
                         const int o = __ldg(a.off + v[q]);
-                        for (int i = 0; i < len[q]; ++i) a.out[p + i] = __ldg(a.text + o + i);
+                        for (int i = 0; i < len[q]; ++i) dst[i] = __ldg(a.text + o + i);
                     } else if (len[q] == 1) {
                         const int unk = 1 << (2 * a.k);
-                        a.out[p] = v[q] == unk ? '?' : "ACGT"[v[q] & 3];
+                        dst[0] = v[q] == unk ? (uint8_t)'?' : base_char(v[q] & 3);
                     } else {
                         for (int i = 0; i < a.k; ++i)
-                            a.out[p + i] = "ACGT"[(v[q] >> (2 * (a.k - 1 - i))) & 3];
+                            dst[i] = base_char((v[q] >> (2 * (a.k - 1 - i))) & 3);
                     }
                 }
                 local += len[q];
             }
             __syncthreads();
+            if (staged) {
+                const int span = shift + total;
+                uint8_t *g = a.out + (base - shift);  // 16-byte aligned
+                const long long lim = a.cap - (base - shift);  // bytes of g inside the buffer
+                for (int c = tid; c < (span + 15) >> 4; c += kDThreads) {
+                    const int lo = c * 16, hi = lo + 16;
+                    if (lo >= shift && hi <= span && hi <= lim) {
+                        *reinterpret_cast<uint4 *>(g + lo) = *reinterpret_cast<const uint4 *>(s_out + lo);
+                    } else {
+                        for (int y = lo > shift ? lo : shift; y < (hi < span ? hi : span); ++y)
+                            if (y < lim) g[y] = s_out[y];
+                    }
+                }
+            }
             for (long long r = s_ra + tid; r < s_rb; r += kDThreads) {
                 const long long f = a.keys[r] - t0;
                 if (f >= 0 && f < t1 - t0) a.rec_out[r] = base + s_pos[f];

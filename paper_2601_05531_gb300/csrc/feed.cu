@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "dnatok.h"
+#include "search.cuh"
 
 namespace {
 
@@ -92,9 +93,10 @@ dnatok_status feed_args_ok(const int32_t *ids_d, const int64_t *id_offsets_d, in
 // ------------------------------------------------------ reverse complement
 
 constexpr int kRThreads = 256;
-constexpr int kRChunk = 16;                 // output bytes per thread
-constexpr int kRTile = kRThreads * kRChunk;  // output bytes per CTA step
-constexpr int kRRW = 64;                     // records of a tile kept in shared memory
+constexpr int kRChunk = 16;                          // output bytes per chunk
+constexpr int kRPer = 4;                             // chunks per thread and tile
+constexpr int kRTile = kRThreads * kRChunk * kRPer;  // output bytes per tile (16 KB)
+constexpr int kRRW = 64;                             // records kept in shared memory
 
 __device__ __forceinline__ uint8_t comp_of(int b) {
     switch (b) {
@@ -118,14 +120,19 @@ __device__ long long rec_of(const long long *so, long long n, long long p) {
     return lo;
 }
 
-// Each thread writes the 16 output bytes [p, p + 16) of its chunk.  When the
-// chunk lies inside one record and the output is 16-byte aligned, the 16
-// mirrored input bytes come from four or five aligned words, are shifted into
-// place, reversed and complemented through a shared table, and leave in one
-// 16-byte store; otherwise byte by byte.
-__global__ void __launch_bounds__(kRThreads) revcomp_kernel(const uint8_t *in, long long n,
-                                                            const long long *so, long long n_seq,
-                                                            uint8_t *out, int vec_out) {
+// Each CTA walks a contiguous run of 16 KB tiles of the output, keeping a
+// window of up to 64 record offsets in shared memory (searched again only
+// when a tile starts past it).  Each thread writes four 16-byte chunks
+// [p, p + 16) of a tile.  A chunk inside one record with a 16-byte aligned
+// output takes the fast path: the 16 mirrored input bytes come from four or
+// five aligned words (all chunks' loads issued before any store), are
+// shifted into place, reversed and complemented through a shared table, and
+// leave in one 16-byte store.  Other chunks go byte by byte.
+__global__ void __launch_bounds__(kRThreads) revcomp_kernel(const uint8_t *__restrict__ in,
+                                                            long long n,
+                                                            const long long *__restrict__ so,
+                                                            long long n_seq,
+                                                            uint8_t *__restrict__ out, int vec_out) {
     __shared__ uint8_t s_comp[256];
     __shared__ long long s_so[kRRW + 1];
     __shared__ long long s_rb;
@@ -133,73 +140,93 @@ __global__ void __launch_bounds__(kRThreads) revcomp_kernel(const uint8_t *in, l
     const int tid = threadIdx.x;
     s_comp[tid] = comp_of(tid);
     const long long n_tiles = (n + kRTile - 1) / kRTile;
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long long t_begin = (long long)blockIdx.x * n_tiles / gridDim.x;
+    const long long t_end = (long long)(blockIdx.x + 1) * n_tiles / gridDim.x;
+    for (long long tile = t_begin; tile < t_end; ++tile) {
         const long long p0 = tile * kRTile;
-        if (tid == 0) {
-            const long long rb = rec_of(so, n_seq, p0);
-            s_rb = rb;
-            s_nw = (n_seq - rb < kRRW) ? (int)(n_seq - rb) : kRRW;
+        // (the previous tile ended with a barrier: every thread reads the same window)
+        const bool reuse = tile > t_begin && s_so[0] <= p0 && (p0 < s_so[s_nw] || s_rb + s_nw >= n_seq);
+        if (!reuse) {
+            __syncthreads();
+            if (tid < 32) {
+                const long long rb = dnatok::warp_find_le(so, n_seq, p0);
+                if (tid == 0) {
+                    s_rb = rb;
+                    s_nw = (n_seq - rb < kRRW) ? (int)(n_seq - rb) : kRRW;
+                }
+            }
+            __syncthreads();
+            for (int l = tid; l <= s_nw; l += kRThreads) s_so[l] = so[s_rb + l];
+            __syncthreads();
         }
-        __syncthreads();
         const long long rb = s_rb;
         const int nw = s_nw;
-        for (int l = tid; l <= nw; l += kRThreads) s_so[l] = so[rb + l];
-        __syncthreads();
-        const long long p = p0 + (long long)tid * kRChunk;
-        // the record holding p
-        long long s, e;
-        if (p >= s_so[nw] && rb + nw < n_seq) {
-            const long long r = rec_of(so, n_seq, p < n ? p : n - 1);
-            s = so[r];
-            e = so[r + 1];
-        } else {
-            int lo = 0, hi = nw - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_so[mid] <= p) lo = mid; else hi = mid - 1;
-            }
-            s = s_so[lo];
-            e = s_so[lo + 1];
-        }
-        if (vec_out && p >= s && p + kRChunk <= e && s >= 0 && e <= n) {
-            // input bytes [a, a + 16) mirror output bytes [p, p + 16)
-            const long long a = s + e - p - kRChunk;
-            const uintptr_t ua = reinterpret_cast<uintptr_t>(in + a);
-            const unsigned *wp = reinterpret_cast<const unsigned *>(ua & ~(uintptr_t)3);
-            const unsigned sh = (unsigned)(ua & 3) * 8u;
-            unsigned w[5];
+        long long cs[kRPer], ce[kRPer];
+        bool fast[kRPer];
+        unsigned w[kRPer][5], sh[kRPer];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) w[i] = __ldg(wp + i);
-            // the fifth word holds input bytes only when the start is unaligned
-            w[4] = sh ? __ldg(wp + 4) : 0u;
-            unsigned x[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) x[i] = __funnelshift_r(w[i], w[i + 1], sh);
-            uint4 v;
-            unsigned *vv = reinterpret_cast<unsigned *>(&v);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const unsigned y = x[3 - j];  // bytes 4(3-j) .. 4(3-j)+3, reversed below
-                vv[j] = (unsigned)s_comp[y >> 24] | ((unsigned)s_comp[(y >> 16) & 0xFFu] << 8) |
-                        ((unsigned)s_comp[(y >> 8) & 0xFFu] << 16) |
-                        ((unsigned)s_comp[y & 0xFFu] << 24);
-            }
-            *reinterpret_cast<uint4 *>(out + p) = v;
-        } else {
-            for (int q = 0; q < kRChunk; ++q) {
-                const long long P = p + q;
-                if (P >= n) break;
-                long long ss = s, ee = e;
-                if (!(P >= ss && P < ee)) {
-                    const long long r = rec_of(so, n_seq, P);
-                    ss = so[r];
-                    ee = so[r + 1];
+        for (int h = 0; h < kRPer; ++h) {
+            const long long p = p0 + ((long long)h * kRThreads + tid) * kRChunk;
+            long long s, e;  // the record holding p
+            if (p >= s_so[nw] && rb + nw < n_seq) {
+                const long long r = rec_of(so, n_seq, p < n ? p : n - 1);
+                s = so[r];
+                e = so[r + 1];
+            } else {
+                int lo = 0, hi = nw - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_so[mid] <= p) lo = mid; else hi = mid - 1;
                 }
-                const long long m = ss + ee - 1 - P;
-                if (P >= ss && P < ee && m >= 0 && m < n) out[P] = s_comp[in[m]];
+                s = s_so[lo];
+                e = s_so[lo + 1];
+            }
+            cs[h] = s;
+            ce[h] = e;
+            fast[h] = vec_out && p >= s && p + kRChunk <= e && s >= 0 && e <= n;
+            sh[h] = 0;
+            if (fast[h]) {
+                // input bytes [a, a + 16) mirror output bytes [p, p + 16)
+                const uintptr_t ua = reinterpret_cast<uintptr_t>(in + (s + e - p - kRChunk));
+                const unsigned *wp = reinterpret_cast<const unsigned *>(ua & ~(uintptr_t)3);
+                sh[h] = (unsigned)(ua & 3) * 8u;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[h][i] = __ldg(wp + i);
+                // the fifth word holds input bytes only when the start is unaligned
+                w[h][4] = sh[h] ? __ldg(wp + 4) : 0u;
             }
         }
-        __syncthreads();  // s_so is reused by the next tile
+#pragma unroll
+        for (int h = 0; h < kRPer; ++h) {
+            const long long p = p0 + ((long long)h * kRThreads + tid) * kRChunk;
+            if (fast[h]) {
+                uint4 v;
+                unsigned *vv = reinterpret_cast<unsigned *>(&v);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    // output word j = input bytes 4(3-j) .. 4(3-j)+3, reversed
+                    const unsigned y = __funnelshift_r(w[h][3 - j], w[h][4 - j], sh[h]);
+                    vv[j] = (unsigned)s_comp[y >> 24] | ((unsigned)s_comp[(y >> 16) & 0xFFu] << 8) |
+                            ((unsigned)s_comp[(y >> 8) & 0xFFu] << 16) |
+                            ((unsigned)s_comp[y & 0xFFu] << 24);
+                }
+                *reinterpret_cast<uint4 *>(out + p) = v;
+            } else {
+                for (int q = 0; q < kRChunk; ++q) {
+                    const long long P = p + q;
+                    if (P >= n) break;
+                    long long ss = cs[h], ee = ce[h];
+                    if (!(P >= ss && P < ee)) {
+                        const long long r = rec_of(so, n_seq, P);
+                        ss = so[r];
+                        ee = so[r + 1];
+                    }
+                    const long long m = ss + ee - 1 - P;
+                    if (P >= ss && P < ee && m >= 0 && m < n) out[P] = s_comp[in[m]];
+                }
+            }
+        }
+        __syncthreads();  // s_so may be replaced by the next tile
     }
 }
 
@@ -292,8 +319,12 @@ dnatok_status dnatok_reverse_complement(const uint8_t *bytes_d, int64_t n_bytes,
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;  // one resident wave: each CTA takes a contiguous run of tiles
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, revcomp_kernel, kRThreads, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
     const long long tiles = (n_bytes + kRTile - 1) / kRTile;
-    long long grid = (long long)(sms > 0 ? sms : 1) * 8;
+    long long grid = (long long)(sms > 0 ? sms : 1) * per_sm;
     if (grid > tiles) grid = tiles;
     const int vec = ((uintptr_t)out_d & 15u) == 0;
     revcomp_kernel<<<(unsigned)grid, kRThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(

@@ -27,7 +27,7 @@
 //   1. the symbol pass, as above;
 //   2. offsets_kernel<kOffsetsWindows>: record starts to the workspace and
 //      the window offsets wpre[r] = sum of ceil(L / k) over earlier records;
-//   3. ktab_tile_kernel<K, false>: per tile of 1024 windows, its token count;
+//   3. ktab_tile_kernel<K, false>: per tile of 4096 windows, its token count;
 //   4. tile_scan_kernel (one block): exclusive scan of the tile counts, the
 //      totals and the offsets of records with no window left;
 //   5. ktab_tile_kernel<K, true>: recounts, scans inside the block and writes
@@ -35,6 +35,7 @@
 #include <cstring>
 
 #include "handle.h"
+#include "search.cuh"
 #include "tile_kernel.cuh"
 
 struct OvlState {
@@ -69,6 +70,22 @@ __device__ long long ovl_find(const long long *srec, long long n_rec, long long 
         if (srec[mid] <= j) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Stage sym[j0 .. j0 + n) in shared memory as the 16-byte aligned span
+// around it, s[x] = sym[(j0 & ~15) + x] for x < (j0 & 15) + n rounded up to
+// 16, with 16-byte loads issued together.
+// The symbol buffer is 16-byte aligned and has 16 spare bytes at its end, so
+// the rounded span stays inside it.  Returns j0 & 15, the shift of j0 in s.
+__device__ __forceinline__ int stage_symbols(uint8_t *s, const uint8_t *sym, long long j0, long long n,
+                                             int tid, int nthreads) {
+    const int lead = (int)(j0 & 15);
+    const uint4 *src = reinterpret_cast<const uint4 *>(sym + (j0 - lead));
+    uint4 *dst = reinterpret_cast<uint4 *>(s);
+    const int chunks = (int)((lead + n + 15) >> 4);
+#pragma unroll 4
+    for (int c = tid; c < chunks; c += nthreads) dst[c] = src[c];
+    return lead;
 }
 
 enum { kOffsetsTokens = 0, kOffsetsWindows = 1 };
@@ -165,7 +182,7 @@ __global__ void __launch_bounds__(kOThreads) ovl_emit_kernel(const uint8_t *sym,
                                                              const long long *offs, const long long *tot,
                                                              int *out, long long ids_cap) {
     constexpr unsigned UNK = 1u << (2 * K);
-    __shared__ uint8_t s_sym[kOT + 16];
+    __shared__ __align__(16) uint8_t s_sym[kOT + 32];
     __shared__ long long s_rs[kORW + 1], s_ob[kORW];
     __shared__ long long s_rb;
     __shared__ int s_nw;
@@ -179,7 +196,7 @@ __global__ void __launch_bounds__(kOThreads) ovl_emit_kernel(const uint8_t *sym,
         const long long j0 = tile * kOT;
         const long long j1 = (j0 + kOT < n_sym) ? j0 + kOT : n_sym;
         const long long jh = (j1 + K - 1 < n_sym) ? j1 + K - 1 : n_sym;
-        for (long long i = tid; i < jh - j0; i += kOThreads) s_sym[i] = sym[j0 + i];
+        stage_symbols(s_sym, sym, j0, jh - j0, tid, kOThreads);  // (j0 is a multiple of 4096)
         if (tid == 0) {
             // the record holding j0: from the last tile's window when it is there
             long long rb;
@@ -250,29 +267,86 @@ cudaError_t launch_emit(int k, unsigned grid, const uint8_t *sym, const long lon
 
 // ------------------------------------------------------ table-driven k-mers
 
-constexpr int kKW = 1024;       // windows per tile
-constexpr int kKThreads = 256;  // four consecutive windows per thread
-constexpr int kKPer = kKW / kKThreads;
+constexpr int kKW = 4096;       // windows per tile
+constexpr int kKThreads = 256;
+constexpr int kKPer = kKW / kKThreads;  // consecutive windows per thread
 constexpr int kKRW = 64;        // records of a tile kept in shared memory
 
 struct KtabIds {
     int b[5];  // ids of the single symbols A C G T N
 };
 
+// One window: its record (r, its first window wp, its symbol range [sr, sr1))
+// from the tile's shared record window (advancing the caller's index i, as
+// windows only grow), else by a search of wpre.
+struct KWin {
+    long long r, t, j;  // record, window within the record, first symbol in s_sym
+    int cnt, ent;       // tokens; the table entry of a whole window (-1: none)
+};
+
+template <int K>
+__device__ __forceinline__ KWin ktab_window(long long w, int &i, int nw, long long rb, long long n_rec,
+                                            const long long *s_wp, const long long *s_sr,
+                                            const long long *wpre, const long long *srec,
+                                            const uint8_t *s_sym, long long jlo, long long nsym,
+                                            const int *klut) {
+    KWin q;
+    q.r = -1;
+    q.cnt = 0;
+    q.ent = -1;
+    long long wp, sr, sr1;
+    if (w >= s_wp[nw] && rb + nw < n_rec) {
+        // more records start in this tile than the window holds
+        const long long r = ovl_find(wpre, n_rec, w);
+        q.r = r;
+        wp = wpre[r];
+        sr = srec[r];
+        sr1 = srec[r + 1];
+    } else {
+        while (i + 1 < nw && s_wp[i + 1] <= w) ++i;
+        q.r = rb + i;
+        wp = s_wp[i];
+        sr = s_sr[i];
+        sr1 = s_sr[i + 1];
+    }
+    q.t = w - wp;
+    q.j = sr + q.t * K - jlo;
+    const long long rem = (sr1 - sr) - q.t * K;
+    const int n_s = rem >= K ? K : (int)rem;
+    if (q.j < 0 || n_s < 1 || q.j + n_s > nsym) {  // (malformed input)
+        q.r = -1;
+        return q;
+    }
+    if (n_s == K) {
+        int index = 0;
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            const int d = s_sym[q.j + x];
+            index = index * 5 + (d < 5 ? d : 4);
+        }
+        q.ent = __ldg(klut + index);
+        q.cnt = q.ent >= 0 ? 1 : K;
+    } else {
+        q.cnt = n_s;
+    }
+    return q;
+}
+
 // One tile of windows [w0, w1): count (EMIT = false: the tile's token count
-// to tsum[tile]) or emit (EMIT = true: ids from tsum[tile], now the tile's
-// exclusive token offset, and the record offsets of records whose first
-// window is here).
+// to tsum[tile]) or emit (EMIT = true: ids from tsum[tile], by then the
+// tile's exclusive token offset, and the record offsets of records whose
+// first window is here).  Each thread takes kKPer consecutive windows; the
+// emit recounts them after the block scan instead of keeping them in
+// registers.
 template <int K, bool EMIT>
 __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
     const uint8_t *sym, const long long *srec, const long long *wpre, const long long *tot,
     const int *klut, KtabIds base, long long *tsum, int *out, long long ids_cap,
     long long *id_offsets) {
-    __shared__ uint8_t s_sym[kKW * K + 16];
+    __shared__ __align__(16) uint8_t s_sym[kKW * K + 32];
     __shared__ long long s_wp[kKRW + 1], s_sr[kKRW + 1];
     __shared__ long long s_rb, s_jlo, s_jhi;
-    __shared__ int s_nw;
-    __shared__ long long s_wsum[kKThreads / 32];
+    __shared__ int s_wsum[kKThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n_rec = tot[1];
     if (n_rec < 1) return;
@@ -281,21 +355,24 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const long long w0 = tile * kKW;
         const long long w1 = (w0 + kKW < n_win) ? w0 + kKW : n_win;
-        if (tid == 0) {
-            const long long rb = ovl_find(wpre, n_rec, w0);
-            s_rb = rb;
-            s_nw = (n_rec - rb < kKRW) ? (int)(n_rec - rb) : kKRW;
-            s_jlo = srec[rb] + (w0 - wpre[rb]) * K;
+        // the records holding w0 and w1 (one warp each), and the tile's symbols
+        if (warp == 0) {
+            const long long rb = warp_find_le(wpre, n_rec, w0);
+            if (lane == 0) {
+                s_rb = rb;
+                s_jlo = srec[rb] + (w0 - wpre[rb]) * K;
+            }
+        } else if (warp == 1) {
             if (w1 >= n_win) {
-                s_jhi = srec[n_rec];
+                if (lane == 0) s_jhi = srec[n_rec];
             } else {
-                const long long r1 = ovl_find(wpre, n_rec, w1);
-                s_jhi = srec[r1] + (w1 - wpre[r1]) * K;
+                const long long r1 = warp_find_le(wpre, n_rec, w1);
+                if (lane == 0) s_jhi = srec[r1] + (w1 - wpre[r1]) * K;
             }
         }
         __syncthreads();
         const long long rb = s_rb, jlo = s_jlo;
-        const int nw = s_nw;
+        const int nw = (n_rec - rb < kKRW) ? (int)(n_rec - rb) : kKRW;
         long long nsym = s_jhi - jlo;
         if (nsym > (long long)kKW * K) nsym = (long long)kKW * K;  // (malformed input)
         if (nsym < 0) nsym = 0;
@@ -303,63 +380,21 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
             s_wp[l] = wpre[rb + l];
             s_sr[l] = srec[rb + l];
         }
-        for (long long i = tid; i < nsym; i += kKThreads) s_sym[i] = sym[jlo + i];
+        const int lead = stage_symbols(s_sym, sym, jlo, nsym, tid, kKThreads);
         __syncthreads();
+        const uint8_t *t_sym = s_sym + lead;  // t_sym[x] = sym[jlo + x]
 
-        // this thread's windows: counts and, for whole windows, the table entry
-        int cnt[kKPer], ent[kKPer];
-        long long jw[kKPer], rr[kKPer], tw[kKPer];
+        const long long wt = w0 + (long long)tid * kKPer;
         int sum = 0;
-#pragma unroll
-        for (int q = 0; q < kKPer; ++q) {
-            const long long w = w0 + (long long)tid * kKPer + q;
-            cnt[q] = 0;
-            ent[q] = -1;
-            jw[q] = 0;
-            rr[q] = -1;
-            tw[q] = 0;
-            if (w >= w1) continue;
-            long long r, wp, sr, sr1;
-            if (w >= s_wp[nw] && rb + nw < n_rec) {
-                // more records start in this tile than the window holds
-                r = ovl_find(wpre, n_rec, w);
-                wp = wpre[r];
-                sr = srec[r];
-                sr1 = srec[r + 1];
-            } else {
-                int lo = 0, hi = nw - 1;  // largest i with s_wp[i] <= w
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_wp[mid] <= w) lo = mid; else hi = mid - 1;
-                }
-                r = rb + lo;
-                wp = s_wp[lo];
-                sr = s_sr[lo];
-                sr1 = s_sr[lo + 1];
+        {
+            int i = 0;
+            for (int q = 0; q < kKPer; ++q) {
+                const long long w = wt + q;
+                if (w >= w1) break;
+                sum += ktab_window<K>(w, i, nw, rb, n_rec, s_wp, s_sr, wpre, srec, t_sym, jlo,
+                                      nsym, klut).cnt;
             }
-            const long long t = w - wp;
-            const long long j = sr + t * K - jlo;  // in s_sym
-            const long long rem = (sr1 - sr) - t * K;
-            const int n_s = rem >= K ? K : (int)rem;
-            if (j < 0 || n_s < 1 || j + n_s > nsym) continue;  // (malformed input)
-            rr[q] = r;
-            tw[q] = t;
-            jw[q] = j;
-            if (n_s == K) {
-                int index = 0;
-#pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    const int d = s_sym[j + i];
-                    index = index * 5 + (d < 5 ? d : 4);
-                }
-                ent[q] = __ldg(klut + index);
-                cnt[q] = ent[q] >= 0 ? 1 : K;
-            } else {
-                cnt[q] = n_s;
-            }
-            sum += cnt[q];
         }
-        // block scan of the per-thread counts
         int x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -377,26 +412,29 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
         } else {
             long long pos = tsum[tile] + x - sum;
             for (int w = 0; w < warp; ++w) pos += s_wsum[w];
-#pragma unroll
+            int i = 0;
             for (int q = 0; q < kKPer; ++q) {
-                if (rr[q] < 0) continue;
-                const long long w = w0 + (long long)tid * kKPer + q;
-                if (tw[q] == 0) {
+                const long long w = wt + q;
+                if (w >= w1) break;
+                const KWin a = ktab_window<K>(w, i, nw, rb, n_rec, s_wp, s_sr, wpre, srec, t_sym,
+                                              jlo, nsym, klut);
+                if (a.r < 0) continue;
+                if (a.t == 0) {
                     // the record's first window: its offset, and that of the
                     // empty records just before it
-                    long long r = rr[q];
+                    long long r = a.r;
                     id_offsets[r] = pos;
                     while (r > 0 && wpre[r - 1] == w) id_offsets[--r] = pos;
                 }
-                if (cnt[q] == 1 && ent[q] >= 0) {
-                    if (pos < ids_cap) out[pos] = ent[q];
+                if (a.cnt == 1 && a.ent >= 0) {
+                    if (pos < ids_cap) out[pos] = a.ent;
                 } else {
-                    for (int i = 0; i < cnt[q]; ++i) {
-                        const int d = s_sym[jw[q] + i];
-                        if (pos + i < ids_cap) out[pos + i] = base.b[d < 5 ? d : 4];
+                    for (int y = 0; y < a.cnt; ++y) {
+                        const int d = t_sym[a.j + y];
+                        if (pos + y < ids_cap) out[pos + y] = base.b[d < 5 ? d : 4];
                     }
                 }
-                pos += cnt[q];
+                pos += a.cnt;
             }
         }
         __syncthreads();  // shared memory is reused by the next tile
