@@ -229,6 +229,18 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
         if (e == cudaSuccess)
             e = cudaMemcpy(h->d_klut, h->klut_host.data(), sizeof(int32_t) * (size_t)n_index,
                            cudaMemcpyHostToDevice);
+        // a u16 copy that fits shared memory (31 KB for k = 6), padded to 16 bytes
+        bool small = k <= 6;
+        for (long long i = 0; small && i < n_index; ++i) small = h->klut_host[i] < 0xFFFF;
+        if (e == cudaSuccess && small) {
+            std::vector<uint16_t> t16((size_t)((n_index + 7) / 8 * 8), 0xFFFF);
+            for (long long i = 0; i < n_index; ++i)
+                t16[i] = h->klut_host[i] < 0 ? (uint16_t)0xFFFF : (uint16_t)h->klut_host[i];
+            e = cudaMalloc(&h->d_klut16, sizeof(uint16_t) * t16.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h->d_klut16, t16.data(), sizeof(uint16_t) * t16.size(),
+                               cudaMemcpyHostToDevice);
+        }
     }
     if (e != cudaSuccess) {
         std::string m = std::string("CUDA setup failed: ") + cudaGetErrorString(e);
@@ -259,6 +271,7 @@ void dnatok_destroy(dnatok_handle *h) {
     ovl_destroy(h);
     dec_destroy(h);
     cudaFree(h->d_klut);
+    cudaFree(h->d_klut16);
     cudaFree(h->d_lut);
     cudaFree(h->d_desc);
     cudaFree(h->d_tile_rec);

@@ -77,18 +77,37 @@ __global__ void __launch_bounds__(kDThreads) dec_tile_kernel(DecArgs a) {
     __shared__ int s_wsum[kDThreads / 32], s_winv[kDThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n_tiles = (a.n_ids + kDT - 1) / kDT;
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // a contiguous run of tiles per CTA: the records starting in one tile
+    // begin where the previous tile's ended
+    const long long t_begin = (long long)blockIdx.x * n_tiles / gridDim.x;
+    const long long t_end = (long long)(blockIdx.x + 1) * n_tiles / gridDim.x;
+    for (long long tile = t_begin; tile < t_end; ++tile) {
         const long long t0 = tile * kDT;
         const long long t1 = (t0 + kDT < a.n_ids) ? t0 + kDT : a.n_ids;
         const bool need_rec = (MODE == DEC_OVL) || EMIT;
         if (need_rec) {
-            // the records starting in [t0, t1): one warp searches each end
+            // the records starting in [t0, t1): [s_ra, s_rb)
+            if (tile == t_begin) {
+                if (warp == 0) {
+                    const long long r = warp_first_ge(a.keys, a.n_rec, t0);
+                    if (lane == 0) s_ra = r < a.n_rec ? r : a.n_rec;
+                }
+                __syncthreads();
+            } else if (tid == 0) {
+                s_ra = s_rb;
+            }
             if (warp == 0) {
-                const long long r = warp_first_ge(a.keys, a.n_rec, t0);
-                if (lane == 0) s_ra = r < a.n_rec ? r : a.n_rec;
-            } else if (warp == 1) {
-                const long long r = warp_first_ge(a.keys, a.n_rec, t1);
-                if (lane == 0) s_rb = r < a.n_rec + 1 ? r : a.n_rec + 1;
+                // forward from s_ra, 32 offsets per round (offsets are sorted)
+                long long r = (tile == t_begin) ? s_ra : s_rb;
+                while (true) {
+                    const long long idx = r + lane;
+                    const unsigned m = __ballot_sync(0xffffffffu, idx <= a.n_rec && a.keys[idx] < t1);
+                    const int c = __popc(m);
+                    r += c;
+                    if (c < 32) break;
+                }
+                __syncwarp();
+                if (lane == 0) s_rb = r;
             }
             if (MODE == DEC_OVL)
                 for (int i = tid; i < kDT; i += kDThreads) s_first[i] = 0;

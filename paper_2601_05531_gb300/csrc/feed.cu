@@ -93,10 +93,7 @@ dnatok_status feed_args_ok(const int32_t *ids_d, const int64_t *id_offsets_d, in
 // ------------------------------------------------------ reverse complement
 
 constexpr int kRThreads = 256;
-constexpr int kRChunk = 16;                          // output bytes per chunk
-constexpr int kRPer = 4;                             // chunks per thread and tile
-constexpr int kRTile = kRThreads * kRChunk * kRPer;  // output bytes per tile (16 KB)
-constexpr int kRRW = 64;                             // records kept in shared memory
+constexpr int kRStep = 512;  // bytes per warp step, 16 per lane
 
 __device__ __forceinline__ uint8_t comp_of(int b) {
     switch (b) {
@@ -110,123 +107,77 @@ __device__ __forceinline__ uint8_t comp_of(int b) {
     }
 }
 
-// Largest r in [0, n - 1] with so[r] <= p (so non-decreasing, so[0] <= p).
-__device__ long long rec_of(const long long *so, long long n, long long p) {
-    long long lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const long long mid = (lo + hi + 1) >> 1;
-        if (so[mid] <= p) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Each CTA walks a contiguous run of 16 KB tiles of the output, keeping a
-// window of up to 64 record offsets in shared memory (searched again only
-// when a tile starts past it).  Each thread writes four 16-byte chunks
-// [p, p + 16) of a tile.  A chunk inside one record with a 16-byte aligned
-// output takes the fast path: the 16 mirrored input bytes come from four or
-// five aligned words (all chunks' loads issued before any store), are
-// shifted into place, reversed and complemented through a shared table, and
-// leave in one 16-byte store.  Other chunks go byte by byte.
+// Warp-streamed: each warp owns the output range [B0, B1) (B0 a multiple of
+// 512) and walks it in 512-byte steps, lane l writing the 16 bytes
+// [p, p + 16), p = step + 16 l.  The record [s, e) of the step is kept in
+// registers (the same in every lane) and looked up again, by a one-warp
+// search, only when a step starts past it.  A chunk inside the record with a
+// 16-byte aligned output takes the fast path: the 16 mirrored input bytes
+// come from four or five aligned words, are shifted into place, reversed
+// and complemented through a shared table, and leave in one 16-byte store.
+// Other chunks (record boundaries, the end, unaligned output) go byte by
+// byte.  No block-wide barrier after the table is built.
 __global__ void __launch_bounds__(kRThreads) revcomp_kernel(const uint8_t *__restrict__ in,
                                                             long long n,
                                                             const long long *__restrict__ so,
                                                             long long n_seq,
-                                                            uint8_t *__restrict__ out, int vec_out) {
+                                                            uint8_t *__restrict__ out, int vec_out,
+                                                            long long per_warp) {
     __shared__ uint8_t s_comp[256];
-    __shared__ long long s_so[kRRW + 1];
-    __shared__ long long s_rb;
-    __shared__ int s_nw;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     s_comp[tid] = comp_of(tid);
-    const long long n_tiles = (n + kRTile - 1) / kRTile;
-    const long long t_begin = (long long)blockIdx.x * n_tiles / gridDim.x;
-    const long long t_end = (long long)(blockIdx.x + 1) * n_tiles / gridDim.x;
-    for (long long tile = t_begin; tile < t_end; ++tile) {
-        const long long p0 = tile * kRTile;
-        // (the previous tile ended with a barrier: every thread reads the same window)
-        const bool reuse = tile > t_begin && s_so[0] <= p0 && (p0 < s_so[s_nw] || s_rb + s_nw >= n_seq);
-        if (!reuse) {
-            __syncthreads();
-            if (tid < 32) {
-                const long long rb = dnatok::warp_find_le(so, n_seq, p0);
-                if (tid == 0) {
-                    s_rb = rb;
-                    s_nw = (n_seq - rb < kRRW) ? (int)(n_seq - rb) : kRRW;
-                }
-            }
-            __syncthreads();
-            for (int l = tid; l <= s_nw; l += kRThreads) s_so[l] = so[s_rb + l];
-            __syncthreads();
-        }
-        const long long rb = s_rb;
-        const int nw = s_nw;
-        long long cs[kRPer], ce[kRPer];
-        bool fast[kRPer];
-        unsigned w[kRPer][5], sh[kRPer];
+    __syncthreads();
+    const long long gw = ((long long)blockIdx.x * kRThreads + tid) >> 5;
+    const long long B0 = gw * per_warp;
+    if (B0 >= n) return;
+    const long long B1 = (B0 + per_warp < n) ? B0 + per_warp : n;
+    long long r = dnatok::warp_find_le(so, n_seq, B0);
+    long long s = so[r], e = so[r + 1];
+    for (long long p0 = B0; p0 < B1; p0 += kRStep) {
+        const long long p = p0 + 16 * lane;
+        if (vec_out && p < B1 && p >= s && p + 16 <= e && s >= 0 && e <= n) {
+            // input bytes [a, a + 16) mirror output bytes [p, p + 16)
+            const uintptr_t ua = reinterpret_cast<uintptr_t>(in + (s + e - p - 16));
+            const unsigned *wp = reinterpret_cast<const unsigned *>(ua & ~(uintptr_t)3);
+            const unsigned sh = (unsigned)(ua & 3) * 8u;
+            unsigned w[5];
 #pragma unroll
-        for (int h = 0; h < kRPer; ++h) {
-            const long long p = p0 + ((long long)h * kRThreads + tid) * kRChunk;
-            long long s, e;  // the record holding p
-            if (p >= s_so[nw] && rb + nw < n_seq) {
-                const long long r = rec_of(so, n_seq, p < n ? p : n - 1);
-                s = so[r];
-                e = so[r + 1];
-            } else {
-                int lo = 0, hi = nw - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_so[mid] <= p) lo = mid; else hi = mid - 1;
-                }
-                s = s_so[lo];
-                e = s_so[lo + 1];
-            }
-            cs[h] = s;
-            ce[h] = e;
-            fast[h] = vec_out && p >= s && p + kRChunk <= e && s >= 0 && e <= n;
-            sh[h] = 0;
-            if (fast[h]) {
-                // input bytes [a, a + 16) mirror output bytes [p, p + 16)
-                const uintptr_t ua = reinterpret_cast<uintptr_t>(in + (s + e - p - kRChunk));
-                const unsigned *wp = reinterpret_cast<const unsigned *>(ua & ~(uintptr_t)3);
-                sh[h] = (unsigned)(ua & 3) * 8u;
+            for (int i = 0; i < 4; ++i) w[i] = __ldg(wp + i);
+            // the fifth word holds input bytes only when the start is unaligned
+            w[4] = sh ? __ldg(wp + 4) : 0u;
+            uint4 v;
+            unsigned *vv = reinterpret_cast<unsigned *>(&v);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) w[h][i] = __ldg(wp + i);
-                // the fifth word holds input bytes only when the start is unaligned
-                w[h][4] = sh[h] ? __ldg(wp + 4) : 0u;
+            for (int j = 0; j < 4; ++j) {
+                // output word j = input bytes 4(3-j) .. 4(3-j)+3, reversed
+                const unsigned y = __funnelshift_r(w[3 - j], w[4 - j], sh);
+                vv[j] = (unsigned)s_comp[y >> 24] | ((unsigned)s_comp[(y >> 16) & 0xFFu] << 8) |
+                        ((unsigned)s_comp[(y >> 8) & 0xFFu] << 16) | ((unsigned)s_comp[y & 0xFFu] << 24);
+            }
+            *reinterpret_cast<uint4 *>(out + p) = v;
+        } else if (p < B1) {
+            // a record boundary (or the end) inside the chunk: walk forward
+            // from the step's record, one offset per record passed
+            long long rr = r, ss = s, ee = e;
+            for (int q = 0; q < 16; ++q) {
+                const long long P = p + q;
+                if (P >= B1) break;
+                while (P >= ee && rr + 1 < n_seq) {
+                    ++rr;
+                    ss = ee;
+                    ee = so[rr + 1];
+                }
+                const long long m = ss + ee - 1 - P;
+                if (P >= ss && P < ee && m >= 0 && m < n) out[P] = s_comp[in[m]];
             }
         }
-#pragma unroll
-        for (int h = 0; h < kRPer; ++h) {
-            const long long p = p0 + ((long long)h * kRThreads + tid) * kRChunk;
-            if (fast[h]) {
-                uint4 v;
-                unsigned *vv = reinterpret_cast<unsigned *>(&v);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    // output word j = input bytes 4(3-j) .. 4(3-j)+3, reversed
-                    const unsigned y = __funnelshift_r(w[h][3 - j], w[h][4 - j], sh[h]);
-                    vv[j] = (unsigned)s_comp[y >> 24] | ((unsigned)s_comp[(y >> 16) & 0xFFu] << 8) |
-                            ((unsigned)s_comp[(y >> 8) & 0xFFu] << 16) |
-                            ((unsigned)s_comp[y & 0xFFu] << 24);
-                }
-                *reinterpret_cast<uint4 *>(out + p) = v;
-            } else {
-                for (int q = 0; q < kRChunk; ++q) {
-                    const long long P = p + q;
-                    if (P >= n) break;
-                    long long ss = cs[h], ee = ce[h];
-                    if (!(P >= ss && P < ee)) {
-                        const long long r = rec_of(so, n_seq, P);
-                        ss = so[r];
-                        ee = so[r + 1];
-                    }
-                    const long long m = ss + ee - 1 - P;
-                    if (P >= ss && P < ee && m >= 0 && m < n) out[P] = s_comp[in[m]];
-                }
-            }
+        // the next step's record (warp-uniform: s, e and p0 are the same in every lane)
+        const long long nx = p0 + kRStep;
+        if (nx < B1 && nx >= e) {
+            r = dnatok::warp_find_le(so, n_seq, nx);
+            s = so[r];
+            e = so[r + 1];
         }
-        __syncthreads();  // s_so may be replaced by the next tile
     }
 }
 
@@ -319,16 +270,19 @@ dnatok_status dnatok_reverse_complement(const uint8_t *bytes_d, int64_t n_bytes,
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 0;  // one resident wave: each CTA takes a contiguous run of tiles
+    // one resident wave of warps, each owning a 512-byte-aligned range
+    int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, revcomp_kernel, kRThreads, 0) !=
             cudaSuccess || per_sm < 1)
         per_sm = 1;
-    const long long tiles = (n_bytes + kRTile - 1) / kRTile;
-    long long grid = (long long)(sms > 0 ? sms : 1) * per_sm;
-    if (grid > tiles) grid = tiles;
+    const long long warps = (long long)(sms > 0 ? sms : 1) * per_sm * (kRThreads / 32);
+    long long per_warp = (n_bytes + warps - 1) / warps;
+    per_warp = (per_warp + kRStep - 1) / kRStep * kRStep;
+    const long long grid = ((n_bytes + per_warp - 1) / per_warp + kRThreads / 32 - 1) / (kRThreads / 32);
     const int vec = ((uintptr_t)out_d & 15u) == 0;
     revcomp_kernel<<<(unsigned)grid, kRThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        bytes_d, n_bytes, reinterpret_cast<const long long *>(seq_offsets_d), n_seq, out_d, vec);
+        bytes_d, n_bytes, reinterpret_cast<const long long *>(seq_offsets_d), n_seq, out_d, vec,
+        per_warp);
     return cudaGetLastError() == cudaSuccess ? DNATOK_OK : DNATOK_ERR_CUDA;
 }
 

@@ -52,6 +52,7 @@ struct dnatok_handle {
 
     // table-driven k-mers: kmer_lut (5^k ids) on the device, the single-symbol ids
     int32_t *d_klut = nullptr;
+    uint16_t *d_klut16 = nullptr;  // the same as u16 (0xFFFF = none) when k <= 6 and ids < 0xFFFF
     std::vector<int32_t> klut_host;
     int32_t base_ids[5] = {0, 1, 2, 3, 4};
     std::vector<int32_t> merges_host;  // BPE table, kept for the decode table

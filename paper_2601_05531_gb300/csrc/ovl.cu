@@ -27,11 +27,14 @@
 //   1. the symbol pass, as above;
 //   2. offsets_kernel<kOffsetsWindows>: record starts to the workspace and
 //      the window offsets wpre[r] = sum of ceil(L / k) over earlier records;
-//   3. ktab_tile_kernel<K, false>: per tile of 4096 windows, its token count;
+//   3. ktab_tile_kernel<K, false>: per tile of 2048 windows, its token count;
 //   4. tile_scan_kernel (one block): exclusive scan of the tile counts, the
 //      totals and the offsets of records with no window left;
 //   5. ktab_tile_kernel<K, true>: recounts, scans inside the block and writes
 //      the ids and the record offsets.
+// For k <= 6 with every id below 0xFFFF the table is held in each CTA's
+// shared memory as u16 (a blocked 6-mer vocabulary takes 31 KB).
+#include <atomic>
 #include <cstring>
 
 #include "handle.h"
@@ -177,12 +180,23 @@ __global__ void __launch_bounds__(kOPlanThreads) offsets_kernel(long long *offs,
     }
 }
 
+// Ids of overlapping k-mers, one tile of 4096 symbols at a time (a
+// contiguous run of tiles per CTA).  Phase 1: each thread slides a 2-bit
+// register window over 16 consecutive staged symbols (plus k - 1 of
+// lookahead), remembering where the last N-class symbol was, and writes the
+// 16 ids to shared memory (rows of 17 ints, so neighbouring threads hit
+// different banks).  Phase 2 walks the records overlapping the tile; the
+// starts of each that have a token (j + k <= record end) are a contiguous
+// run with contiguous output slots, which consecutive threads copy.
 template <int K>
 __global__ void __launch_bounds__(kOThreads) ovl_emit_kernel(const uint8_t *sym, const long long *srec,
                                                              const long long *offs, const long long *tot,
                                                              int *out, long long ids_cap) {
     constexpr unsigned UNK = 1u << (2 * K);
+    constexpr unsigned MASK = UNK - 1u;
+    constexpr int kPer = kOT / kOThreads;  // 16 starts per thread in phase 1
     __shared__ __align__(16) uint8_t s_sym[kOT + 32];
+    __shared__ int s_id[kOThreads * (kPer + 1)];
     __shared__ long long s_rs[kORW + 1], s_ob[kORW];
     __shared__ long long s_rb;
     __shared__ int s_nw;
@@ -217,33 +231,53 @@ __global__ void __launch_bounds__(kOThreads) ovl_emit_kernel(const uint8_t *sym,
             s_rs[l] = srec[rb + l];
             if (l < nw) s_ob[l] = offs[rb + l];
         }
-        __syncthreads();
-        int i = 0;  // this thread's window record (its j only grow)
-        for (long long j = j0 + tid; j < j1; j += kOThreads) {
-            while (i + 1 < nw && s_rs[i + 1] <= j) ++i;
-            long long rs, re, ob;
-            if (i + 1 == nw && rb + nw < n_rec && s_rs[nw] <= j) {
-                // more records start in this tile than the window holds
-                const long long r = ovl_find(srec, n_rec, j);
-                rs = srec[r];
-                re = srec[r + 1];
-                ob = offs[r];
-            } else {
-                rs = s_rs[i];
-                re = s_rs[i + 1];
-                ob = s_ob[i];
-            }
-            if (j + K <= re) {
-                const uint8_t *w = s_sym + (j - j0);
-                unsigned id = 0, bad = 0;
+        // phase 1: ids of starts j0 + 16 tid .. + 15 (bytes past the staged
+        // symbols only reach starts that phase 2 never writes)
+        {
+            const uint4 a = *reinterpret_cast<const uint4 *>(s_sym + kPer * tid);
+            const uint4 b = *reinterpret_cast<const uint4 *>(s_sym + kPer * tid + 16);
+            const unsigned wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            unsigned id = 0;
+            int last_n = -1000;  // position of the last N-class symbol
+            int *row = s_id + tid * (kPer + 1);
 #pragma unroll
-                for (int t = 0; t < K; ++t) {
-                    const unsigned c = w[t];
-                    id = (id << 2) | (c & 3u);
-                    bad |= c & 4u;
+            for (int p = 0; p < kPer + K - 1; ++p) {
+                const unsigned c = (wd[p >> 2] >> (8 * (p & 3))) & 0xFFu;
+                id = ((id << 2) | (c & 3u)) & MASK;
+                if (c >= 4u) last_n = p;
+                if (p >= K - 1) row[p - (K - 1)] = (last_n > p - K) ? (int)UNK : (int)id;
+            }
+        }
+        __syncthreads();
+        // phase 2: record by record over the tile; the starts of record r
+        // that have a token are [max(rs, j0), min(re - K + 1, j1)), and they
+        // go to consecutive slots from ob + (start - rs)
+        for (int l = 0;; ++l) {
+            long long rs, re, ob;
+            if (l < nw) {
+                rs = s_rs[l];
+                re = s_rs[l + 1];
+                ob = s_ob[l];
+            } else if (rb + l < n_rec) {  // more records start in this tile than the window holds
+                rs = srec[rb + l];
+                re = srec[rb + l + 1];
+                ob = offs[rb + l];
+            } else {
+                break;
+            }
+            if (rs >= j1) break;
+            const long long a = rs > j0 ? rs : j0;
+            const long long b = (re - K + 1 < j1) ? re - K + 1 : j1;
+            if (b > a) {
+                const int xa = (int)(a - j0), n = (int)(b - a);
+                const long long oa = ob + (a - rs);  // slot of start a
+                if (oa >= 0 && oa + n <= ids_cap) {
+                    int *dst = out + oa;
+                    for (int y = tid; y < n; y += kOThreads) {
+                        const int x = xa + y;
+                        dst[y] = s_id[(x >> 4) * (kPer + 1) + (x & 15)];
+                    }
                 }
-                const long long o = ob + (j - rs);
-                if (o >= 0 && o < ids_cap) out[o] = (int)(bad ? UNK : id);  // (malformed input)
             }
         }
         __syncthreads();  // the tile's shared memory is reused by the next
@@ -267,14 +301,27 @@ cudaError_t launch_emit(int k, unsigned grid, const uint8_t *sym, const long lon
 
 // ------------------------------------------------------ table-driven k-mers
 
-constexpr int kKW = 4096;       // windows per tile
+constexpr int kKW = 2048;       // windows per tile
 constexpr int kKThreads = 256;
 constexpr int kKPer = kKW / kKThreads;  // consecutive windows per thread
 constexpr int kKRW = 64;        // records of a tile kept in shared memory
+constexpr int kKTok = 2560;     // ids of a tile staged in shared memory by the emit
 
 struct KtabIds {
     int b[5];  // ids of the single symbols A C G T N
 };
+
+__host__ __device__ constexpr int pow5(int k) { return k == 0 ? 1 : 5 * pow5(k - 1); }
+
+// Dynamic shared memory of a ktab_tile_kernel: [u16 table (T16)] [symbols]
+// [staged ids (EMIT)], each part 16-byte aligned.
+__host__ __device__ constexpr int ktab_tab_bytes(int K, bool T16) {
+    return T16 ? ((pow5(K) * 2 + 15) / 16) * 16 : 0;
+}
+__host__ __device__ constexpr int ktab_sym_bytes(int K) { return ((kKW * K + 32 + 15) / 16) * 16; }
+__host__ __device__ constexpr int ktab_smem(int K, bool EMIT, bool T16) {
+    return ktab_tab_bytes(K, T16) + ktab_sym_bytes(K) + (EMIT ? kKTok * 4 + 16 : 0);
+}
 
 // One window: its record (r, its first window wp, its symbol range [sr, sr1))
 // from the tile's shared record window (advancing the caller's index i, as
@@ -284,12 +331,12 @@ struct KWin {
     int cnt, ent;       // tokens; the table entry of a whole window (-1: none)
 };
 
-template <int K>
+template <int K, bool T16>
 __device__ __forceinline__ KWin ktab_window(long long w, int &i, int nw, long long rb, long long n_rec,
                                             const long long *s_wp, const long long *s_sr,
                                             const long long *wpre, const long long *srec,
                                             const uint8_t *s_sym, long long jlo, long long nsym,
-                                            const int *klut) {
+                                            const int *klut, const uint16_t *s_tab) {
     KWin q;
     q.r = -1;
     q.cnt = 0;
@@ -324,11 +371,85 @@ __device__ __forceinline__ KWin ktab_window(long long w, int &i, int nw, long lo
             const int d = s_sym[q.j + x];
             index = index * 5 + (d < 5 ? d : 4);
         }
-        q.ent = __ldg(klut + index);
+        if (T16) {
+            const unsigned v = s_tab[index];
+            q.ent = v == 0xFFFFu ? -1 : (int)v;
+        } else {
+            q.ent = __ldg(klut + index);
+        }
         q.cnt = q.ent >= 0 ? 1 : K;
     } else {
         q.cnt = n_s;
     }
+    return q;
+}
+
+// A thread's walk over its consecutive windows in 32-bit tile-local terms:
+// record i of the tile's shared window, j = the window's first symbol in the
+// staged symbols, rem = symbols of the record from j on (clamped).  Set up
+// once per thread; each window then costs a few int operations.
+struct KCursor {
+    int i, j, rem;
+    bool first;  // the window is its record's first
+};
+
+template <int K>
+__device__ __forceinline__ KCursor kc_init(long long w, int nw, const long long *s_wp,
+                                           const long long *s_sr, long long jlo) {
+    KCursor c;
+    int i = 0;
+    while (i + 1 < nw && s_wp[i + 1] <= w) ++i;
+    const long long t = w - s_wp[i];
+    const long long rem = (s_sr[i + 1] - s_sr[i]) - t * K;
+    c.i = i;
+    c.j = (int)(s_sr[i] + t * K - jlo);
+    c.rem = (int)(rem < (1ll << 30) ? rem : (1ll << 30));
+    c.first = (t == 0);
+    return c;
+}
+
+// The window at the cursor (then advanced by one window), or cnt = 0 with
+// r = -1 past the shared window's records or on malformed input.
+template <int K, bool T16>
+__device__ __forceinline__ KWin kc_window(KCursor &c, int nw, long long rb, const long long *s_sr,
+                                          long long jlo, const uint8_t *s_sym, long long nsym,
+                                          const int *klut, const uint16_t *s_tab) {
+    KWin q;
+    q.r = -1;
+    q.cnt = 0;
+    q.ent = -1;
+    while (c.rem <= 0 && c.i + 1 < nw) {  // the record's windows are used up: the next record's
+        ++c.i;
+        const long long len = s_sr[c.i + 1] - s_sr[c.i];
+        c.j = (int)(s_sr[c.i] - jlo);
+        c.rem = (int)(len < (1ll << 30) ? len : (1ll << 30));
+        c.first = true;
+    }
+    const int n_s = c.rem >= K ? K : c.rem;
+    if (n_s < 1 || c.j < 0 || c.j + n_s > nsym) return q;  // (malformed input)
+    q.r = rb + c.i;
+    q.t = c.first ? 0 : 1;
+    q.j = c.j;
+    if (n_s == K) {
+        int index = 0;
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            const int d = s_sym[c.j + x];
+            index = index * 5 + (d < 5 ? d : 4);
+        }
+        if (T16) {
+            const unsigned v = s_tab[index];
+            q.ent = v == 0xFFFFu ? -1 : (int)v;
+        } else {
+            q.ent = __ldg(klut + index);
+        }
+        q.cnt = q.ent >= 0 ? 1 : K;
+    } else {
+        q.cnt = n_s;
+    }
+    c.j += K;
+    c.rem -= K;
+    c.first = false;
     return q;
 }
 
@@ -337,62 +458,115 @@ __device__ __forceinline__ KWin ktab_window(long long w, int &i, int nw, long lo
 // tile's exclusive token offset, and the record offsets of records whose
 // first window is here).  Each thread takes kKPer consecutive windows; the
 // emit recounts them after the block scan instead of keeping them in
-// registers.
-template <int K, bool EMIT>
+// registers, assembles the tile's ids in shared memory when they fit, and
+// writes them out in aligned 16-byte stores.  T16: the ids table lives in
+// shared memory as u16 (k <= 6, every id below 0xFFFF, 0xFFFF = no entry),
+// loaded once per CTA; otherwise each window reads kmer_lut from global
+// memory.
+template <int K, bool EMIT, bool T16>
 __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
     const uint8_t *sym, const long long *srec, const long long *wpre, const long long *tot,
-    const int *klut, KtabIds base, long long *tsum, int *out, long long ids_cap,
-    long long *id_offsets) {
-    __shared__ __align__(16) uint8_t s_sym[kKW * K + 32];
+    const int *klut, const uint16_t *klut16, KtabIds base, long long *tsum, int *out,
+    long long ids_cap, long long *id_offsets) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    uint16_t *s_tab = reinterpret_cast<uint16_t *>(dyn);
+    uint8_t *s_sym = dyn + ktab_tab_bytes(K, T16);
+    int *s_tok = reinterpret_cast<int *>(dyn + ktab_tab_bytes(K, T16) + ktab_sym_bytes(K));
     __shared__ long long s_wp[kKRW + 1], s_sr[kKRW + 1];
     __shared__ long long s_rb, s_jlo, s_jhi;
+    __shared__ int s_nw;
     __shared__ int s_wsum[kKThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n_rec = tot[1];
     if (n_rec < 1) return;
+    if (T16) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(klut16);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_tab);
+        for (int c = tid; c < ktab_tab_bytes(K, T16) / 16; c += kKThreads) dst[c] = src[c];
+        // (ordered before the first read by the barrier after the staging below)
+    }
     const long long n_win = wpre[n_rec];
+    const long long n_sym = srec[n_rec];
     const long long n_tiles = (n_win + kKW - 1) / kKW;
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // a contiguous run of tiles per CTA, so the shared record window of one
+    // tile usually covers the next
+    const long long t_begin = (long long)blockIdx.x * n_tiles / gridDim.x;
+    const long long t_end = (long long)(blockIdx.x + 1) * n_tiles / gridDim.x;
+    for (long long tile = t_begin; tile < t_end; ++tile) {
         const long long w0 = tile * kKW;
         const long long w1 = (w0 + kKW < n_win) ? w0 + kKW : n_win;
-        // the records holding w0 and w1 (one warp each), and the tile's symbols
-        if (warp == 0) {
-            const long long rb = warp_find_le(wpre, n_rec, w0);
-            if (lane == 0) {
-                s_rb = rb;
-                s_jlo = srec[rb] + (w0 - wpre[rb]) * K;
-            }
-        } else if (warp == 1) {
+        // (the previous tile ended with a barrier: every thread sees the same window)
+        const bool reuse = tile > t_begin && s_wp[0] <= w0 &&
+                           (s_rb + s_nw >= n_rec || s_wp[s_nw] > w1);
+        long long rb, jlo, jhi;
+        int nw;
+        if (reuse) {
+            // the symbols of w0 and w1 from the window, in every thread
+            rb = s_rb;
+            nw = s_nw;
+            int i0 = 0;
+            while (i0 + 1 < nw && s_wp[i0 + 1] <= w0) ++i0;
+            jlo = s_sr[i0] + (w0 - s_wp[i0]) * K;
             if (w1 >= n_win) {
-                if (lane == 0) s_jhi = srec[n_rec];
+                jhi = n_sym;
             } else {
-                const long long r1 = warp_find_le(wpre, n_rec, w1);
-                if (lane == 0) s_jhi = srec[r1] + (w1 - wpre[r1]) * K;
+                int i1 = i0;
+                while (i1 + 1 < nw && s_wp[i1 + 1] <= w1) ++i1;
+                jhi = s_sr[i1] + (w1 - s_wp[i1]) * K;
             }
+        } else {
+            // the records holding w0 and w1 (one warp each), then the window
+            if (warp == 0) {
+                const long long r0 = warp_find_le(wpre, n_rec, w0);
+                if (lane == 0) {
+                    s_rb = r0;
+                    s_jlo = srec[r0] + (w0 - wpre[r0]) * K;
+                }
+            } else if (warp == 1) {
+                if (w1 >= n_win) {
+                    if (lane == 0) s_jhi = n_sym;
+                } else {
+                    const long long r1 = warp_find_le(wpre, n_rec, w1);
+                    if (lane == 0) s_jhi = srec[r1] + (w1 - wpre[r1]) * K;
+                }
+            }
+            __syncthreads();
+            rb = s_rb;
+            jlo = s_jlo;
+            jhi = s_jhi;
+            nw = (n_rec - rb < kKRW) ? (int)(n_rec - rb) : kKRW;
+            for (int l = tid; l <= nw; l += kKThreads) {
+                s_wp[l] = wpre[rb + l];
+                s_sr[l] = srec[rb + l];
+            }
+            if (tid == 0) s_nw = nw;
         }
-        __syncthreads();
-        const long long rb = s_rb, jlo = s_jlo;
-        const int nw = (n_rec - rb < kKRW) ? (int)(n_rec - rb) : kKRW;
-        long long nsym = s_jhi - jlo;
+        long long nsym = jhi - jlo;
         if (nsym > (long long)kKW * K) nsym = (long long)kKW * K;  // (malformed input)
         if (nsym < 0) nsym = 0;
-        for (int l = tid; l <= nw; l += kKThreads) {
-            s_wp[l] = wpre[rb + l];
-            s_sr[l] = srec[rb + l];
-        }
         const int lead = stage_symbols(s_sym, sym, jlo, nsym, tid, kKThreads);
         __syncthreads();
         const uint8_t *t_sym = s_sym + lead;  // t_sym[x] = sym[jlo + x]
 
         const long long wt = w0 + (long long)tid * kKPer;
+        // more records start in this tile than the shared window holds: the
+        // general per-window path (searches past the window)
+        const bool dense = rb + nw < n_rec && s_wp[nw] < w1;
         int sum = 0;
-        {
+        if (!dense) {
+            if (wt < w1) {
+                KCursor c = kc_init<K>(wt, nw, s_wp, s_sr, jlo);
+                const int nq = (int)((w1 - wt < kKPer) ? w1 - wt : kKPer);
+                for (int q = 0; q < nq; ++q)
+                    sum += kc_window<K, T16>(c, nw, rb, s_sr, jlo, t_sym, nsym, klut, s_tab).cnt;
+            }
+        } else {
             int i = 0;
             for (int q = 0; q < kKPer; ++q) {
                 const long long w = wt + q;
                 if (w >= w1) break;
-                sum += ktab_window<K>(w, i, nw, rb, n_rec, s_wp, s_sr, wpre, srec, t_sym, jlo,
-                                      nsym, klut).cnt;
+                sum += ktab_window<K, T16>(w, i, nw, rb, n_rec, s_wp, s_sr, wpre, srec, t_sym, jlo,
+                                           nsym, klut, s_tab).cnt;
             }
         }
         int x = sum;
@@ -410,15 +584,28 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
                 tsum[tile] = tt;
             }
         } else {
-            long long pos = tsum[tile] + x - sum;
-            for (int w = 0; w < warp; ++w) pos += s_wsum[w];
+            int loc = x - sum, total = 0;
+            for (int w = 0; w < kKThreads / 32; ++w) {
+                if (w < warp) loc += s_wsum[w];
+                total += s_wsum[w];
+            }
+            const long long tbase = tsum[tile];
+            // staged: ids go to s_tok[shift + loc], shift being the
+            // misalignment (in ids) of the tile's first output
+            const int shift = (int)((reinterpret_cast<uintptr_t>(out + tbase) >> 2) & 3u);
+            const bool staged = total + shift <= kKTok;
             int i = 0;
+            KCursor c{0, 0, 0, false};
+            if (!dense && wt < w1) c = kc_init<K>(wt, nw, s_wp, s_sr, jlo);
             for (int q = 0; q < kKPer; ++q) {
                 const long long w = wt + q;
                 if (w >= w1) break;
-                const KWin a = ktab_window<K>(w, i, nw, rb, n_rec, s_wp, s_sr, wpre, srec, t_sym,
-                                              jlo, nsym, klut);
+                const KWin a = dense ? ktab_window<K, T16>(w, i, nw, rb, n_rec, s_wp, s_sr, wpre,
+                                                           srec, t_sym, jlo, nsym, klut, s_tab)
+                                     : kc_window<K, T16>(c, nw, rb, s_sr, jlo, t_sym, nsym, klut,
+                                                         s_tab);
                 if (a.r < 0) continue;
+                const long long pos = tbase + loc;
                 if (a.t == 0) {
                     // the record's first window: its offset, and that of the
                     // empty records just before it
@@ -426,43 +613,109 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
                     id_offsets[r] = pos;
                     while (r > 0 && wpre[r - 1] == w) id_offsets[--r] = pos;
                 }
-                if (a.cnt == 1 && a.ent >= 0) {
+                if (staged) {
+                    int *d = s_tok + shift + loc;
+                    if (a.cnt == 1 && a.ent >= 0) {
+                        d[0] = a.ent;
+                    } else {
+                        for (int y = 0; y < a.cnt; ++y) {
+                            const int dg = t_sym[a.j + y];
+                            d[y] = base.b[dg < 5 ? dg : 4];
+                        }
+                    }
+                } else if (a.cnt == 1 && a.ent >= 0) {
                     if (pos < ids_cap) out[pos] = a.ent;
                 } else {
                     for (int y = 0; y < a.cnt; ++y) {
-                        const int d = t_sym[a.j + y];
-                        if (pos + y < ids_cap) out[pos + y] = base.b[d < 5 ? d : 4];
+                        const int dg = t_sym[a.j + y];
+                        if (pos + y < ids_cap) out[pos + y] = base.b[dg < 5 ? dg : 4];
                     }
                 }
-                pos += a.cnt;
+                loc += a.cnt;
+            }
+            if (staged) {
+                __syncthreads();
+                const int span = shift + total;
+                int *g = out + (tbase - shift);  // 16-byte aligned
+                const long long lim = ids_cap - (tbase - shift);  // ids of g inside the buffer
+                for (int c = tid; c < (span + 3) >> 2; c += kKThreads) {
+                    const int lo = c * 4, hi = lo + 4;
+                    if (lo >= shift && hi <= span && hi <= lim) {
+                        *reinterpret_cast<int4 *>(g + lo) = *reinterpret_cast<const int4 *>(s_tok + lo);
+                    } else {
+                        for (int y = lo > shift ? lo : shift; y < (hi < span ? hi : span); ++y)
+                            if (y < lim) g[y] = s_tok[y];
+                    }
+                }
             }
         }
         __syncthreads();  // shared memory is reused by the next tile
     }
 }
 
-cudaError_t launch_ktab(int k, bool emit, unsigned grid, const uint8_t *sym, const long long *srec,
-                        const long long *wpre, const long long *tot, const int *klut,
+// Resident CTAs per SM of one instantiation; the first call also raises its
+// dynamic shared memory limit (dnatok_reserve makes that call, so a first
+// encode under stream capture finds it done).
+template <int K, bool EMIT, bool T16>
+cudaError_t ktab_init(int *per_sm_out) {
+    constexpr int smem = ktab_smem(K, EMIT, T16);
+    static std::atomic<int> per_sm{0};
+    if (per_sm.load() == 0) {
+        cudaError_t e = cudaFuncSetAttribute(ktab_tile_kernel<K, EMIT, T16>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ktab_tile_kernel<K, EMIT, T16>,
+                                                          kKThreads, smem);
+        if (e != cudaSuccess) return e;
+        per_sm.store(n > 0 ? n : 1);
+    }
+    *per_sm_out = per_sm.load();
+    return cudaSuccess;
+}
+
+template <int K, bool EMIT, bool T16>
+cudaError_t launch_ktab_k(int sm_count, long long max_tiles, const uint8_t *sym,
+                          const long long *srec, const long long *wpre, const long long *tot,
+                          const int *klut, const uint16_t *klut16, KtabIds base, long long *tsum,
+                          int *out, long long cap, long long *id_offsets, cudaStream_t s) {
+    constexpr int smem = ktab_smem(K, EMIT, T16);
+    int per_sm = 1;
+    cudaError_t e = ktab_init<K, EMIT, T16>(&per_sm);
+    if (e != cudaSuccess) return e;
+    if (!sym) return cudaSuccess;  // (initialization only)
+    long long grid = (long long)sm_count * per_sm;
+    if (grid > max_tiles) grid = max_tiles;
+    if (grid < 1) grid = 1;
+    ktab_tile_kernel<K, EMIT, T16><<<(unsigned)grid, kKThreads, smem, s>>>(
+        sym, srec, wpre, tot, klut, klut16, base, tsum, out, cap, id_offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ktab(int k, bool emit, bool t16, int sm_count, long long max_tiles,
+                        const uint8_t *sym, const long long *srec, const long long *wpre,
+                        const long long *tot, const int *klut, const uint16_t *klut16,
                         KtabIds base, long long *tsum, int *out, long long cap,
                         long long *id_offsets, cudaStream_t s) {
-    switch (k) {
+#define DNATOK_KT(KK, EM, TT)                                                                  \
+    return launch_ktab_k<KK, EM, TT>(sm_count, max_tiles, sym, srec, wpre, tot, klut, klut16,  \
+                                     base, tsum, out, cap, id_offsets, s)
 #define DNATOK_KT_K(KK)                                                                        \
     case KK:                                                                                   \
-        if (emit)                                                                              \
-            ktab_tile_kernel<KK, true><<<grid, kKThreads, 0, s>>>(sym, srec, wpre, tot, klut,  \
-                                                                  base, tsum, out, cap,        \
-                                                                  id_offsets);                 \
-        else                                                                                   \
-            ktab_tile_kernel<KK, false><<<grid, kKThreads, 0, s>>>(sym, srec, wpre, tot, klut, \
-                                                                   base, tsum, out, cap,       \
-                                                                   id_offsets);                \
-        break;
+        if (emit) {                                                                            \
+            if (t16 && KK <= 6) DNATOK_KT(KK, true, (KK <= 6));                                \
+            DNATOK_KT(KK, true, false);                                                        \
+        } else {                                                                               \
+            if (t16 && KK <= 6) DNATOK_KT(KK, false, (KK <= 6));                               \
+            DNATOK_KT(KK, false, false);                                                       \
+        }
+    switch (k) {
         DNATOK_KT_K(1) DNATOK_KT_K(2) DNATOK_KT_K(3) DNATOK_KT_K(4) DNATOK_KT_K(5)
         DNATOK_KT_K(6) DNATOK_KT_K(7) DNATOK_KT_K(8) DNATOK_KT_K(9) DNATOK_KT_K(10)
-#undef DNATOK_KT_K
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+#undef DNATOK_KT_K
+#undef DNATOK_KT
 }
 
 void free_ovl(OvlState *o) {
@@ -497,6 +750,16 @@ dnatok_status ovl_reserve(dnatok_handle *h, long long max_bytes, long long max_o
         if (!h->ovl) return fail(h, DNATOK_ERR_NOMEM, "host allocation failed");
     }
     OvlState *o = h->ovl;
+    if (h->mode == DNATOK_KMER_TABLE) {
+        // launch limits of the table kernels (a no-op after the first time)
+        KtabIds none{};
+        for (int emit = 0; emit < 2; ++emit) {
+            cudaError_t e = launch_ktab(h->k, emit != 0, h->d_klut16 != nullptr, 1, 1, nullptr,
+                                        nullptr, nullptr, nullptr, nullptr, nullptr, none, nullptr,
+                                        nullptr, 0, nullptr, s);
+            if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer kernel setup");
+        }
+    }
     if (max_bytes <= o->cap_sym && max_offsets <= o->cap_srec && o->d_tot) return DNATOK_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
@@ -647,13 +910,12 @@ dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_by
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "window offsets launch");
     // 3-5. count, scan, emit
-    long long tiles = n_bytes / kKW + 1;
-    long long grid = (long long)h->sm_count * 8;
-    if (grid > tiles) grid = tiles;
+    const long long tiles = n_bytes / kKW + 1;
+    const bool t16 = h->d_klut16 != nullptr;
     KtabIds base;
     for (int d = 0; d < 5; ++d) base.b[d] = h->base_ids[d];
-    e = launch_ktab(h->k, false, (unsigned)grid, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,
-                    h->d_klut, base, o->d_tsum, ids_out_d, ids_capacity, offs, s);
+    e = launch_ktab(h->k, false, t16, h->sm_count, tiles, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,
+                    h->d_klut, h->d_klut16, base, o->d_tsum, ids_out_d, ids_capacity, offs, s);
     if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer count launch");
     tile_scan_kernel<<<1, kTileScanThreads, 0, s>>>(o->d_tsum, nullptr, o->d_wpre, o->d_tot + 1, 0,
                                                 nullptr, -1, kKW, offs,
@@ -661,8 +923,8 @@ dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_by
                                                 h->d_status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer scan launch");
-    e = launch_ktab(h->k, true, (unsigned)grid, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,
-                    h->d_klut, base, o->d_tsum, ids_out_d, ids_capacity, offs, s);
+    e = launch_ktab(h->k, true, t16, h->sm_count, tiles, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,
+                    h->d_klut, h->d_klut16, base, o->d_tsum, ids_out_d, ids_capacity, offs, s);
     if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer emit launch");
     return DNATOK_OK;
 }

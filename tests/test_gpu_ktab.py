@@ -224,3 +224,28 @@ def test_ktab_full_kmer_batch_4096(P):
     lut, base = synth.kmer_vocab(6, seed=49)
     data, offs = synth.kmer_batch_4096()
     same(run(P, data, 6, lut, base, offs), want(data, 6, lut, base, offs), "4096 sequences")
+
+
+@pytest.mark.parametrize("k", [2, 6])
+def test_ktab_wide_ids_global_table(P, k):
+    # ids that do not fit 16 bits keep the table in global memory
+    rng = np.random.default_rng(70 + k)
+    lut = rng.integers(0, 1 << 30, size=5 ** k).astype(np.int32)
+    lut[rng.random(5 ** k) < 0.2] = -1
+    base = rng.integers(0, 1 << 30, size=5).astype(np.int32)
+    data, offs = ragged(80 + k, 150, 0, 5000)
+    same(run(P, data, k, lut, base, offs), want(data, k, lut, base, offs), "k=%d" % k)
+
+
+def test_ktab_u16_boundary_ids(P):
+    # 0xFFFE is the largest id the shared-memory table holds; one id of
+    # 0xFFFF moves the table to global memory; both give the same ids
+    rng = np.random.default_rng(5)
+    data, offs = ragged(90, 100, 0, 4000)
+    for top in (0xFFFE, 0xFFFF):
+        lut = rng.integers(0, 1000, size=5 ** 3).astype(np.int32)
+        lut[7] = top
+        lut[rng.random(5 ** 3) < 0.3] = -1
+        lut[8] = top
+        base = np.array([0, 1, 2, 3, 4], np.int32)
+        same(run(P, data, 3, lut, base, offs), want(data, 3, lut, base, offs), "top %d" % top)
