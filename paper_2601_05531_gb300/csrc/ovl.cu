@@ -453,6 +453,46 @@ __device__ __forceinline__ KWin kc_window(KCursor &c, int nw, long long rb, cons
     return q;
 }
 
+// The kKPer whole windows of one record starting at staged symbol A (all in
+// shared memory): the span is read as 32-bit words and shifted into place
+// once, and each window's digits are then taken from registers at
+// compile-time positions (instead of k single-byte shared-memory loads per
+// window).  ent[q] = the table entry (-1: none), cnt[q] = 1 or K.
+template <int K, bool T16>
+__device__ __forceinline__ void ktab_fast_windows(const uint8_t *s_base, int A, const int *klut,
+                                                  const uint16_t *s_tab, int (&ent)[kKPer],
+                                                  int (&cnt)[kKPer]) {
+    constexpr int NB = kKPer * K;          // bytes of the span
+    constexpr int NW = (NB + 3) / 4 + 1;   // words read (one more for the shift)
+    const uint32_t *w32 = reinterpret_cast<const uint32_t *>(s_base + (A & ~3));
+    const unsigned sh = 8u * (unsigned)(A & 3);
+    uint32_t W[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) W[i] = w32[i];
+    uint32_t X[NW - 1];
+#pragma unroll
+    for (int i = 0; i < NW - 1; ++i) X[i] = __funnelshift_r(W[i], W[i + 1], sh);
+#pragma unroll
+    for (int q = 0; q < kKPer; ++q) {
+        int index = 0;
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            const int b = q * K + x;
+            const int d = (int)((X[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+            index = index * 5 + (d < 5 ? d : 4);
+        }
+        int e;
+        if (T16) {
+            const unsigned v = s_tab[index];
+            e = v == 0xFFFFu ? -1 : (int)v;
+        } else {
+            e = __ldg(klut + index);
+        }
+        ent[q] = e;
+        cnt[q] = e >= 0 ? 1 : K;
+    }
+}
+
 // One tile of windows [w0, w1): count (EMIT = false: the tile's token count
 // to tsum[tile]) or emit (EMIT = true: ids from tsum[tile], by then the
 // tile's exclusive token offset, and the record offsets of records whose
@@ -557,8 +597,16 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
             if (wt < w1) {
                 KCursor c = kc_init<K>(wt, nw, s_wp, s_sr, jlo);
                 const int nq = (int)((w1 - wt < kKPer) ? w1 - wt : kKPer);
-                for (int q = 0; q < nq; ++q)
-                    sum += kc_window<K, T16>(c, nw, rb, s_sr, jlo, t_sym, nsym, klut, s_tab).cnt;
+                if (nq == kKPer && c.rem >= kKPer * K && c.j >= 0 && c.j + kKPer * K <= nsym) {
+                    // all eight windows whole and in one record
+                    int ent[kKPer], cn[kKPer];
+                    ktab_fast_windows<K, T16>(s_sym, lead + c.j, klut, s_tab, ent, cn);
+#pragma unroll
+                    for (int q = 0; q < kKPer; ++q) sum += cn[q];
+                } else {
+                    for (int q = 0; q < nq; ++q)
+                        sum += kc_window<K, T16>(c, nw, rb, s_sr, jlo, t_sym, nsym, klut, s_tab).cnt;
+                }
             }
         } else {
             int i = 0;
@@ -597,7 +645,43 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
             int i = 0;
             KCursor c{0, 0, 0, false};
             if (!dense && wt < w1) c = kc_init<K>(wt, nw, s_wp, s_sr, jlo);
-            for (int q = 0; q < kKPer; ++q) {
+            const bool fast = !dense && wt + kKPer <= w1 && c.rem >= kKPer * K && c.j >= 0 &&
+                              c.j + kKPer * K <= nsym;
+            if (fast) {
+                // all eight windows whole and in one record (as in the count)
+                int ent[kKPer], cn[kKPer];
+                ktab_fast_windows<K, T16>(s_sym, lead + c.j, klut, s_tab, ent, cn);
+                if (c.first) {
+                    long long r = rb + c.i;
+                    const long long pos = tbase + loc;
+                    id_offsets[r] = pos;
+                    while (r > 0 && wpre[r - 1] == wt) id_offsets[--r] = pos;
+                }
+#pragma unroll
+                for (int q = 0; q < kKPer; ++q) {
+                    const long long pos = tbase + loc;
+                    if (staged) {
+                        int *d = s_tok + shift + loc;
+                        if (ent[q] >= 0) {
+                            d[0] = ent[q];
+                        } else {
+                            for (int y = 0; y < K; ++y) {
+                                const int dg = t_sym[c.j + q * K + y];
+                                d[y] = base.b[dg < 5 ? dg : 4];
+                            }
+                        }
+                    } else if (ent[q] >= 0) {
+                        if (pos < ids_cap) out[pos] = ent[q];
+                    } else {
+                        for (int y = 0; y < K; ++y) {
+                            const int dg = t_sym[c.j + q * K + y];
+                            if (pos + y < ids_cap) out[pos + y] = base.b[dg < 5 ? dg : 4];
+                        }
+                    }
+                    loc += cn[q];
+                }
+            }
+            for (int q = 0; q < (fast ? 0 : kKPer); ++q) {
                 const long long w = wt + q;
                 if (w >= w1) break;
                 const KWin a = dense ? ktab_window<K, T16>(w, i, nw, rb, n_rec, s_wp, s_sr, wpre,
