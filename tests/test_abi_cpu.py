@@ -60,3 +60,37 @@ def test_oracle_is_not_linked_into_library(lib):
     from paper_2601_05531_gb300 import binding
     out = subprocess.run(["nm", "-D", binding.lib_path()], capture_output=True, text=True).stdout
     assert "oracle_" not in out
+
+
+def test_microbatch_rows_rule_on_host(lib):
+    # Algorithm 2: b = min(B_emb, max(1, floor(M / T'))); a host-only call
+    from paper_2601_05531_gb300 import binding
+    cases = [((64, 100_000, 1000), 64), ((64, 10_000, 1000), 10), ((64, 999, 1000), 1),
+             ((1, 10 ** 9, 7), 1), ((512, 2 ** 18, 2048), 128)]
+    for args, want in cases:
+        assert binding.dnatok_microbatch_rows(*args) == want, args
+    for bad in ((0, 10, 10), (4, -1, 10), (4, 10, 0)):
+        with pytest.raises(binding.DnatokError):
+            binding.dnatok_microbatch_rows(*bad)
+
+
+def test_feed_and_revcomp_reject_bad_arguments_on_host(lib):
+    # argument checks happen before any CUDA call
+    import ctypes
+    from paper_2601_05531_gb300 import binding
+    off = (ctypes.c_int64 * 2)(0, 4)
+    ids = (ctypes.c_int32 * 4)()
+    p_off, p_ids = ctypes.addressof(off), ctypes.addressof(ids)
+    ERR_ARG = -1
+    L = binding.lib()
+    assert L.dnatok_feed(p_ids, p_off, 0, 1, 4, 0, 0, 2, None) == ERR_ARG        # width 2
+    assert L.dnatok_feed(p_ids, p_off, 0, 1, 4, 1 << 40, 0, 4, None) == ERR_ARG  # pad > int32
+    assert L.dnatok_feed(p_ids, 0, 0, 1, 4, 0, 0, 8, None) == ERR_ARG            # no offsets
+    assert L.dnatok_feed(p_ids, p_off, -1, 1, 4, 0, 0, 8, None) == ERR_ARG       # row_begin < 0
+    assert L.dnatok_feed(p_ids, p_off, 0, 1, 4, 0, 0, 8, None) == ERR_ARG        # no output
+    assert L.dnatok_reverse_complement(0, 10, p_off, 0, 0, None) == ERR_ARG      # bytes, no records
+    assert L.dnatok_reverse_complement(0, -1, p_off, 1, 0, None) == ERR_ARG      # negative size
+    assert L.dnatok_reverse_complement(0, 0, p_off, 1, 0, None) == 0             # empty: nothing to do
+    buf = (ctypes.c_uint8 * 32)()
+    b = ctypes.addressof(buf)
+    assert L.dnatok_reverse_complement(b, 16, p_off, 1, b + 8, None) == ERR_ARG  # overlapping
