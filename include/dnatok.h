@@ -425,6 +425,24 @@ DNATOK_API dnatok_status dnatok_feed_pipeline(const int32_t *ids_d, const int64_
                                               dnatok_cuda_stream consumer_stream,
                                               dnatok_feed_consumer consumer, void *user);
 
+/* --------------------------------------------------------------- shards */
+
+/*
+ * Byte-balanced contiguous record shards for encoding one batch with one
+ * process per GPU.  Records are independent, so rank i encodes records
+ * [bounds[i], bounds[i+1]) with no exchange on the data path; turning its
+ * local id offsets into global ones needs only the exclusive scan of the
+ * ranks' id counts (one integer per rank, done by the caller's collective).
+ * bounds[0] = 0, bounds[world_size] = n_seq, and bounds[i] is the first
+ * record that starts at or after i * n_bytes / world_size (records are never
+ * split; one that spans a split point stays with the earlier rank).
+ *   seq_offsets_host  n_seq + 1 non-decreasing int64 (HOST) with [0] = 0.
+ *   bounds_out        world_size + 1 int64 (HOST).
+ * Host only, no GPU work; DNATOK_ERR_ARG for bad arguments.
+ */
+DNATOK_API dnatok_status dnatok_shard_records(const int64_t *seq_offsets_host, int64_t n_seq,
+                                              int32_t world_size, int64_t *bounds_out);
+
 /* ------------------------------------------------------ no allocation */
 
 /*

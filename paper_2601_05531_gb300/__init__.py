@@ -13,7 +13,7 @@ from .binding import (BPE, CHAR, END_OF_STREAM, FASTA, HOST_PINNED, KMER, KMER_O
 
 __all__ = ["binding", "Tokenizer", "CHAR", "KMER", "KMER_OVERLAP", "KMER_TABLE", "BPE", "RAW", "FASTA",
            "DnatokError", "END_OF_STREAM", "NEW_RECORD", "HOST_PINNED", "build", "reverse_complement",
-           "feed", "microbatch_rows", "feed_pipeline"]
+           "feed", "microbatch_rows", "feed_pipeline", "shard_records", "global_id_offsets"]
 
 
 def build(force: bool = False) -> str:
@@ -223,3 +223,26 @@ def feed_pipeline(ids, id_offsets, token_len: int, id_pad: int, rows_per_batch: 
                                  bufs[1].data_ptr(), int(fs.cuda_stream), int(cs.cuda_stream),
                                  _consume)
     return bufs, fs
+
+
+def shard_records(seq_offsets, world_size: int):
+    """Byte-balanced contiguous record bounds (world_size + 1) for one
+    process per GPU; rank i encodes records bounds[i] .. bounds[i+1]."""
+    return binding.dnatok_shard_records(seq_offsets, world_size)
+
+
+def global_id_offsets(local_offsets, group=None):
+    """Turn a rank's local id offsets (its shard's n + 1 int64 offsets
+    starting at 0) into global ones: the exclusive scan of every rank's id
+    count, exchanged with one all_gather of one integer per rank (any
+    torch.distributed backend).  Returns (global offsets, total ids)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    mine = local_offsets[-1:].to(torch.int64).reshape(1)
+    counts = [torch.zeros_like(mine) for _ in range(ws)]
+    dist.all_gather(counts, mine, group=group)
+    counts = torch.cat(counts).cpu()
+    base = int(counts[:rank].sum())
+    return local_offsets + base, int(counts.sum())

@@ -140,6 +140,7 @@ def lib():
             "dnatok_reverse_complement": (_ST, [_P, _I64, _P, _I64, _P, _P]),
             "dnatok_feed": (_ST, [_P, _P, _I64, _I64, _I64, _I64, _P, ctypes.c_int32, _P]),
             "dnatok_microbatch_rows": (_ST, [_I64, _I64, _I64, ctypes.POINTER(_I64)]),
+            "dnatok_shard_records": (_ST, [_P, _I64, ctypes.c_int32, _P]),
             "dnatok_feed_pipeline": (_ST, [_P, _P, _I64, _I64, _I64, ctypes.c_int32, _I64, _P, _P,
                                            _P, _P, FEED_CONSUMER, _P]),
         }
@@ -453,3 +454,13 @@ def dnatok_feed_pipeline(ids_d: int, id_offsets_d: int, n_rows: int, token_len: 
     return check(lib().dnatok_feed_pipeline(ids_d, id_offsets_d, n_rows, token_len, id_pad,
                                             out_bytes, rows_per_batch, buf0_d, buf1_d,
                                             feed_stream, consumer_stream, cb, None))
+
+
+def dnatok_shard_records(seq_offsets, world_size: int):
+    """seq_offsets: n_seq + 1 host int64 (numpy-compatible).  Returns the
+    world_size + 1 record bounds as a numpy int64 array."""
+    import numpy as np
+    so = np.ascontiguousarray(seq_offsets, dtype=np.int64)
+    out = np.empty(world_size + 1, dtype=np.int64)
+    check(lib().dnatok_shard_records(so.ctypes.data, so.size - 1, world_size, out.ctypes.data))
+    return out

@@ -94,3 +94,34 @@ def test_feed_and_revcomp_reject_bad_arguments_on_host(lib):
     buf = (ctypes.c_uint8 * 32)()
     b = ctypes.addressof(buf)
     assert L.dnatok_reverse_complement(b, 16, p_off, 1, b + 8, None) == ERR_ARG  # overlapping
+
+
+def test_shard_records_bounds(lib):
+    # contiguous, covering, never splitting a record, and each split at the
+    # first record starting at or after i * n_bytes / world
+    import numpy as np
+    import synth
+    from paper_2601_05531_gb300 import binding
+    rng = np.random.default_rng(3)
+    for trial in range(50):
+        n_seq = int(rng.integers(0, 300))
+        lens = rng.integers(0, 5000, size=n_seq)
+        lens[rng.random(n_seq) < 0.2] = 0
+        offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        for world in (1, 2, 3, 8, 17):
+            b = binding.dnatok_shard_records(offs, world)
+            assert b[0] == 0 and b[-1] == n_seq and (np.diff(b) >= 0).all()
+            n = int(offs[-1])
+            for i in range(1, world):
+                p = n * i // world
+                assert b[i] == int(np.searchsorted(offs[:n_seq + 1], p, side="left")), (trial, world, i)
+    # the config-2 batch over 8 ranks: no shard more than one record over its share
+    lens = synth.log_uniform_lengths(4096, 1000, 128000, seed=44)
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    b = binding.dnatok_shard_records(offs, 8)
+    sizes = offs[b[1:]] - offs[b[:-1]]
+    assert sizes.max() <= offs[-1] / 8 + lens.max()
+    with pytest.raises(binding.DnatokError):
+        binding.dnatok_shard_records(np.array([0, 5, 3]), 2)  # decreasing
+    with pytest.raises(binding.DnatokError):
+        binding.dnatok_shard_records(np.array([1, 5]), 2)     # [0] != 0
