@@ -16,7 +16,7 @@
  *                A0 C1 G2 T3, UNK = 4^k (MapKmer, Algorithm 2);
  *   DNATOK_BPE   greedy rank-ordered BPE merges of a fixed table
  *                (segmentation identical to the table's tokenizer, Sec. 4.3);
- *   DNATOK_KMER_OVERLAP  overlapping k-mers with stride 1: a token at every
+ *   DNATOK_KMER_OVERLAP  overlapping k-mers (window step 1): a token at every
  *                kept base j with j + k <= L of a record of L kept bases
  *                (L - k + 1 tokens, none when L < k; Sec. 1.1, Table 1), same
  *                ids and UNK as DNATOK_KMER.  One-shot encodes only (no

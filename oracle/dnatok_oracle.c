@@ -18,8 +18,9 @@
  *     id = sum_i 4^(k-1-i) * code(b_i);
  *   - BPE with a fixed, rank-ordered merge table whose segmentation and
  *     IDs must match the source tokenizer (Sec. 1.1, Sec. 4.3);
- *   - overlapping k-mers with stride 1: every substring of k bases is a
- *     token, adjacent tokens share k-1 bases, and an input of L bases gives
+ *   - overlapping k-mers (a window at every position): each run of k
+ *     consecutive bases is one token, so neighbours overlap in all but one
+ *     base, and an input of L bases gives
  *     L-k+1 tokens (Sec. 1.1, Table 1).
  *
  * Readings where the paper is silent (each one is a test in tests/):

@@ -1,10 +1,10 @@
-// ovl.cu -- the modes built on the symbol pass: overlapping k-mers with
-// stride 1 and table-driven k-mers.
+// ovl.cu -- the modes built on the symbol pass: overlapping k-mers (a window
+// at every position) and table-driven k-mers.
 //
 // Overlapping k-mers: every window of k consecutive kept bases of a record is
-// a token, adjacent tokens share k - 1 bases, and a record of L kept bases
-// gives max(0, L - k + 1) tokens (Sec. 1.1 and Table 1: overlapping k-mer
-// tokenization with stride 1 yields L - k + 1 tokens).  Ids are the closed
+// a token, neighbours overlapping in all but one base, and a record of L kept
+// bases gives max(0, L - k + 1) tokens (Sec. 1.1 and Table 1 give the
+// L - k + 1 count).  Ids are the closed
 // form of the non-overlapping mode, sum_i 4^(k-1-i) * code(b_i) with A0 C1 G2
 // T3, and UNK = 4^k for a window holding an N-class base.  Three launches:
 //   1. the symbol pass (the tile kernel in MODE_SYM, or its direct path): one
