@@ -446,7 +446,7 @@ def _decode_rc_feed(torch, P, dev, d_bytes, d_offs, n, n_seq, flush_l2):
             "roofline": _hbm(alg, ms, "CUDA events around the one launch")}
 
         # micro-batched feed into an embedding lookup (d = 256, bf16 table):
-        # two streams with ping-pong buffers vs the same work on one stream
+        # two streams with two buffers used in turn vs the same work on one stream
         rows = P.microbatch_rows(256, 1 << 18, T)
         emb = torch.randn(4099, 256, device=dev, dtype=torch.bfloat16)
         sink = torch.empty((rows, T, 256), device=dev, dtype=torch.bfloat16)

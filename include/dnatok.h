@@ -326,8 +326,9 @@ DNATOK_API void dnatok_server_destroy(dnatok_server *s);
 /* ---------------------------------------------------------------- decode */
 
 /*
- * Token ids back to text on the device (Sec. 4, "Decode Operations": an
- * inverse vocabulary table maps each id to its character span).  Per mode:
+ * Token ids back to text on the device (Sec. 4, "Decode Operations", where
+ * the paper leaves it as future work): a reverse lookup from each id to the
+ * bases it stands for.  Per mode:
  *   DNATOK_CHAR   id v -> the first byte b with lut[b] == v in the order
  *                 "ACGTN", 'A'..'Z', 'a'..'z', then 0..255;
  *   DNATOK_KMER   id < 4^k -> its k bases (A C G T); UNK = 4^k -> one '?';
@@ -404,9 +405,9 @@ DNATOK_API dnatok_status dnatok_microbatch_rows(int64_t emb_batch_cap, int64_t t
                                                 int64_t token_len, int64_t *rows);
 
 /*
- * Micro-batched feed on two streams (Sec. 2.2, "Pipelined streaming": ping-
- * pong device buffers so that preparing micro-batch n+1 overlaps the
- * embedding compute of micro-batch n).  For each micro-batch of up to
+ * Micro-batched feed on two streams (Sec. 2.2, "Pipelined streaming"): two
+ * device buffers are used in turn, so the next micro-batch is written while
+ * the consumer still works on the one before.  For each micro-batch of up to
  * rows_per_batch rows, dnatok_feed writes it into buf[i % 2] on
  * feed_stream; consumer_stream then waits for it and `consumer` is called
  * (on this host thread) to enqueue its work on consumer_stream; feed_stream

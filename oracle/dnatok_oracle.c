@@ -56,7 +56,7 @@
  *       index sum_i 5^(k-1-i) d_i emits kmer_lut[index] when that entry is
  *       >= 0, else each of its k symbols as base_ids[d]; a tail of L mod k
  *       symbols emits base_ids[d] for each one.  1 <= k <= 10.
- *   C17 decode (Sec. 4, "Decode Operations": an inverse vocabulary table):
+ *   C17 decode (Sec. 4, "Decode Operations"; a reverse id -> text lookup):
  *       single-nucleotide ids through the inverse of the handle's 256-entry
  *       table -- for id v the first byte b in the order "ACGTN", then 'A'..'Z',
  *       'a'..'z', then 0..255, with lut[b] == v; table-driven k-mer ids

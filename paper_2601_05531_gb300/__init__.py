@@ -201,7 +201,7 @@ def microbatch_rows(emb_batch_cap: int, tokens_per_call: int, token_len: int) ->
 
 def feed_pipeline(ids, id_offsets, token_len: int, id_pad: int, rows_per_batch: int, consumer,
                   dtype=None, feed_stream=None, consumer_stream=None):
-    """Micro-batched feed on two streams with ping-pong buffers.  For every
+    """Micro-batched feed on two streams with two buffers used in turn.  For every
     micro-batch consumer(row_begin, batch, stream) is called with a
     (rows, token_len) tensor view and the torch stream it must enqueue its
     work on (e.g. an embedding lookup); the buffer is reused only after that

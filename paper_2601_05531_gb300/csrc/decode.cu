@@ -1,6 +1,6 @@
 // decode.cu -- token ids back to text on the device (Sec. 4, "Decode
-// Operations": an inverse vocabulary table maps ids back to character spans
-// with the same table-lookup structure as the encode).
+// Operations", future work there): a reverse lookup from each id to the
+// bases it stands for, run as table gathers like the encode.
 //
 // Per mode the text of an id is
 //   DNATOK_CHAR          one byte: the first byte b with lut[b] == id in the

@@ -3,7 +3,7 @@
 //   * the fixed-shape model feed (Algorithm 2: rows left-padded with id_pad
 //     to token_len, their own tokens right-aligned; Sec. 2.2: int32 ids
 //     promoted to int64 on the device), one-shot or micro-batched over two
-//     streams with ping-pong buffers (Sec. 2.2, "Pipelined streaming");
+//     streams with two buffers used in turn (Sec. 2.2, "Pipelined streaming");
 //   * the reverse complement of every record (Sec. 4, "Integration with Data
 //     Augmentation": the augmentation the paper leaves to future GPU work).
 #include <cuda_runtime.h>

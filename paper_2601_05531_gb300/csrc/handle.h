@@ -57,7 +57,7 @@ struct dnatok_handle {
     int32_t base_ids[5] = {0, 1, 2, 3, 4};
     std::vector<int32_t> merges_host;  // BPE table, kept for the decode table
 
-    // decode: inverse vocabulary (text of id v = text[off[v] .. off[v+1])),
+    // decode: reverse lookup table (text of id v = text[off[v] .. off[v+1])),
     // built at the first dnatok_decode; dec_v < 0 until then
     int32_t *d_dec_off = nullptr;
     uint8_t *d_dec_text = nullptr;
