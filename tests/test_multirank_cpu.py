@@ -63,3 +63,47 @@ def test_two_ranks_match_one_encode(mode, k):
     assert t0 == t1 == len(want_ids)
     assert np.array_equal(np.concatenate([ids0, ids1]), want_ids)
     assert np.array_equal(np.concatenate([g0[:-1], g1]), want_offs)
+
+
+def _rank_main_small(rank, world, port, out_q):
+    import torch.distributed as dist
+    import torch
+    import paper_2601_05531_gb300 as P
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # two records over three ranks: one rank's shard is empty
+        data, offs = synth.markov_batch([900, 40], 0.4, seed=4)
+        b = P.shard_records(offs, world)
+        r0, r1 = int(b[rank]), int(b[rank + 1])
+        lo, hi = int(offs[r0]), int(offs[r1])
+        ids, loc = oracle.encode(data[lo:hi], oracle.KMER, k=3, seq_offsets=offs[r0:r1 + 1] - lo)
+        g, total = P.global_id_offsets(torch.from_numpy(loc))
+        out_q.put((rank, r0, r1, ids, g.numpy(), total))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_three_ranks_with_an_empty_shard():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main_small, args=(r, 3, port, q)) for r in range(3)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    data, offs = synth.markov_batch([900, 40], 0.4, seed=4)
+    want_ids, want_offs = oracle.encode(data, oracle.KMER, k=3, seq_offsets=offs)
+    assert any(r1 == r0 for _, r0, r1, _, _, _ in res)  # one shard holds no record
+    ids = np.concatenate([x[3] for x in res])
+    got_offs = [0]
+    for _, r0, r1, _, g, _ in res:
+        got_offs.extend(g[1:].tolist())
+    assert np.array_equal(ids, want_ids)
+    assert got_offs == want_offs.tolist()
+    assert all(x[5] == len(want_ids) for x in res)
