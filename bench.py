@@ -6,18 +6,20 @@ Workload (seeded, synthetic): 4096 sequences with lengths log-uniform in
 soft-masked lowercase stretches; 6-mer ids (4096 k-mers + UNK), int32.
 
 One step = one dnatok_encode of the whole batch with inputs resident in
-HBM: three launches -- the record plan, the direct k-mer kernel, and the
-general tile kernel behind it, which exits at once when the input holds no
-separators (it runs only when the direct path's premise fails).  Before every
+HBM, replayed from a CUDA graph captured once (the batched form); the same
+call launched directly is reported beside it as `plain_launch`.  Before every
 timed step, outside the timed events, L2 is flushed by a 256 MB write followed
 by a 256 MB read, so the step starts with none of its data in L2 and with no
 dirty lines of the flush left to write back.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line.  N > 1 runs as torchrun ranks, one GPU each; every
-rank encodes its own copy of the batch (independent shards, weak scaling, no
-data-path collective); the timing takes the max over ranks.
+Prints one JSON line.  N > 1 runs as torchrun ranks, one GPU each: the global
+batch is N copies of the 4096 sequences, split by dnatok_shard_records into
+byte-balanced contiguous record ranges (the work per GPU stays fixed: weak
+scaling); the only exchange is global_id_offsets' all_gather of one id count
+per rank, made once after the timed steps; the timing takes the max over
+ranks.
 """
 from __future__ import annotations
 
@@ -476,29 +478,22 @@ def _decode_rc_feed(torch, P, dev, d_bytes, d_offs, n, n_seq, flush_l2):
     return out
 
 
-def _serving(torch, P, dev, seconds: float):
-    """Config-5 request trace (Poisson 2000/s, 200 B-1 MB, 30% single-
-    nucleotide / 50% 6-mer / 20% BPE with the 4096-merge table) replayed in
-    real time through the serving loop, and through per-request plain
-    launches (host copy + encode + wait, one request at a time)."""
+def _served(P, tr, merges, seconds):
+    """Replay a request trace in real time through the serving loop.  Latency
+    of a request = the time its completion is seen by this host thread minus
+    its arrival time in the trace (the time it waits while the loop refuses
+    it for lack of memory or slots is included)."""
     import numpy as np
-    import synth
+    import torch
     B = P.binding
-    tr = synth.request_trace(duration_s=seconds)
     n = len(tr.sizes)
-    m = np.loadtxt(os.path.join(ROOT, "tests", "golden", "bpe_merges_markov45_seed45_4096.txt"),
-                   dtype=np.int32)
     pin = torch.from_numpy(tr.data).pin_memory()
     base = pin.data_ptr()
-    res = {"requests": n, "offered_bytes_per_s": float(tr.sizes.sum() / seconds),
-           "budget_bytes": 4 << 30}
-
-    # --- serving loop
     srv = B.dnatok_server_create(budget_bytes=4 << 30, host_arena_bytes=1 << 30,
                                  max_batch_bytes=32 << 20, max_batch_requests=256, n_slots=4,
-                                 kmer_k=6, merges=m)
+                                 kmer_k=6, merges=merges)
     lat = np.zeros(n)
-    toks = 0
+    toks, refused = 0, 0
     done_t = 0.0
     try:
         pending = []
@@ -510,7 +505,8 @@ def _serving(torch, P, dev, seconds: float):
                 r = B.dnatok_server_submit(srv, int(tr.modes[i]), base + int(tr.offsets[i]),
                                            int(tr.sizes[i]))
                 if r is None:
-                    break
+                    refused += 1
+                    break  # retried on the next pass; its latency keeps running
                 pending.append((i, r))
                 i += 1
             still = []
@@ -519,19 +515,43 @@ def _serving(torch, P, dev, seconds: float):
                 if out is None:
                     still.append((k, r))
                     continue
-                lat[k] = out[2] / 1e3
+                done_t = time.perf_counter() - t0
+                lat[k] = 1e3 * (done_t - tr.arrival_s[k])
                 toks += out[1]
                 B.dnatok_server_release(srv, r)
-                done_t = time.perf_counter() - t0
             pending = still
         st = B.dnatok_server_stats(srv)
     finally:
         B.dnatok_server_destroy(srv)
-    res["served"] = {"tokens_per_s": toks / done_t, "p50_ms": float(np.percentile(lat, 50)),
-                     "p99_ms": float(np.percentile(lat, 99)), "batches": st["batches_launched"],
-                     "wall_s": done_t, "tokens": int(toks)}
+    return {"tokens_per_s": toks / done_t, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "batches": st["batches_launched"],
+            "wall_s": done_t, "tokens": int(toks), "refused_submits": refused,
+            "offered_bytes_per_s": float(tr.sizes.sum() / seconds)}
+
+
+def _serving(torch, P, dev, seconds: float):
+    """Config-5 request trace (Poisson 2000/s, 200 B-1 MB, 30% single-
+    nucleotide / 50% 6-mer / 20% BPE with the 4096-merge table) replayed in
+    real time through the serving loop, and through per-request plain
+    launches (host copy + encode + wait, one request at a time); then the
+    serving loop alone at three times the arrival rate."""
+    import numpy as np
+    import synth
+    B = P.binding
+    tr = synth.request_trace(duration_s=seconds)
+    n = len(tr.sizes)
+    m = np.loadtxt(os.path.join(ROOT, "tests", "golden", "bpe_merges_markov45_seed45_4096.txt"),
+                   dtype=np.int32)
+    res = {"requests": n, "offered_bytes_per_s": float(tr.sizes.sum() / seconds),
+           "budget_bytes": 4 << 30,
+           "latency": "both arms: completion seen by the submitting host thread minus the "
+                      "request's arrival time in the trace (queueing and refused submits "
+                      "included)"}
+    res["served"] = _served(P, tr, m, seconds)
 
     # --- per-request plain launches
+    pin = torch.from_numpy(tr.data).pin_memory()
+    base = pin.data_ptr()
     toks_b = {0: P.Tokenizer(P.CHAR), 1: P.Tokenizer(P.KMER, k=6), 2: P.Tokenizer(P.BPE, merges=m)}
     mx = int(tr.sizes.max())
     for t in toks_b.values():
@@ -562,19 +582,22 @@ def _serving(torch, P, dev, seconds: float):
                                    "p50_ms": float(np.percentile(lat_b, 50)),
                                    "p99_ms": float(np.percentile(lat_b, 99)), "wall_s": wall_b,
                                    "tokens": toks2}
-    res["latency"] = "served: submit -> completion seen by the worker; per-request: arrival -> " \
-                     "result on the host (includes waiting behind earlier requests)"
+    over_s = min(3.0, seconds)
+    tr3 = synth.request_trace(rate=6000.0, duration_s=over_s)
+    res["served_x3_rate"] = dict(_served(P, tr3, m, over_s), requests=len(tr3.sizes),
+                                 rate_per_s=6000.0)
     return res
 
 
 def _cpu_baseline(data, offs, budget_s: float = 10.0):
-    """The oracle as it stands, single-threaded on this host, on a bounded
-    sample of the same workload (whole records, repeated until ~budget_s)."""
+    """The oracle as it stands on this host, on a bounded sample of the same
+    workload: single-threaded on a ~25 MB slice of whole records (repeated
+    until ~budget_s), and on all cores with the whole batch split into
+    byte-balanced record ranges, one per task."""
     import numpy as np
 
     import oracle
     n_seq = len(offs) - 1
-    # a contiguous slice of records (~25 MB) keeps one pass near a second or two
     stop = int(np.searchsorted(offs, 25_000_000))
     stop = max(1, min(stop, n_seq))
     sample = data[: offs[stop]]
@@ -586,9 +609,304 @@ def _cpu_baseline(data, offs, budget_s: float = 10.0):
         secs += time.perf_counter() - t0
         toks += len(ids)
         reps += 1
-    return {"value": toks / secs, "unit": "tokens/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d of %d sequences (%.1f MB), %d pass(es), %.1f s single-threaded"
-                      % (stop, n_seq, offs[stop] / 1e6, reps, secs)}
+    out = {"value": toks / secs, "unit": "tokens/s", "cores": 1, "kind": "oracle",
+           "bytes_per_s": reps * int(offs[stop]) / secs,
+           "sample": "first %d of %d sequences (%.1f MB), %d pass(es), %.1f s single-threaded"
+                     % (stop, n_seq, offs[stop] / 1e6, reps, secs), "cpu_model": _cpu_model()}
+    nc = _cores()
+    parts = 4 * nc
+    cuts = np.searchsorted(offs, np.linspace(0, offs[-1], parts + 1)).clip(0, n_seq)
+    cuts[0], cuts[-1] = 0, n_seq
+    spans = [(int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    args = [(data[offs[a]:offs[b]], offs[a:b + 1] - offs[a]) for a, b in spans]
+    res, wall = _all_cores(_oracle_kmer_part, args)
+    out["all_cores"] = {"value": sum(res) / wall, "unit": "tokens/s", "cores": nc,
+                        "bytes_per_s": int(offs[-1]) / wall,
+                        "sample": "all %d sequences (%.1f MB) in %d record ranges on %d spawned "
+                                  "workers, %.2f s" % (n_seq, offs[-1] / 1e6, len(spans), nc,
+                                                       wall)}
+    return out
+
+
+def _extras(line, torch, P, dev, data, offs, d_bytes, d_offs, flush_l2, args):
+    """The other configurations and rows, each with its own roofline line."""
+    n_bytes, n_seq = len(data), len(offs) - 1
+    line["batched"] = _batched(torch, P, dev, data, offs, d_bytes, d_offs)
+    line["char_1mb"] = _char_1mb(torch, P, dev, flush_l2)
+    line["kmer6_4096seq_uniform"] = _kmer_uniform(torch, P, dev, flush_l2)
+    line["bpe_1gib"] = _bpe_1gib(torch, P, dev, flush_l2, with_cpu=not args.no_cpu_baseline)
+    line["fasta_chunk_64mib"] = _fasta_chunk(torch, P, dev, 64)
+    line["kmer6_overlap_4096seq"] = _overlap(torch, P, dev, d_bytes, d_offs, n_bytes, n_seq,
+                                             flush_l2)
+    line["kmer6_table_4096seq"] = _ktab(torch, P, dev, d_bytes, d_offs, n_bytes, n_seq, flush_l2)
+    line.update(_decode_rc_feed(torch, P, dev, d_bytes, d_offs, n_bytes, n_seq, flush_l2))
+    if args.serve_seconds > 0:
+        line["serving"] = _serving(torch, P, dev, args.serve_seconds)
+
+
+def _graph_of(P, tok, stream, fn):
+    """fn() captured once on `stream` through the library's graph API."""
+    B = P.binding
+    B.dnatok_graph_begin(tok.h, stream.cuda_stream)
+    fn()
+    return B.dnatok_graph_end(tok.h, stream.cuda_stream)
+
+
+def _char_1mb(torch, P, dev, flush_l2):
+    """Config 1: single-nucleotide ids of one 1 MB sequence.  One call with
+    L2 flushed before it (plain launch and graph replay), and 64 independent
+    1 MB calls replayed back to back from one graph (64 MB in, 256 MB out,
+    more than L2 holds)."""
+    import synth
+    B = P.binding
+    one, _ = synth.single_sequence_1mb()
+    m1 = len(one)
+    s = torch.cuda.current_stream()
+    out = {"workload": "single-nucleotide ids of one 1 MB sequence (i.i.d. ACGT, 1% N runs, "
+                       "5% lowercase)", "input_bytes": m1}
+    with P.Tokenizer(P.CHAR) as tok:
+        tok.reserve(m1, 1)
+        d = torch.from_numpy(one).to(dev)
+        so = torch.tensor([0, m1], dtype=torch.int64, device=dev)
+        ids, o, tot = tok.alloc_outputs(m1, 1, device=dev)
+
+        def call():
+            tok.encode(d, so, ids, o, tot, stream=s)
+
+        plain = _time_median(torch, call, flush_l2, steps=20)
+        g = _graph_of(P, tok, s, call)
+        rep = _time_median(torch, lambda: B.dnatok_graph_launch(g, s.cuda_stream), flush_l2,
+                           steps=20)
+        B.dnatok_graph_destroy(g)
+        tok.sync()
+        n_ids = int(tot[0].item())
+        alg = 5 * n_ids + 32
+        out.update({"tokens": n_ids, "us_per_call": 1e3 * plain, "us_per_call_graph": 1e3 * rep,
+                    "tokens_per_s": n_ids / (rep / 1e3),
+                    "roofline": _hbm(alg, rep, "CUDA events around one graph replay of one "
+                                               "call (L2 flushed before it)")})
+        calls = 64
+        ins = [torch.from_numpy(synth.single_sequence_1mb(seed=43 + i)[0]).to(dev)
+               for i in range(calls)]
+        outs = [tok.alloc_outputs(m1, 1, device=dev) for _ in range(calls)]
+
+        def batch():
+            for i in range(calls):
+                tok.encode(ins[i], so, *outs[i], stream=s)
+
+        g = _graph_of(P, tok, s, batch)
+        ms = _time_median(torch, lambda: B.dnatok_graph_launch(g, s.cuda_stream), flush_l2,
+                          steps=10)
+        B.dnatok_graph_destroy(g)
+        tok.sync()
+        toks = sum(int(x[2][0].item()) for x in outs)
+        out["x64_graph"] = {"calls": calls, "ms": ms, "us_per_call": 1e3 * ms / calls,
+                            "tokens_per_s": toks / (ms / 1e3),
+                            "roofline": _hbm(5 * toks + 32 * calls, ms,
+                                             "CUDA events around one replay of 64 calls")}
+    return out
+
+
+def _kmer_uniform(torch, P, dev, flush_l2):
+    """Config 2u: the same 6-mer encode on 4096 sequences with lengths
+    uniform in [1 kb, 128 kb] (about 264 MB), graph replay and plain launch."""
+    import synth
+    B = P.binding
+    data, offs = synth.kmer_batch_4096(uniform=True)
+    n, n_seq = len(data), len(offs) - 1
+    s = torch.cuda.current_stream()
+    with P.Tokenizer(P.KMER, k=6) as tok:
+        tok.reserve(n, n_seq)
+        d = torch.from_numpy(data).to(dev)
+        so = torch.from_numpy(offs).to(dev)
+        ids, o, tot = tok.alloc_outputs(n, n_seq, device=dev)
+
+        def call():
+            tok.encode(d, so, ids, o, tot, stream=s)
+
+        plain = _time_median(torch, call, flush_l2, steps=10)
+        g = _graph_of(P, tok, s, call)
+        rep = _time_median(torch, lambda: B.dnatok_graph_launch(g, s.cuda_stream), flush_l2,
+                           steps=10)
+        B.dnatok_graph_destroy(g)
+        tok.sync()
+        n_ids = int(tot[0].item())
+    alg = n + 4 * n_ids + 16 * (n_seq + 1)
+    return {"workload": "6-mer ids of 4096 sequences, lengths uniform 1-128 kb", "input_bytes": n,
+            "tokens": n_ids, "ms": rep, "ms_plain": plain, "tokens_per_s": n_ids / (rep / 1e3),
+            "roofline": _hbm(alg, rep, "CUDA events around one graph replay"),
+            "roofline_plain": _hbm(alg, plain, "CUDA events around one plain call")}
+
+
+def _bpe_1gib(torch, P, dev, flush_l2, with_cpu: bool = True, steps: int = 5):
+    """Config 3: BPE with the 4096-merge table (trained by the oracle's
+    trainer on a 10 MB Markov corpus) on 512 x 2,097,152 fresh bases (1 GiB).
+    Device-resident encode (L2 flushed; the input is 8x L2 anyway), the
+    repair statistics of the merge pass, the end-to-end call from pinned
+    host buffers, and the oracle on a sample of records."""
+    import numpy as np
+    import synth
+    B = P.binding
+    data, offs = synth.bpe_apply_corpus()
+    merges = np.loadtxt(os.path.join(ROOT, "tests", "golden",
+                                     "bpe_merges_markov45_seed45_4096.txt"), dtype=np.int32)
+    n, n_seq = len(data), len(offs) - 1
+    s = torch.cuda.current_stream()
+    out = {"workload": "BPE (4096 merges) of 512 x 2,097,152 uppercase bases (1 GiB), "
+                       "order-3 Markov 45% GC", "input_bytes": n}
+    with P.Tokenizer(P.BPE, merges=merges) as tok:
+        tok.reserve(n, n_seq)
+        d = torch.from_numpy(data).to(dev)
+        so = torch.from_numpy(offs).to(dev)
+        ids, o, tot = tok.alloc_outputs(n, n_seq, device=dev)
+        ms = _time_median(torch, lambda: tok.encode(d, so, ids, o, tot, stream=s), flush_l2,
+                          steps=steps)
+        tok.sync()
+        n_ids = int(tot[0].item())
+        out["merge_pass"] = B.dnatok_bpe_stats(tok.h, s.cuda_stream)
+        out["segment_halo"] = list(B.dnatok_get_bpe_launch(tok.h))
+        del d, so
+        # end to end from pinned host buffers
+        h_bytes = torch.from_numpy(data).pin_memory()
+        h_offs = torch.from_numpy(offs).pin_memory()
+        h_ooff = torch.empty(n_seq + 1, dtype=torch.int64).pin_memory()
+        h_tot = torch.zeros(2, dtype=torch.int64)
+
+        def e2e():
+            B.dnatok_encode_host(tok.h, h_bytes.data_ptr(), n, h_offs.data_ptr(), n_seq,
+                                 ids.data_ptr(), ids.numel(), h_ooff.data_ptr(), n_seq + 1,
+                                 h_tot.data_ptr(), s.cuda_stream)
+
+        e2e()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            e2e()
+        e2e_s = (time.perf_counter() - t0) / 3
+        assert int(h_tot[0]) == n_ids
+    alg = n + 4 * n_ids + 16 * (n_seq + 1)
+    out.update({"tokens": n_ids, "bases_per_token": n / n_ids, "ms": ms,
+                "tokens_per_s": n_ids / (ms / 1e3), "bytes_per_s": n / (ms / 1e3),
+                "roofline": _hbm(alg, ms, "CUDA events around the whole encode (symbol pass, "
+                                          "merge pass, maps, scans, emit, offsets)"),
+                "e2e": {"value": n_ids / e2e_s, "unit": "tokens/s", "ms_per_step": 1e3 * e2e_s,
+                        "h2d_bytes_per_step": n + 8 * (n_seq + 1),
+                        "d2h_bytes_per_step": 8 * (n_seq + 1) + 16,
+                        "api": "dnatok_encode_host (pinned host buffers)"}})
+    if with_cpu:
+        out["cpu_baseline"] = _cpu_baseline_bpe(data, offs, merges)
+    return out
+
+
+def _fasta_chunk(torch, P, dev, mib: int, steps: int = 10):
+    """Device-resident 6-mer encode of one FASTA chunk (the first `mib` MiB
+    of the seeded 8 GiB stream): the unit of work the host-streamed encode
+    hands the general kernel."""
+    import numpy as np
+    import synth
+    n = mib << 20
+    host = np.empty(n, dtype=np.uint8)
+    synth.fasta_stream(n, seed=47, out=host)
+    d = torch.from_numpy(host).to(dev)
+    s = torch.cuda.current_stream()
+    with P.Tokenizer(P.KMER, k=6, fmt=P.FASTA) as tok:
+        ids, o, tot = tok.alloc_outputs(n, 1, device=dev)
+        ms = _time_median(torch, lambda: tok.encode(d, None, ids, o, tot, stream=s),
+                          lambda i: None, steps=steps)
+        tok.sync()
+        n_ids, n_rec = int(tot[0].item()), int(tot[1].item())
+    alg = n + 4 * n_ids + 8 * (n_rec + 1)
+    return {"workload": "6-mer ids of a %d MiB FASTA chunk (device-resident)" % mib,
+            "tokens": n_ids, "records": n_rec, "ms": ms, "gb_per_s": n / (ms / 1e3) / 1e9,
+            "roofline": _hbm(alg, ms, "CUDA events around one encode (the chunk is "
+                                      "%d MiB; L2 not flushed)" % mib)}
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def _oracle_kmer_part(data, offs):
+    import oracle
+    ids, _ = oracle.encode(data, oracle.KMER, k=6, seq_offsets=offs)
+    return len(ids)
+
+
+def _oracle_bpe_part(r0, r1):
+    import numpy as np
+    import oracle
+    import synth
+    d, o = synth.bpe_apply_corpus(records=(r0, r1), threads=1)
+    m = np.loadtxt(os.path.join(ROOT, "tests", "golden", "bpe_merges_markov45_seed45_4096.txt"),
+                   dtype=np.int32)
+    t0 = time.perf_counter()
+    ids, _ = oracle.encode(d, oracle.BPE, seq_offsets=o, merges=m)
+    return len(ids), time.perf_counter() - t0
+
+
+def _all_cores(fn, parts):
+    """fn(*part) for every part on every core of this process (spawned
+    workers, one part each at a time); returns (results, wall seconds of
+    the whole map after the workers started)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(_cores(), mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_noop, range(_cores())))  # start every worker first
+        t0 = time.perf_counter()
+        res = list(ex.map(fn, *zip(*parts)))
+        return res, time.perf_counter() - t0
+
+
+def _noop(_):
+    return 0
+
+
+def _cpu_baseline_bpe(data, offs, merges, budget_s: float = 10.0):
+    """The oracle's BPE as it stands on this host: one thread on whole
+    records until ~budget_s, and all cores on 4 records per core."""
+    import oracle
+    n_seq = len(offs) - 1
+    toks, secs, recs = 0, 0.0, 0
+    while secs < budget_s and recs < n_seq:
+        a, b = int(offs[recs]), int(offs[recs + 1])
+        t0 = time.perf_counter()
+        ids, _ = oracle.encode(data[a:b], oracle.BPE, merges=merges)
+        secs += time.perf_counter() - t0
+        toks += len(ids)
+        recs += 1
+    out = {"value": toks / secs, "unit": "tokens/s", "cores": 1, "kind": "oracle",
+           "bytes_per_s": int(offs[recs]) / secs,
+           "sample": "first %d of %d records (%.1f MB), %.1f s single-threaded"
+                     % (recs, n_seq, offs[recs] / 1e6, secs), "cpu_model": _cpu_model()}
+    nc = _cores()
+    per = 4 * nc
+    res, wall = _all_cores(_oracle_bpe_part, [(r, r + 1) for r in range(min(per, n_seq))])
+    t_all = sum(r[0] for r in res)
+    out["all_cores"] = {"value": t_all / wall, "unit": "tokens/s", "cores": nc,
+                        "bytes_per_s": min(per, n_seq) * (offs[1] - offs[0]) / wall,
+                        "sample": "%d records (one per task) on %d spawned workers, %.1f s"
+                                  % (min(per, n_seq), nc, wall)}
+    return out
 
 
 def run_reference(args):
@@ -628,6 +946,39 @@ def run_reference(args):
     return 0
 
 
+def _shard(data, offs, ws: int, rank: int):
+    """This rank's records of the global batch: N copies of the 4096-sequence
+    batch back to back (N = world size, so the work per GPU stays fixed),
+    split into byte-balanced contiguous record ranges by the library's own
+    dnatok_shard_records.  Returns (bytes, offsets rebased to 0, record range)."""
+    import numpy as np
+    from paper_2601_05531_gb300 import binding
+    if ws == 1:
+        return data, offs, (0, len(offs) - 1)
+    n, n_seq = len(data), len(offs) - 1
+    g_offs = np.concatenate([offs[:-1] + i * n for i in range(ws)] + [[ws * n]]).astype(np.int64)
+    bounds = binding.dnatok_shard_records(g_offs, ws)
+    r0, r1 = int(bounds[rank]), int(bounds[rank + 1])
+    b0, b1 = int(g_offs[r0]), int(g_offs[r1])
+    reps = np.concatenate([data] * ((b1 - 1) // n - b0 // n + 1)) if b1 > b0 else data[:0]
+    mine = reps[b0 - (b0 // n) * n: b0 - (b0 // n) * n + (b1 - b0)]
+    return np.ascontiguousarray(mine), g_offs[r0:r1 + 1] - b0, (r0, r1)
+
+
+def _time_steps(torch, stream, step, flush_l2, steps: int):
+    """CUDA-event time (ms) of each of `steps` calls of step() on `stream`,
+    L2 flushed before each call, outside the events."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for i in range(steps):
+        flush_l2(i)
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -646,13 +997,15 @@ def run_gpu(args):
     import paper_2601_05531_gb300 as P
     from paper_2601_05531_gb300 import binding
 
-    data, offs = _workload()
+    full_data, full_offs = _workload()
+    data, offs, (rec0, rec1) = _shard(full_data, full_offs, ws, rank)
     n_bytes, n_seq = len(data), len(offs) - 1
     d_bytes = torch.from_numpy(data).to(dev)
     d_offs = torch.from_numpy(offs).to(dev)
     tok = P.Tokenizer(P.KMER, k=6)
     if args.shape:
         tok.set_launch(*[int(x) for x in args.shape.split(",")])
+    tok.reserve(n_bytes, n_seq)
     ids, o_out, totals = tok.alloc_outputs(n_bytes, n_seq, device=dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -665,13 +1018,20 @@ def run_gpu(args):
         flush.fill_(i & 255)
         flush_acc.copy_(flush_rd.sum(dtype=torch.int64).view(1))
 
-    def step():
+    def plain_step():
         tok.encode(d_bytes, d_offs, ids, o_out, totals, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        plain_step()
     tok.sync()
     n_ids = int(totals[0].item())
+    # the same encode captured once as a CUDA graph (the batched form's launch)
+    binding.dnatok_graph_begin(tok.h, stream.cuda_stream)
+    plain_step()
+    graph = binding.dnatok_graph_end(tok.h, stream.cuda_stream)
+
+    def graph_step():
+        binding.dnatok_graph_launch(graph, stream.cuda_stream)
 
     sampler = ClockSampler(dev.index if ws == 1 else local)
     sampler.start()
@@ -680,23 +1040,20 @@ def run_gpu(args):
     # while the clock sampler started
     for i in range(max(args.warmup, 3)):
         flush_l2(i)
-        step()
+        graph_step()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush_l2(i)  # outside the timed events
-        evs[i][0].record(stream)
-        step()
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = _time_steps(torch, stream, graph_step, flush_l2, args.steps)
     if ws > 1:
         torch.distributed.barrier()
-    tok.sync()
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+    for i in range(3):
+        flush_l2(i)
+        plain_step()
+    plain_ms = _time_steps(torch, stream, plain_step, flush_l2, args.steps)
+    tok.sync()
+    assert int(totals[0].item()) == n_ids
     total_ms = sum(step_ms)
 
     # end to end through the public host-buffer entry point
@@ -720,20 +1077,31 @@ def run_gpu(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     assert int(h_tot[0]) == n_ids
 
+    sharding = None
     if ws > 1:
-        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+        # the one exchange of the sharded path: global id offsets
+        g_off, g_ids = P.global_id_offsets(o_out[: n_seq + 1])
+        sharding = {"records": [rec0, rec1], "global_ids": g_ids}
+        t = torch.tensor([total_ms, e2e_s, sum(plain_ms)], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms, e2e_s = float(t[0]), float(t[1])
+        all_ids = torch.tensor([n_ids], dtype=torch.int64, device=dev)
+        torch.distributed.all_reduce(all_ids)
+        job_ids = int(all_ids[0])
+    else:
+        job_ids = n_ids
+    binding.dnatok_graph_destroy(graph)
 
     if rank == 0:
         peak, peak_kind = _peaks()
         alg_bytes = n_bytes + 4 * n_ids + 16 * (n_seq + 1)
         mean_s = total_ms / 1e3 / args.steps
         achieved = alg_bytes / mean_s / 1e9
+        plain_mean = statistics.mean(plain_ms) / 1e3
         traffic = _traffic(n_bytes)
         line = {
             "metric": METRIC,
-            "value": n_ids * ws * args.steps / (total_ms / 1e3),
+            "value": job_ids * args.steps / (total_ms / 1e3),
             "unit": "tokens/s",
             "n_gpus": ws, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": total_ms / args.steps,
@@ -744,32 +1112,39 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_sequences": n_seq, "input_bytes": n_bytes,
-                       "tokens_per_step": n_ids, "k": 6, "l2": "flushed before every step (256 MB write, then 256 MB read)",
-                       "launch": list(tok.get_launch()), "parallelism": "replicas x%d" % ws},
+                       "tokens_per_step": n_ids, "k": 6,
+                       "l2": "flushed before every step (256 MB write, then 256 MB read)",
+                       "launch_form": "CUDA graph replay of one dnatok_encode (value, "
+                                      "roofline); plain_launch below is the same call "
+                                      "launched directly",
+                       "launch": list(tok.get_launch()),
+                       "parallelism": ("record shards x%d (dnatok_shard_records over %d "
+                                       "copies of the batch)" % (ws, ws)) if ws > 1
+                       else "one GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": KERNEL,
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "duration": "CUDA events around the whole step (all three launches)"},
-            "e2e": {"value": n_ids * ws / e2e_s, "unit": "tokens/s",
+                         "duration": "CUDA events around the whole graph replay (every "
+                                     "launch of the step)"},
+            "plain_launch": {"ms_per_step": 1e3 * plain_mean,
+                             "p50_ms": statistics.median(plain_ms),
+                             "tokens_per_s": n_ids / plain_mean,
+                             "roofline_frac": alg_bytes / plain_mean / 1e9 / peak},
+            "e2e": {"value": job_ids / e2e_s, "unit": "tokens/s",
                     "h2d_bytes_per_step": n_bytes + 8 * (n_seq + 1),
                     "d2h_bytes_per_step": 8 * (n_seq + 1) + 16,
                     "ms_per_step": 1e3 * e2e_s, "api": "dnatok_encode_host (pinned host buffers)"},
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
         }
+        if sharding:
+            line["sharding"] = sharding
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(data, offs)
         if ws == 1 and not args.no_extras:
-            line["batched"] = _batched(torch, P, dev, data, offs, d_bytes, d_offs)
-            line["kmer6_overlap_4096seq"] = _overlap(torch, P, dev, d_bytes, d_offs, n_bytes,
-                                                     n_seq, flush_l2)
-            line["kmer6_table_4096seq"] = _ktab(torch, P, dev, d_bytes, d_offs, n_bytes, n_seq,
-                                                flush_l2)
-            line.update(_decode_rc_feed(torch, P, dev, d_bytes, d_offs, n_bytes, n_seq, flush_l2))
-            if args.serve_seconds > 0:
-                line["serving"] = _serving(torch, P, dev, args.serve_seconds)
-        if args.stream_gib > 0:
+            _extras(line, torch, P, dev, data, offs, d_bytes, d_offs, flush_l2, args)
+        if ws == 1 and args.stream_gib > 0:
             line["host_streamed"] = _streamed(torch, P, dev, int(args.stream_gib * 2**30))
         print(json.dumps(line), flush=True)
     tok.close()

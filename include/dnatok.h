@@ -558,6 +558,17 @@ DNATOK_API dnatok_status dnatok_set_bpe_launch(dnatok_handle *h, int32_t seg_sym
 DNATOK_API dnatok_status dnatok_get_bpe_launch(const dnatok_handle *h, int32_t *seg_symbols,
                                                int32_t *halo);
 
+/* BPE handles: statistics of the last encode on this handle, for tuning the
+ * segment and halo sizes.  stats3[0] = symbols (kept bases and N-class bytes)
+ * the merge pass ran over, stats3[1] = segments of seg_symbols symbols,
+ * stats3[2] = segments whose halo pass did not agree with the neighbour to
+ * their left and were recomputed exactly.  All zero before the first encode.
+ * Synchronizes `stream` (the stream of that encode).  DNATOK_ERR_STATE on a
+ * handle of another mode.  (Diagnostics of this library's own BPE method:
+ * the paper defines no GPU BPE.) */
+DNATOK_API dnatok_status dnatok_bpe_stats(dnatok_handle *h, int64_t *stats3,
+                                          dnatok_cuda_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

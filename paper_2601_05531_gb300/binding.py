@@ -118,6 +118,7 @@ def lib():
             "dnatok_set_direct": (_ST, [_P, ctypes.c_int32]),
             "dnatok_get_bpe_launch": (_ST, [_P, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
+            "dnatok_bpe_stats": (_ST, [_P, ctypes.POINTER(_I64), _P]),
             "dnatok_graph_begin": (_ST, [_P, _P]),
             "dnatok_graph_end": (_ST, [_P, _P, ctypes.POINTER(_P)]),
             "dnatok_graph_launch": (_ST, [_P, _P]),
@@ -288,6 +289,12 @@ def dnatok_get_bpe_launch(h) -> tuple:
     a, b = ctypes.c_int32(), ctypes.c_int32()
     check(lib().dnatok_get_bpe_launch(h, ctypes.byref(a), ctypes.byref(b)), h)
     return (a.value, b.value)
+
+
+def dnatok_bpe_stats(h, stream: int = 0) -> dict:
+    v = (_I64 * 3)()
+    check(lib().dnatok_bpe_stats(h, v, stream), h)
+    return {"symbols": v[0], "segments": v[1], "repaired_segments": v[2]}
 
 
 def dnatok_graph_begin(h, stream: int) -> None:

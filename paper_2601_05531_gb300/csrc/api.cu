@@ -475,6 +475,15 @@ dnatok_status dnatok_get_bpe_launch(const dnatok_handle *h, int32_t *seg_symbols
     return bpe_get_launch(h, seg_symbols, halo);
 }
 
+dnatok_status dnatok_bpe_stats(dnatok_handle *h, int64_t *stats3, dnatok_cuda_stream stream) {
+    if (!h || !stats3) return DNATOK_ERR_ARG;
+    long long v[3];
+    const dnatok_status st = bpe_stats(h, v, reinterpret_cast<cudaStream_t>(stream));
+    if (st != DNATOK_OK) return st;
+    for (int i = 0; i < 3; ++i) stats3[i] = v[i];
+    return DNATOK_OK;
+}
+
 dnatok_status dnatok_set_launch(dnatok_handle *h, const dnatok_launch_cfg *cfg) {
     if (!h || !cfg) return DNATOK_ERR_ARG;
     LaunchShape sh{cfg->tile_bytes, cfg->threads, cfg->ctas_per_sm, cfg->chunk_tiles};

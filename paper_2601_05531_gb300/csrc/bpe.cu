@@ -1001,6 +1001,23 @@ dnatok_status bpe_set_launch(dnatok_handle *h, int seg_symbols, int halo) {
     return DNATOK_OK;
 }
 
+dnatok_status bpe_stats(dnatok_handle *h, long long *out, cudaStream_t s) {
+    BpeState *b = h->bpe;
+    if (!b) return fail(h, DNATOK_ERR_STATE, "not a BPE handle");
+    out[0] = out[1] = out[2] = 0;
+    if (!b->d_tot || !b->d_bad) return DNATOK_OK;  // nothing encoded yet
+    long long tot[2] = {0, 0};
+    int bad = 0;
+    cudaError_t e = cudaMemcpyAsync(tot, b->d_tot, sizeof(tot), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, b->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e, "BPE statistics read");
+    out[0] = tot[0];
+    out[1] = (tot[0] + b->ws_S - 1) / (b->ws_S > 0 ? b->ws_S : 1);
+    out[2] = bad;
+    return DNATOK_OK;
+}
+
 dnatok_status bpe_get_launch(const dnatok_handle *h, int *seg_symbols, int *halo) {
     if (!h->bpe) return DNATOK_ERR_STATE;
     *seg_symbols = h->bpe->S;

@@ -108,6 +108,9 @@ void bpe_destroy(dnatok_handle *h);
 dnatok_status bpe_reserve(dnatok_handle *h, long long max_bytes);
 dnatok_status bpe_set_launch(dnatok_handle *h, int seg_symbols, int halo);
 dnatok_status bpe_get_launch(const dnatok_handle *h, int *seg_symbols, int *halo);
+// {symbols, segments, segments that went through the exact repair} of the
+// last encode (synchronizes the stream)
+dnatok_status bpe_stats(dnatok_handle *h, long long *out, cudaStream_t s);
 dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
                          const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
                          int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,

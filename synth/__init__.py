@@ -64,9 +64,9 @@ def _load():
         i64, u32, u64, cint = ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
         lib.synth_iid_sequence.argtypes = [u8p, i64, u32, cint, cint, u32, u64]
         lib.synth_markov_batch.argtypes = [u8p, i64p, i64, u32p, u32, cint, cint, u32, i32p,
-                                           u64, cint]
+                                           u64, cint, i64, i64]
         lib.synth_fasta.argtypes = [u8p, i64, i64, i64p, i32p, i32p, i64p, u32p, u32, cint,
-                                    cint, u32, i32p, u64, cint]
+                                    cint, u32, i32p, u64, cint, i64, i64]
         lib.synth_random_bytes.argtypes = [u8p, i64, u64]
         for f in (lib.synth_iid_sequence, lib.synth_markov_batch, lib.synth_fasta,
                   lib.synth_random_bytes):
@@ -159,14 +159,20 @@ def iid_sequence(n: int, seed: int, n_fraction: float = N_FRACTION,
 
 
 def markov_batch(lengths, gc: float, seed: int, n_runs: bool = True, soft_mask: bool = True,
-                 model_seed: int | None = None, out: np.ndarray | None = None):
-    """Back-to-back Markov sequences.  Returns (bytes uint8, offsets int64[n+1])."""
+                 model_seed: int | None = None, out: np.ndarray | None = None,
+                 records: tuple | None = None, threads: int | None = None):
+    """Back-to-back Markov sequences.  Returns (bytes uint8, offsets int64[n+1]).
+    ``records=(r0, r1)`` writes only sequences r0..r1-1 (the same bytes as
+    that slice of the whole batch, each sequence seeded by its index) and
+    returns them with their offsets rebased to 0."""
     lengths = np.asarray(lengths, dtype=np.int64)
     offsets = np.zeros(len(lengths) + 1, dtype=np.int64)
     np.cumsum(lengths, out=offsets[1:])
-    total = int(offsets[-1])
+    r0, r1 = (0, len(lengths)) if records is None else (int(records[0]), int(records[1]))
+    assert 0 <= r0 <= r1 <= len(lengths)
+    total = int(offsets[r1] - offsets[r0])
     if out is None:
-        out = np.empty(total, dtype=np.uint8)
+        out = np.empty(max(total, 1), dtype=np.uint8)
     assert out.size >= total and out.dtype == np.uint8
     _, cdf, _ = markov_model(gc, seed if model_seed is None else model_seed)
     table = _lower_len_table()
@@ -174,7 +180,9 @@ def markov_batch(lengths, gc: float, seed: int, n_runs: bool = True, soft_mask: 
                                len(lengths), _ptr(cdf, ctypes.c_uint32),
                                _NRUN_P if n_runs else 0, N_RUN[0], N_RUN[1],
                                _LOWER_P if soft_mask else 0, _ptr(table, ctypes.c_int32),
-                               seed, _threads())
+                               seed, threads or _threads(), r0, r1)
+    if records is not None:
+        return out[:total], offsets[r0:r1 + 1] - offsets[r0]
     return out[:total], offsets
 
 
@@ -240,12 +248,13 @@ def bpe_training_corpus(seed: int = 45, n: int = 10_000_000) -> np.ndarray:
 
 
 def bpe_apply_corpus(seed: int = 46, n_seq: int = 512, length: int = 2_097_152,
-                     model_seed: int = 45):
+                     model_seed: int = 45, records: tuple | None = None,
+                     threads: int | None = None):
     """512 sequences of 2 Mb, uppercase ACGT, drawn from the same Markov
     model as the trainer corpus (model parameters from ``model_seed``) with a
-    fresh chain seed."""
+    fresh chain seed.  ``records=(r0, r1)``: only those sequences."""
     return markov_batch([length] * n_seq, 0.45, seed, n_runs=False, soft_mask=False,
-                        model_seed=model_seed)
+                        model_seed=model_seed, records=records, threads=threads)
 
 
 @dataclass
@@ -273,22 +282,30 @@ def fasta_layout(n_total: int, seed: int, rec_lo: float = 10_000, rec_hi: float 
                        np.array(wraps, dtype=np.int32), np.array(lens, dtype=np.int64), n_total)
 
 
-def fasta_stream(n_total: int, seed: int = 47, out: np.ndarray | None = None, **layout_kw):
+def fasta_stream(n_total: int, seed: int = 47, out: np.ndarray | None = None,
+                 records: tuple | None = None, threads: int | None = None, **layout_kw):
     """FASTA text of exactly n_total bytes (the last record is cut at the
     end), Markov 40% GC with N runs and soft-masked stretches.  ``out`` may
-    be a pinned host buffer.  Returns (bytes, layout)."""
+    be a pinned host buffer.  Returns (bytes, layout).  ``records=(r0, r1)``
+    writes only records r0..r1-1 (the same bytes as that slice of the whole
+    stream, each record seeded by its index)."""
     lay = fasta_layout(n_total, seed, **layout_kw)
+    n_rec = len(lay.rec_off)
+    r0, r1 = (0, n_rec) if records is None else (int(records[0]), int(records[1]))
+    assert 0 <= r0 <= r1 <= n_rec
+    starts = np.append(lay.rec_off, n_total)
+    size = int(starts[r1] - starts[r0])
     if out is None:
-        out = np.empty(n_total, dtype=np.uint8)
-    assert out.dtype == np.uint8 and out.size >= n_total
+        out = np.empty(max(size, 1), dtype=np.uint8)
+    assert out.dtype == np.uint8 and out.size >= size
     _, cdf, _ = markov_model(0.40, seed)
     table = _lower_len_table()
-    _load().synth_fasta(_ptr(out, ctypes.c_uint8), n_total, len(lay.rec_off),
+    _load().synth_fasta(_ptr(out, ctypes.c_uint8), n_total, n_rec,
                         _ptr(lay.rec_off, ctypes.c_int64), _ptr(lay.hdr_len, ctypes.c_int32),
                         _ptr(lay.wrap, ctypes.c_int32), _ptr(lay.seq_len, ctypes.c_int64),
                         _ptr(cdf, ctypes.c_uint32), _NRUN_P, N_RUN[0], N_RUN[1], _LOWER_P,
-                        _ptr(table, ctypes.c_int32), seed, _threads())
-    return out[:n_total], lay
+                        _ptr(table, ctypes.c_int32), seed, threads or _threads(), r0, r1)
+    return out[:size], lay
 
 
 @dataclass

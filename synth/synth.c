@@ -117,12 +117,13 @@ typedef struct {
     uint32_t lower_p32;
     const int32_t *len_table;
     uint64_t seed;
-    int64_t next;
+    int64_t next, end;  /* records [next, end) are still to be written */
+    int64_t base;       /* byte offset of out[0] in the whole batch */
     pthread_mutex_t lock;
 } batch_job;
 
 static void batch_one(batch_job *J, int64_t s) {
-    uint8_t *p = J->out + J->offsets[s];
+    uint8_t *p = J->out + (J->offsets[s] - J->base);
     int64_t n = J->offsets[s + 1] - J->offsets[s];
     uint64_t rm = stream_seed(J->seed, (uint64_t)s, 11);
     fill_markov(p, n, J->cdf, &rm);
@@ -138,20 +139,26 @@ static void *batch_worker(void *arg) {
         pthread_mutex_lock(&J->lock);
         int64_t s = J->next++;
         pthread_mutex_unlock(&J->lock);
-        if (s >= J->n_seq) break;
+        if (s >= J->end) break;
         batch_one(J, s);
     }
     return NULL;
 }
 
-/* Fill n_seq Markov sequences laid out back to back at offsets[0..n_seq]. */
+/* Fill Markov sequences [first, last) of a batch laid out back to back at
+ * offsets[0..n_seq]; out holds bytes offsets[first] .. offsets[last]. */
 void synth_markov_batch(uint8_t *out, const int64_t *offsets, int64_t n_seq, const uint32_t *cdf,
                         uint32_t nrun_p32, int nrun_lo, int nrun_hi, uint32_t lower_p32,
-                        const int32_t *len_table, uint64_t seed, int n_threads) {
+                        const int32_t *len_table, uint64_t seed, int n_threads, int64_t first,
+                        int64_t last) {
     batch_job J;
     J.out = out; J.offsets = offsets; J.n_seq = n_seq; J.cdf = cdf;
     J.nrun_p32 = nrun_p32; J.nrun_lo = nrun_lo; J.nrun_hi = nrun_hi;
-    J.lower_p32 = lower_p32; J.len_table = len_table; J.seed = seed; J.next = 0;
+    J.lower_p32 = lower_p32; J.len_table = len_table; J.seed = seed;
+    if (first < 0) first = 0;
+    if (last > n_seq) last = n_seq;
+    J.next = first; J.end = last;
+    J.base = (first < n_seq) ? offsets[first] : 0;
     pthread_mutex_init(&J.lock, NULL);
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
@@ -178,14 +185,15 @@ typedef struct {
     uint32_t lower_p32;
     const int32_t *len_table;
     uint64_t seed;
-    int64_t next;
+    int64_t next, end;  /* records [next, end) are still to be written */
+    int64_t base;       /* byte offset of out[0] in the whole stream */
     pthread_mutex_t lock;
 } fasta_job;
 
 static void fasta_one(fasta_job *J, int64_t r, uint8_t *scratch) {
     int64_t off = J->rec_off[r];
     int64_t end = (r + 1 < J->n_rec) ? J->rec_off[r + 1] : J->n_total;
-    uint8_t *p = J->out + off;
+    uint8_t *p = J->out + (off - J->base);
     int64_t room = end - off;
     uint64_t rh = stream_seed(J->seed, (uint64_t)r, 21);
     int64_t w = 0;
@@ -219,7 +227,7 @@ static void *fasta_worker(void *arg) {
         pthread_mutex_lock(&J->lock);
         int64_t r = J->next++;
         pthread_mutex_unlock(&J->lock);
-        if (r >= J->n_rec) break;
+        if (r >= J->end) break;
         if (J->seq_len[r] > cap) {
             free(scratch);
             cap = J->seq_len[r];
@@ -234,16 +242,22 @@ static void *fasta_worker(void *arg) {
 
 /* Write n_rec FASTA records at the byte offsets rec_off (computed by the
  * caller so that each record occupies exactly its header line plus its
- * wrapped sequence lines). */
+ * wrapped sequence lines); only records [first, last) are written, out
+ * holding bytes rec_off[first] onwards. */
 void synth_fasta(uint8_t *out, int64_t n_total, int64_t n_rec, const int64_t *rec_off,
                  const int32_t *hdr_len, const int32_t *wrap, const int64_t *seq_len,
                  const uint32_t *cdf, uint32_t nrun_p32, int nrun_lo, int nrun_hi,
-                 uint32_t lower_p32, const int32_t *len_table, uint64_t seed, int n_threads) {
+                 uint32_t lower_p32, const int32_t *len_table, uint64_t seed, int n_threads,
+                 int64_t first, int64_t last) {
     fasta_job J;
     J.out = out; J.n_total = n_total; J.n_rec = n_rec; J.rec_off = rec_off;
     J.hdr_len = hdr_len; J.wrap = wrap; J.seq_len = seq_len; J.cdf = cdf;
     J.nrun_p32 = nrun_p32; J.nrun_lo = nrun_lo; J.nrun_hi = nrun_hi;
-    J.lower_p32 = lower_p32; J.len_table = len_table; J.seed = seed; J.next = 0;
+    J.lower_p32 = lower_p32; J.len_table = len_table; J.seed = seed;
+    if (first < 0) first = 0;
+    if (last > n_rec) last = n_rec;
+    J.next = first; J.end = last;
+    J.base = (first < n_rec) ? rec_off[first] : 0;
     pthread_mutex_init(&J.lock, NULL);
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;

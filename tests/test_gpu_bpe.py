@@ -4,7 +4,7 @@ tables on short words (every segment / halo setting, including a halo of 0
 that sends every mid-word segment through the exact repair pass), the
 4096-merge table on Markov DNA with N runs, separators, lowercase and many
 records, FASTA input, table validation, and the 1 GiB workload (512 x 2 Mb)
-on sampled records."""
+on every record."""
 import numpy as np
 import pytest
 
@@ -142,11 +142,14 @@ def test_table_validation(P):
     assert ei.value.status == -2
 
 
-def test_full_size_1gib_sampled(P, merges4096):
-    """512 x 2 Mb uppercase ACGT (1 GiB), the default launch: every sampled
-    record's ids equal the oracle's encoding of that record alone, and the
-    offsets are consistent."""
+def test_full_size_1gib_every_record(P, merges4096):
+    """512 x 2 Mb uppercase ACGT (1 GiB), the default launch: every record's
+    ids equal the oracle's encoding of that record, element by element, and
+    the offsets agree.  The oracle runs over ranges of 8 records in worker
+    processes that regenerate their records from the seeded generator."""
     import torch
+
+    from tests import _oracle_pool as pool
     data, offs = synth.bpe_apply_corpus()
     n_seq = len(offs) - 1
     with P.Tokenizer(P.BPE, merges=merges4096) as tok:
@@ -156,10 +159,13 @@ def test_full_size_1gib_sampled(P, merges4096):
         tok.sync()
         n_ids, n_rec = (int(x) for x in tot.cpu().tolist())
         o = o[: n_rec + 1].cpu().numpy()
-        assert n_rec == n_seq and o[0] == 0 and o[-1] == n_ids and np.all(np.diff(o) > 0)
-        rng = np.random.default_rng(5)
-        for r in sorted(set(rng.choice(n_seq, size=6, replace=False).tolist()) | {0, n_seq - 1}):
-            rec = data[offs[r]:offs[r + 1]]
-            want, _ = oracle.encode(rec, oracle.BPE, merges=merges4096)
-            got = ids[int(o[r]):int(o[r + 1])].cpu().numpy()
-            assert np.array_equal(got, want), "record %d" % r
+        got = ids[:n_ids].cpu().numpy()
+        del d, so, ids
+    assert n_rec == n_seq and o[0] == 0 and o[-1] == n_ids and np.all(np.diff(o) > 0)
+    del data
+    ranges = [(r, min(r + 8, n_seq)) for r in range(0, n_seq, 8)]
+    checked = 0
+    for r0, r1, want, wo in pool.run(pool.bpe_corpus_records, ranges):
+        pool.compare(got, o, r0, want, wo, "1 GiB BPE")
+        checked += r1 - r0
+    assert checked == n_seq

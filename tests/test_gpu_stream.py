@@ -187,12 +187,15 @@ def test_poll_pending_then_done(env):
         _same((ids[: res[0]].cpu().numpy(), o[: res[1] + 1].cpu().numpy()), want, "poll")
 
 
-def test_full_size_fasta_stream_sampled(env):
+def test_full_size_fasta_stream_every_record(env):
     """The 8 GiB FASTA stream in pinned host memory, streamed in 64 MiB
-    chunks through 3 slots as the benchmark runs it; records cut by a chunk
-    boundary and a random sample of the rest are re-encoded by the oracle one
-    by one and must match their slice of the output exactly."""
+    chunks through 3 slots as the benchmark runs it: every record's ids equal
+    the oracle's encoding of that record, element by element, records cut by
+    a chunk boundary included.  The oracle runs over ranges of about 128 MB
+    in worker processes that regenerate their records from the seeded
+    generator."""
     torch, P = env
+    from tests import _oracle_pool as pool
     n = 8 << 30
     chunk = 64 << 20
     host = torch.empty(n, dtype=torch.uint8, pin_memory=True)
@@ -208,15 +211,15 @@ def test_full_size_fasta_stream_sampled(env):
     assert bytes_in == n and n_out_rec == n_rec
     o = offs[: n_rec + 1].cpu().numpy()
     assert o[0] == 0 and o[-1] == n_ids and np.all(np.diff(o) >= 0)
+    got = ids[:n_ids].cpu().numpy()
+    del ids, host
     starts = np.append(lay.rec_off, n)
-    cut = [int(np.searchsorted(starts, c, side="right")) - 1 for c in range(chunk, n, chunk)]
-    rng = np.random.default_rng(0)
-    sample = sorted(set(cut[::8]) | set(rng.choice(n_rec, size=12, replace=False).tolist())
-                    | {0, n_rec - 1})
-    hv = host.numpy()
-    for rec in sample:
-        a, b = int(starts[rec]), int(starts[rec + 1])
-        want, wo = oracle.encode(hv[a:b], 1, k=6, fmt=oracle.FASTA)
-        assert wo.tolist() == [0, len(want)]
-        got = ids[int(o[rec]): int(o[rec + 1])].cpu().numpy()
-        assert np.array_equal(got, want), "record %d differs" % rec
+    # record ranges of about 128 MB each
+    cuts = np.searchsorted(starts, np.arange(0, n, 128 << 20), side="left")
+    bounds = sorted(set(int(c) for c in cuts) | {0, n_rec})
+    ranges = [(n, 47, 6, a, b) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+    checked = 0
+    for r0, r1, want, wo in pool.run(pool.fasta_stream_records, ranges):
+        pool.compare(got, o, r0, want, wo, "8 GiB FASTA stream")
+        checked += r1 - r0
+    assert checked == n_rec

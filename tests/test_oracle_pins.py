@@ -2,6 +2,7 @@
 itself -- hand-worked values from the paper's tables, closed forms, invariants,
 and literal brute-force definitions on tiny inputs."""
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -309,8 +310,29 @@ def _tables(n, seed):
 
 
 def test_bpe_bruteforce_all_short_strings():
+    """Every A/C/G/T word of length 1..10 under 50 random valid tables of at
+    most 12 merges (46 drawn at random, 4 learned by the trainer): the
+    literal greedy rule, the rank sweep and the C oracle agree on every word,
+    and every output is self-encoding and pairwise compatible (reading C7).
+    Tables are checked in worker processes (spawned, so no inherited state)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from tests import _bpe_bruteforce
+
+    tables = _tables(46, seed=5)
+    assert len(tables) == 50 and all(1 <= len(t) <= 12 for t in tables)
+    workers = max(1, min(len(tables), len(os.sched_getaffinity(0))))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        counts = list(ex.map(_bpe_bruteforce.check_table, tables))
+    assert counts == [sum(4 ** L for L in range(1, 11))] * 50
+
+
+def test_bpe_bruteforce_literal_empty_and_short():
+    """The Python literal definitions themselves on every word of length
+    0..5 (the array forms above start at length 1)."""
     tables = _tables(6, seed=5)
-    words = [w for L in range(0, 8) for w in itertools.product(range(4), repeat=L)]
+    words = [w for L in range(0, 6) for w in itertools.product(range(4), repeat=L)]
     for merges in tables:
         for w in words:
             c = oracle.bpe_word(np.array(w, dtype=np.int32), merges).tolist()
