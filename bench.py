@@ -1007,7 +1007,9 @@ def run_gpu(args):
         tok.set_launch(*[int(x) for x in args.shape.split(",")])
     tok.reserve(n_bytes, n_seq)
     ids, o_out, totals = tok.alloc_outputs(n_bytes, n_seq, device=dev)
-    stream = torch.cuda.current_stream()
+    # one non-default stream for everything (graph capture needs one)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     flush_rd = torch.ones(64 * 1024 * 1024, dtype=torch.int32, device=dev)
     flush_acc = torch.zeros(1, dtype=torch.int64, device=dev)

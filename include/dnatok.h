@@ -302,6 +302,9 @@ typedef struct {
     int64_t batches_running;
 } dnatok_server_counters;
 
+/* DNATOK_ERR_ARG on a bad configuration; DNATOK_ERR_BUDGET when one request
+ * of max_batch_bytes (input, worst-case ids and offsets) would not fit
+ * budget_bytes on its own. */
 DNATOK_API dnatok_status dnatok_server_create(const dnatok_server_cfg *cfg, dnatok_server **out);
 /* Copy n host bytes into the staging arena and queue them (mode: DNATOK_CHAR
  * with the default table, DNATOK_KMER with cfg.kmer_k, DNATOK_BPE with
@@ -320,6 +323,14 @@ DNATOK_API dnatok_status dnatok_server_read(dnatok_server *s, uint64_t req_id, i
 /* Give the request's device output back to the arena. */
 DNATOK_API dnatok_status dnatok_server_release(dnatok_server *s, uint64_t req_id);
 DNATOK_API dnatok_status dnatok_server_stats(dnatok_server *s, dnatok_server_counters *out);
+/* Failure injection, for testing how a caller handles failed requests: the
+ * next `count` batches the worker launches fail -- kind 1: as if
+ * dnatok_encode refused the batch on the host; kind 2: as if a kernel of the
+ * batch recorded a device-side error (a bounded wait that ran out).  Every
+ * request of such a batch completes with DNATOK_ERR_CUDA from poll/read;
+ * the slot's handle is cleared and the batches after it run normally.
+ * kind 0 cancels.  (No counterpart in the paper.) */
+DNATOK_API dnatok_status dnatok_server_inject(dnatok_server *s, int32_t kind, int32_t count);
 /* Stop the worker, wait for the device, free everything. */
 DNATOK_API void dnatok_server_destroy(dnatok_server *s);
 
@@ -412,9 +423,11 @@ DNATOK_API dnatok_status dnatok_microbatch_rows(int64_t emb_batch_cap, int64_t t
  * feed_stream; consumer_stream then waits for it and `consumer` is called
  * (on this host thread) to enqueue its work on consumer_stream; feed_stream
  * waits for that work before it reuses the buffer.  Each buffer holds
- * rows_per_batch x token_len elements of out_bytes.  Returns once
- * everything is enqueued; a nonzero return from `consumer` stops the loop
- * with DNATOK_ERR_STATE.
+ * rows_per_batch x token_len elements of out_bytes.  ids and id_offsets
+ * must be ready in consumer_stream's order (produced on it, or on a stream
+ * it already waits for): feed_stream first waits for all work enqueued on
+ * consumer_stream before the call.  Returns once everything is enqueued; a
+ * nonzero return from `consumer` stops the loop with DNATOK_ERR_STATE.
  */
 typedef int (*dnatok_feed_consumer)(void *user, int64_t row_begin, int64_t n_rows, void *batch_d,
                                     dnatok_cuda_stream consumer_stream);

@@ -213,6 +213,8 @@ def feed_pipeline(ids, id_offsets, token_len: int, id_pad: int, rows_per_batch: 
             for _ in range(2)]
     fs = feed_stream or torch.cuda.Stream(device=ids.device)
     cs = consumer_stream or torch.cuda.current_stream(ids.device)
+    # the ids may still be in flight on the caller's stream
+    fs.wait_stream(torch.cuda.current_stream(ids.device))
     by_addr = {b.data_ptr(): b for b in bufs}
 
     def _consume(row_begin, n, addr, _stream):

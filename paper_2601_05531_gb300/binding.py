@@ -133,6 +133,7 @@ def lib():
             "dnatok_server_read": (_ST, [_P, ctypes.c_uint64, _P, _I64, ctypes.POINTER(_I64)]),
             "dnatok_server_release": (_ST, [_P, ctypes.c_uint64]),
             "dnatok_server_stats": (_ST, [_P, ctypes.POINTER(ServerCounters)]),
+            "dnatok_server_inject": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
             "dnatok_server_destroy": (None, [_P]),
             "dnatok_encode_kmer_noalloc": (_ST, [ctypes.c_int, _P, _I64, _P, _I64, _P, _I64, _P,
                                                  _I64, _P, _P]),
@@ -390,6 +391,10 @@ def dnatok_server_stats(srv) -> dict:
     c = ServerCounters()
     check(lib().dnatok_server_stats(srv, ctypes.byref(c)))
     return {k: getattr(c, k) for k, _ in ServerCounters._fields_}
+
+
+def dnatok_server_inject(srv, kind: int, count: int = 1) -> None:
+    check(lib().dnatok_server_inject(srv, kind, count))
 
 
 def dnatok_server_destroy(srv) -> None:

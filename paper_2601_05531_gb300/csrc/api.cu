@@ -75,7 +75,7 @@ dnatok_status next_epoch(dnatok_handle *h, cudaStream_t s, unsigned *epoch) {
     h->epoch++;
     if ((h->epoch & ((1u << kEpochBits) - 1)) == 0) {  // epoch wrap: forget every old descriptor
         cudaError_t e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * h->desc_cap, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_gate, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_gate, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
         h->epoch++;
     }
@@ -222,8 +222,8 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
     if (e == cudaSuccess) e = cudaMemset(h->d_counter, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_gate, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(h->d_gate, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_gate, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(h->d_gate, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess && mode == DNATOK_KMER_TABLE) {
         e = cudaMalloc(&h->d_klut, sizeof(int32_t) * (size_t)n_index);
         if (e == cudaSuccess)

@@ -222,11 +222,17 @@ dnatok_status dnatok_feed_pipeline(const int32_t *ids_d, const int64_t *id_offse
     cudaStream_t fs = reinterpret_cast<cudaStream_t>(feed_stream);
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(consumer_stream);
     void *buf[2] = {buf0_d, buf1_d};
-    cudaEvent_t ready[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
-    cudaError_t e = cudaSuccess;
+    cudaEvent_t ready[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr}, entry = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&entry, cudaEventDisableTiming);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming);
+    }
+    // the ids come from work ordered on consumer_stream (the caller's
+    // stream): the feed stream starts after everything enqueued there so far
+    if (e == cudaSuccess && fs != cs) {
+        e = cudaEventRecord(entry, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, entry, 0);
     }
     st = e == cudaSuccess ? DNATOK_OK : DNATOK_ERR_CUDA;
     const long long *offs = reinterpret_cast<const long long *>(id_offsets_d);
@@ -255,6 +261,7 @@ dnatok_status dnatok_feed_pipeline(const int32_t *ids_d, const int64_t *id_offse
         if (ready[j]) cudaEventDestroy(ready[j]);
         if (freed[j]) cudaEventDestroy(freed[j]);
     }
+    if (entry) cudaEventDestroy(entry);
     return st;
 }
 

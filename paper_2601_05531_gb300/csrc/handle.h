@@ -31,7 +31,8 @@ struct dnatok_handle {
     long long rec_cap = 0;
     unsigned long long *d_counter = nullptr;
     int *d_status = nullptr;
-    unsigned *d_gate = nullptr;  // direct path -> general path switch (an epoch)
+    unsigned *d_gate = nullptr;  // [0]: direct path -> general path switch, [1]: record plan
+                                 // published (both hold launch epochs)
     unsigned epoch = 0;
 
     dnatok::LaunchShape shape{16384, 256, 4, 8};

@@ -99,7 +99,8 @@ struct Batch {
     int n_unreleased = 0;
     cudaEvent_t done = nullptr;
     long long *h_offs = nullptr;            // pinned: seq offsets in, id offsets back
-    int *h_status = nullptr;                // pinned
+    int *h_status = nullptr;                // pinned: the handle's device status, copied back
+    bool launch_failed = false;             // dnatok_encode refused the batch on the host
     long long offs_cap = 0;
 };
 
@@ -127,11 +128,16 @@ struct dnatok_server {
     uint64_t next_id = 1;
     long long batches_launched = 0;
     std::string error;
+    // failure injection for tests (dnatok_server_inject): the next
+    // inject_count batches fail as `inject_kind` says
+    int inject_kind = 0, inject_count = 0;
 };
 
 using namespace dnatok;
 
 namespace {
+
+const int kInjectedDeviceError = DEV_TIMEOUT;
 
 // Worker-side: finish batches whose event fired.  Called with mu held.
 void reap(dnatok_server *S) {
@@ -141,7 +147,17 @@ void reap(dnatok_server *S) {
         const cudaError_t q = cudaEventQuery(B.done);
         if (q == cudaErrorNotReady) continue;
         const double t = now_us();
-        const bool ok = (q == cudaSuccess && *B.h_status == 0);
+        const bool dev_error = (q == cudaSuccess && *B.h_status != 0);
+        const bool ok = (q == cudaSuccess && !B.launch_failed && !dev_error);
+        if (dev_error) {
+            // the handle's status word (and, for a look-back that stopped
+            // early, its tile counters) must be clear before its next batch;
+            // the slot's stream orders this before anything launched later
+            dnatok_handle *h = S->handles[B.slot * 3 + B.mode];
+            cudaStream_t st = S->streams[B.slot];
+            cudaMemsetAsync(h->d_status, 0, sizeof(int), st);
+            cudaMemsetAsync(h->d_counter, 0, 2 * sizeof(unsigned long long), st);
+        }
         for (size_t i = 0; i < B.reqs.size(); ++i) {
             Request &R = S->reqs[B.reqs[i]];
             R.state = ok ? RQ_DONE : RQ_FAILED;
@@ -252,19 +268,29 @@ void admit(dnatok_server *S) {
                 B.h_offs[i + 1] = pos;
             }
             cudaMemcpyAsync(d_so, B.h_offs, 8 * (nr + 1), cudaMemcpyHostToDevice, st);
-            dnatok_status rc = dnatok_encode(h, d_in, nb, reinterpret_cast<int64_t *>(d_so), nr,
-                                             d_ids, ob + 4, reinterpret_cast<int64_t *>(d_io),
-                                             nr + 1, reinterpret_cast<int64_t *>(d_tot),
-                                             reinterpret_cast<dnatok_cuda_stream>(st));
+            int inject = 0;
+            if (S->inject_count > 0) {
+                inject = S->inject_kind;
+                --S->inject_count;
+            }
+            if (inject == 2)  // a device-side error, as a bounded wait that ran out records it
+                cudaMemcpyAsync(h->d_status, &kInjectedDeviceError, sizeof(int),
+                                cudaMemcpyHostToDevice, st);
+            dnatok_status rc =
+                inject == 1 ? DNATOK_ERR_STATE
+                            : dnatok_encode(h, d_in, nb, reinterpret_cast<int64_t *>(d_so), nr,
+                                            d_ids, ob + 4, reinterpret_cast<int64_t *>(d_io),
+                                            nr + 1, reinterpret_cast<int64_t *>(d_tot),
+                                            reinterpret_cast<dnatok_cuda_stream>(st));
             // the id offsets come back to the same pinned array (after the
             // kernel has read the sequence offsets it was given)
             cudaMemcpyAsync(B.h_offs, d_io, 8 * (nr + 1), cudaMemcpyDeviceToHost, st);
             cudaMemcpyAsync(B.h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
             cudaEventRecord(B.done, st);
-            if (rc != DNATOK_OK) {
-                *B.h_status = -1;
-                S->error = h->last_error;
-            }
+            // a refusal on the host is kept apart from the status word that
+            // the copy above writes back
+            B.launch_failed = (rc != DNATOK_OK);
+            if (rc != DNATOK_OK) S->error = inject == 1 ? "injected launch failure" : h->last_error;
             ++S->batches_launched;
         }
     }
@@ -319,6 +345,8 @@ dnatok_status dnatok_server_create(const dnatok_server_cfg *cfg, dnatok_server *
     if (!S) return DNATOK_ERR_NOMEM;
     S->cfg = *cfg;
     S->n_slots = cfg->n_slots;
+    // one request of max_batch_bytes must fit the budget on its own, or it
+    // could never be admitted
     dnatok_tables none{nullptr, nullptr, 0, nullptr, nullptr};
     dnatok_tables bpe{nullptr, cfg->merges, cfg->n_merges, nullptr, nullptr};
     for (int slot = 0; slot < S->n_slots; ++slot) {
@@ -345,6 +373,21 @@ dnatok_status dnatok_server_create(const dnatok_server_cfg *cfg, dnatok_server *
         }
         S->streams.push_back(s);
         S->slot_busy.push_back(0);
+    }
+    {
+        long long worst = 0;
+        for (int mode = 0; mode < 3; ++mode) {
+            int64_t cap = 0;
+            dnatok_max_tokens(S->handles[mode], cfg->max_batch_bytes, 1, &cap);
+            const long long in_b = ((cfg->max_batch_bytes + 15) & ~15ll) + 16;
+            const long long out_b = ((4 * (cap + 4) + 15) & ~15ll) + 16 + 16 + 64;
+            const long long f = ((in_b + 255) & ~255ll) + ((out_b + 255) & ~255ll);
+            if (f > worst) worst = f;
+        }
+        if (worst > cfg->budget_bytes) {
+            server_free(S);
+            return DNATOK_ERR_BUDGET;
+        }
     }
     if (cudaMalloc(&S->d_arena, (size_t)cfg->budget_bytes) != cudaSuccess ||
         cudaHostAlloc(&S->h_arena, (size_t)cfg->host_arena_bytes, cudaHostAllocDefault) !=
@@ -439,6 +482,14 @@ dnatok_status dnatok_server_release(dnatok_server *S, uint64_t req_id) {
         S->reqs.erase(it);
     }
     S->cv.notify_one();
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_server_inject(dnatok_server *S, int32_t kind, int32_t count) {
+    if (!S || kind < 0 || kind > 2 || count < 0) return DNATOK_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->inject_kind = kind;
+    S->inject_count = kind == 0 ? 0 : count;
     return DNATOK_OK;
 }
 

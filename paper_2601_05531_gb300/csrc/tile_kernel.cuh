@@ -74,7 +74,9 @@ struct TileParams {
     const unsigned *gate;          // non-null: run only if *gate == gate_epoch
     unsigned gate_epoch;
     unsigned *clear_gate;          // non-null (captured launches behind the direct path):
-                                   // after a run, the last CTA clears *clear_gate and the
+                                   // clear_gate[1] (the direct kernel's plan flag) is
+                                   // cleared on exit; after a run, the last CTA also
+                                   // clears clear_gate[0] and the
                                    // chunk descriptors, so the next replay starts clean
 };
 
@@ -401,7 +403,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
     // behind the direct path: run only when it found its premise broken
     if (p.gate) {
         pdl_wait();
-        if (*(volatile const unsigned *)p.gate != p.gate_epoch) return;
+        if (*(volatile const unsigned *)p.gate != p.gate_epoch) {
+            // captured: the epochs are baked into the graph, so the direct
+            // kernel's record-plan flag is cleared for the next replay
+            if (p.clear_gate && blockIdx.x == 0 && threadIdx.x == 0)
+                *(volatile unsigned *)(p.clear_gate + 1) = 0u;
+            return;
+        }
     }
 
     extern __shared__ __align__(128) uint8_t smem[];
@@ -1191,7 +1199,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
             uint4 *d = reinterpret_cast<uint4 *>(p.desc);
             const long long nw = p.n_chunks * (long long)(sizeof(TileDesc) / sizeof(uint4));
             for (long long i = tid; i < nw; i += NT) d[i] = make_uint4(0u, 0u, 0u, 0u);
-            if (tid == 0) *(volatile unsigned *)p.clear_gate = 0u;
+            if (tid == 0) {
+                *(volatile unsigned *)p.clear_gate = 0u;
+                *(volatile unsigned *)(p.clear_gate + 1) = 0u;
+            }
         }
     }
 }

@@ -107,6 +107,33 @@ def test_feed_pipeline_with_embedding_consumer(P, rows_per_batch):
     assert torch.equal(result, torch.nn.functional.embedding(want, emb))
 
 
+def test_feed_pipeline_right_after_encode_no_sync(P):
+    """encode() and then feed_pipeline() on the caller's current stream with no
+    synchronize in between: the feed must see the finished ids."""
+    import torch
+    data, offs = synth.kmer_batch_4096(n_seq=512)
+    want_ids, want_o = oracle.encode(data, oracle.KMER, k=6, seq_offsets=offs)
+    T = 512
+    emb = torch.randn(4099, 8, device="cuda")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):  # the caller works on its own stream
+        with P.Tokenizer(P.KMER, k=6) as tok:
+            ids, o, tot = tok.alloc_outputs(len(data), len(offs) - 1, device="cuda")
+            ids.fill_(-7)
+            tok.encode(dev(data), dev(offs), ids, o, tot, stream=side)
+            result = torch.empty(len(offs) - 1, T, 8, device="cuda")
+
+            def consumer(row_begin, batch, stream):
+                with torch.cuda.stream(stream):
+                    result[row_begin:row_begin + batch.shape[0]] = \
+                        torch.nn.functional.embedding(batch, emb)
+
+            P.feed_pipeline(ids, o[: len(offs)], T, 4097, 64, consumer)
+            side.synchronize()
+    want = torch.from_numpy(oracle.feed(want_ids, want_o, T, 4097)).cuda()
+    assert torch.equal(result, torch.nn.functional.embedding(want, emb))
+
+
 def test_feed_full_kmer_batch_4096(P):
     import torch
     data, offs = synth.kmer_batch_4096()

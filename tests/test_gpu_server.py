@@ -166,3 +166,56 @@ def test_oversize_and_unknown(env):
         assert ei.value.status == -7
     finally:
         B.dnatok_server_destroy(srv)
+
+
+def _one(B, srv, mode, b, timeout=30.0):
+    r = B.dnatok_server_submit(srv, mode, b.ctypes.data if len(b) else 0, len(b))
+    assert r is not None
+    t0 = time.time()
+    while True:
+        try:
+            out = B.dnatok_server_poll(srv, r)
+        except Exception as e:  # a failed request
+            return r, e
+        if out is not None:
+            return r, out
+        assert time.time() - t0 < timeout, "request did not complete"
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_failed_batch_then_next_request_exact(env, kind):
+    """A batch that fails -- refused on the host (kind 1) or with a device-side
+    error recorded by a kernel (kind 2), both injected -- completes with an
+    error for its request; the next request, on the same slot and handle,
+    comes back bit-exact against the oracle."""
+    torch, P = env
+    B = P.binding
+    m = np.loadtxt(TABLE, dtype=np.int32)
+    reqs = _requests(91, 6, lo=1000, hi=200_000)
+    srv = B.dnatok_server_create(budget_bytes=64 << 20, host_arena_bytes=16 << 20,
+                                 max_batch_bytes=1 << 20, max_batch_requests=8, n_slots=1,
+                                 kmer_k=6, merges=m)
+    try:
+        for mode in (0, 1, 2):
+            b = reqs[mode][1]
+            B.dnatok_server_inject(srv, kind, 1)
+            r, out = _one(B, srv, mode, b)
+            assert isinstance(out, P.DnatokError) and out.status == -4, out
+            B.dnatok_server_release(srv, r)
+            r, out = _one(B, srv, mode, b)
+            assert not isinstance(out, Exception), out
+            got = B.dnatok_server_read(srv, r, out[1])
+            assert np.array_equal(got, _want(mode, b, m)), (kind, mode)
+            B.dnatok_server_release(srv, r)
+        assert B.dnatok_server_stats(srv)["device_bytes_in_use"] == 0
+    finally:
+        B.dnatok_server_destroy(srv)
+
+
+def test_budget_too_small_for_one_request(env):
+    torch, P = env
+    B = P.binding
+    with pytest.raises(P.DnatokError) as ei:
+        B.dnatok_server_create(budget_bytes=1 << 20, host_arena_bytes=4 << 20,
+                               max_batch_bytes=1 << 20, max_batch_requests=8, n_slots=1)
+    assert ei.value.status == -5
