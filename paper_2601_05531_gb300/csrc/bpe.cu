@@ -10,25 +10,30 @@
 //  * A tokenization equals BPE(w) iff every token is self-encoding
 //    (BPE(str t) = [t]) and every adjacent pair (a, b) is compatible
 //    (BPE(str a + str b) = [a, b]).
-//  * So last(j), the last token of BPE of the word prefix ending at symbol
-//    j, is the self-encoding suffix token t compatible with last(j - |t|)
-//    (anything at the word start): one left-to-right pass over the symbols
-//    with a trie of reversed token strings and a compatibility bitmap.
-//    Only |last(j)| (one byte per symbol) is stored.
+//  * So last(j), the token of BPE of the word prefix ending at symbol j that
+//    ends at j, is the longest self-encoding token t ending at j that starts
+//    the word or is compatible with last(j - |t|): one left-to-right pass.
+//    The candidates at j are the tokens that are suffixes of the text read so
+//    far; an Aho-Corasick automaton over the token strings gives them, longest
+//    first, from its state (one 16-byte node record per step: the state's
+//    four transitions and its first two candidates, and a link to the rest).
+//    Compatibility is one bit of a V x V bitmap (L2-resident).
 //  * The choice at j depends only on the previous lmax values, so a pass
 //    started mid-word (a segment's halo) agrees with the exact pass once a
 //    window of lmax values agrees; segments are computed independently and
 //    checked against their left neighbour, and the rare failure is redone
-//    exactly, in order.
+//    exactly, in order, within the run of segments that depend on it.
 //  * The tokens are the chain j -> j - |last(j)| from the last symbol.  Each
-//    segment maps every possible entry (the first chain element at or below
-//    its last symbol: lmax choices) to its exit and token count; the maps
-//    almost always collapse to one exit, which makes the entries local.
-//    Counts are scanned for the output positions; each segment then writes
-//    its ids walking its chain backwards.
+//    segment's pass also carries, for every position, where the chain from
+//    there leaves the segment and how many tokens it holds, so the segment's
+//    map from each of its lmax possible entries to (exit, count) comes out of
+//    the same pass.  The maps almost always collapse to one exit, which makes
+//    the entries local.  Counts are scanned for the output positions; each
+//    segment then writes its ids walking its chain backwards.
 //
 // Kernels per encode: the symbol pass (tile kernel, MODE_SYM), bpe_dp,
-// bpe_sync, bpe_repair, bpe_maps, bpe_entries, three scan kernels,
+// bpe_sync, three kernels that list the segments to repair in order with the
+// region each belongs to, bpe_repair, bpe_entries, three scan kernels,
 // bpe_emit, bpe_offsets.
 #include <algorithm>
 #include <cstring>
@@ -42,44 +47,42 @@ using namespace dnatok;
 namespace {
 
 constexpr int kMaxTokLen = 32;      // longest supported self-encoding token (bases)
-constexpr unsigned kNoTok = 0xFFFFu;
+constexpr unsigned kNone16 = 0xFFFFu;
 constexpr unsigned kHashEmpty = 0xFFFFFFFFu;
 constexpr int kScanItems = 8;       // per thread in the scan kernels
 constexpr int kScanThreads = 256;
+constexpr int kDpThreads = 128;     // threads (segments) per block of the merge pass
 
+// Automaton node record (16 bytes): x, y = transitions on A, C | G, T (u16
+// each); z = first two candidate tokens (u16 each, 0xFFFF = none); w =
+// their lengths (6 bits each) and, in the top 16 bits, the node whose record
+// starts the rest of the candidate list (0xFFFF = none).  Candidates are the
+// self-encoding tokens that are suffixes of the node's string, longest first.
 struct BpeTables {
-    int V;            // 4 + M token ids; N_ID = V
-    int lmax;         // longest self-encoding token
-    int n_deep;       // deep trie nodes (index 0 = "none")
-    // tokens of 1..5 bases: direct tables indexed by the d-mer code (last
-    // base in the low bits), at offsets 0, 4, 20, 84, 340 (1364 entries)
-    const unsigned short *kmtok;
-    // tokens of 6+ bases: the last 6 bases index node6 (4096 entries) -> a
-    // node of the trie of reversed strings below depth 6
-    const unsigned short *node6;
-    const uint2 *child;          // per deep node: 4 x u16 children (0 = none)
-    const unsigned short *tok;   // per deep node: token id ending here or kNoTok
-    const unsigned *compat;      // V x V bits, row = left token
+    int V;                 // 4 + M token ids; N_ID = V
+    int lmax;              // longest self-encoding token
+    const uint4 *node;     // automaton, node 0 = root (empty string)
+    const uint8_t *tok_len;  // V + 1 entries (N_ID has length 1)
+    const unsigned *compat;  // V x V bits, row = left token
 };
-
-// offset of the d-base table: (4^d - 4) / 3 = 0, 4, 20, 84, 340 for d = 1..5
-__host__ __device__ constexpr int km_off(int d) { return ((1 << (2 * d)) - 4) / 3; }
-constexpr int kKmTotal = 1364;
 
 struct BpeWork {
     const uint8_t *sym;          // symbols 0..3 bases, 4 N-class
-    uint8_t *len;                // |last(j)| per symbol
-    uint8_t *halo;               // per segment: halo values of its fresh pass
+    unsigned short *tok;         // last(j) per symbol (N_ID for an N-class symbol)
+    unsigned short *halo;        // per segment: halo values of its fresh pass (0xFFFF: none)
     uint8_t *flags;              // per segment: 1 = exact start
+    uint8_t *bad;                // per segment: 1 = its halo did not agree
     uint8_t *map_v;              // per segment x 32 entries: exit offset
-    unsigned short *map_c;       // per segment x 32 entries: token count
+    unsigned *map_c;             // per segment x 32 entries: token count
     uint8_t *const_v;            // per segment: common exit or 0xFF
     unsigned *count;             // per segment: tokens on the true chain
     uint8_t *entry;              // per segment: true entry offset
     long long *base;             // per segment: exclusive prefix of count
     long long *block_sums;
-    int *bad;                    // [0] = count, then segment ids
-    unsigned *bits;              // per segment: token ends, one bit per symbol
+    long long *rep_sums;         // block sums of the repair listing (count, region)
+    int *n_bad;                  // segments whose halo did not agree
+    int *rep_list;               // segments to repair, in order
+    int *rep_region;             // per listed segment: the last exact segment before it
     long long *tot;              // {n_sym, n_rec} from the symbol pass
     long long *rec_off;          // record starts (symbols), rewritten as id offsets
     long long offsets_cap;
@@ -93,27 +96,14 @@ struct BpeWork {
 
 // ---------------------------------------------------------------- helpers
 
-__device__ __forceinline__ unsigned trie_child(const uint2 *child, unsigned node, unsigned c) {
-    const uint2 v = child[node];
-    const unsigned w = (c < 2) ? v.x : v.y;
-    return (c & 1) ? (w >> 16) : (w & 0xFFFFu);
-}
-
 __device__ __forceinline__ bool compat_bit(const unsigned *compat, int V, unsigned a, unsigned b) {
     const unsigned long long bit = (unsigned long long)a * (unsigned)V + b;
     return (__ldg(compat + (bit >> 5)) >> (bit & 31)) & 1u;
 }
 
-// Token id of the L symbols ending at e (L <= lmax).
-__device__ __forceinline__ unsigned token_at(const BpeTables &T, const uint8_t *sym, long long e,
-                                             int L) {
-    unsigned code = 0;
-    const int d0 = L < 6 ? L : 6;
-    for (int d = d0; d >= 1; --d) code = (code << 2) | sym[e - d + 1];
-    if (L <= 5) return T.kmtok[km_off(L) + code];
-    unsigned node = T.node6[code];
-    for (int d = 7; d <= L; ++d) node = trie_child(T.child, node, sym[e - d + 1]);
-    return T.tok[node];
+__device__ __forceinline__ unsigned node_next(const uint4 &nd, unsigned c) {
+    const unsigned w = (c < 2) ? nd.x : nd.y;
+    return (c & 1) ? (w >> 16) : (w & 0xFFFFu);
 }
 
 // Largest r with rec_off[r] <= x (rec_off[0] = 0, non-decreasing, n entries).
@@ -127,47 +117,66 @@ __device__ __forceinline__ long long rec_upper(const long long *rec_off, long lo
     return lo;
 }
 
-// One step of the prefix DP at symbol j (a base).  reg: codes of the word so
-// far (newest in the low bits); wd: symbols of the word through j; ring:
-// last token ids by position mod 32.  Candidates are tried longest first;
-// the first that starts the word or is compatible with the token before it
-// is last(j).  Returns (length << 16) | token.
-__device__ __forceinline__ unsigned dp_step(const BpeTables &T, unsigned long long reg, int wd,
-                                            long long j, const unsigned short *ring) {
-    const int dm = wd < T.lmax ? wd : T.lmax;
-    auto fits = [&](int d, unsigned t) -> bool {
-        if (d == wd) return true;
-        return compat_bit(T.compat, T.V, ring[(j - d) & 31], t);
-    };
-    if (dm >= 6) {
-        const unsigned n6 = T.node6[(unsigned)reg & 0xFFFu];
-        if (n6) {
-            unsigned short deep[kMaxTokLen];
-            int nd = 0;
-            unsigned node = n6;
-            for (int d = 7; d <= dm; ++d) {
-                node = trie_child(T.child, node, (unsigned)(reg >> (2 * (d - 1))) & 3u);
-                if (!node) break;
-                const unsigned t = T.tok[node];
-                deep[d - 7] = (unsigned short)t;
-                nd = d - 6;
-            }
-            for (int q = nd - 1; q >= 0; --q) {
-                const unsigned t = deep[q];
-                if (t != kNoTok && fits(q + 7, t)) return ((unsigned)(q + 7) << 16) | t;
-            }
-            const unsigned t6 = T.tok[n6];
-            if (t6 != kNoTok && fits(6, t6)) return (6u << 16) | t6;
-        }
+// The state of one left-to-right pass: automaton node (and its record), the
+// word length so far (capped at 63), and a ring of the last R token ids in
+// shared memory (column `tid` of an R x kDpThreads array).
+template <int R>
+struct DpPass {
+    uint4 nd;               // record of the current node
+    unsigned state;
+    int wd;
+    unsigned short *ring;   // ring[i * kDpThreads]
+};
+
+// One step at symbol j (a base c): move the automaton, then take the first
+// candidate (longest first) that starts the word or is compatible with the
+// token before it.  The single base at the end of every list is taken
+// without a check (no other candidate fits).  Returns (length << 16) | token.
+template <int R>
+__device__ __forceinline__ unsigned dp_step(const BpeTables &T, DpPass<R> &P, long long j, unsigned c) {
+    P.state = node_next(P.nd, c);
+    P.nd = __ldg(T.node + P.state);
+    if (P.wd < 63) ++P.wd;
+    const int wd = P.wd;
+    unsigned t1 = P.nd.z & 0xFFFFu, t2 = P.nd.z >> 16;
+    int l1 = (int)(P.nd.w & 63u), l2 = (int)((P.nd.w >> 6) & 63u);
+    // both candidates' checks are issued before either is used
+    const bool n1 = (l1 != wd) && (l1 > 1);
+    const bool n2 = (t2 != kNone16) && (l2 != wd) && (l2 > 1);
+    const unsigned a1 = n1 ? P.ring[((j - l1) & (R - 1)) * kDpThreads] : 0u;
+    const unsigned a2 = n2 ? P.ring[((j - l2) & (R - 1)) * kDpThreads] : 0u;
+    const bool ok1 = !n1 || compat_bit(T.compat, T.V, a1, t1);
+    const bool ok2 = !n2 || compat_bit(T.compat, T.V, a2, t2);
+    if (ok1) return ((unsigned)l1 << 16) | t1;
+    if (t2 != kNone16 && ok2) return ((unsigned)l2 << 16) | t2;
+    // the rest of the list, two candidates per record
+    unsigned nx = P.nd.w >> 16;
+    unsigned last = ((unsigned)l2 << 16) | t2;
+    for (int guard = 0; nx != kNone16 && guard < kMaxTokLen; ++guard) {
+        const uint4 q = __ldg(T.node + nx);
+        t1 = q.z & 0xFFFFu;
+        t2 = q.z >> 16;
+        l1 = (int)(q.w & 63u);
+        l2 = (int)((q.w >> 6) & 63u);
+        if (l1 == wd || l1 == 1 ||
+            compat_bit(T.compat, T.V, P.ring[((j - l1) & (R - 1)) * kDpThreads], t1))
+            return ((unsigned)l1 << 16) | t1;
+        last = ((unsigned)l1 << 16) | t1;
+        if (t2 == kNone16) break;
+        if (l2 == wd || l2 == 1 ||
+            compat_bit(T.compat, T.V, P.ring[((j - l2) & (R - 1)) * kDpThreads], t2))
+            return ((unsigned)l2 << 16) | t2;
+        last = ((unsigned)l2 << 16) | t2;
+        nx = q.w >> 16;
     }
-    unsigned t5[5];
-#pragma unroll
-    for (int d = 1; d <= 5; ++d)
-        t5[d - 1] = T.kmtok[km_off(d) + ((unsigned)reg & ((1u << (2 * d)) - 1u))];
-#pragma unroll
-    for (int d = 5; d >= 2; --d)
-        if (d <= dm && t5[d - 1] != kNoTok && fits(d, t5[d - 1])) return ((unsigned)d << 16) | t5[d - 1];
-    return (1u << 16) | t5[0];  // a single base: no other candidate fits
+    return last;  // unreachable for a valid table (the single base always fits)
+}
+
+template <int R>
+__device__ __forceinline__ void dp_reset(const BpeTables &T, DpPass<R> &P) {
+    P.state = 0;
+    P.nd = __ldg(T.node);
+    P.wd = 0;
 }
 
 // ------------------------------------------------------- table building
@@ -190,7 +199,6 @@ __device__ __forceinline__ unsigned rank_of(const RankHash &h, unsigned a, unsig
         s = (s + 1) & h.mask;
     }
 }
-
 // Greedy BPE (C7) of a short symbol string s[0..n) in place.  boundary >= 0:
 // stop and return -1 as soon as a merge would join s[boundary-1] and
 // s[boundary] (the crossing that makes a pair incompatible).
@@ -268,36 +276,108 @@ __global__ void bpe_compat_kernel(RankHash h, const uint8_t *pool, const int *po
 
 // -------------------------------------------------------- encode kernels
 
-extern __shared__ __align__(16) unsigned char bpe_smem[];
-
-// Copy the lookup tables into shared memory (when they fit) and return the
-// tables the block uses.
-__device__ BpeTables stage_tables(const BpeTables &G, bool smem) {
-    if (!smem) return G;
-    uint2 *c = reinterpret_cast<uint2 *>(bpe_smem);
-    unsigned short *t = reinterpret_cast<unsigned short *>(c + G.n_deep);
-    unsigned short *n6 = t + G.n_deep;
-    unsigned short *km = n6 + 4096;
-    for (int i = threadIdx.x; i < G.n_deep; i += blockDim.x) {
-        c[i] = G.child[i];
-        t[i] = G.tok[i];
+// One pass over symbols [j_begin, e) of segment `seg` (which starts at s),
+// from the state in P (set up for j_begin).  Values before s go to the
+// segment's halo, values from s on to W.tok; from s on the pass also carries
+// F(j) = (exit << 24) | count: where the chain j -> j - |last(j)| first
+// drops below s (offset s - 1 - exit position, < lmax) and how many tokens it
+// holds until then.  At the end F of the last lmax positions is the
+// segment's map.  `exact` turns true when the pass meets a true word start
+// before s.  16 symbols per load and 16 values per pair of stores: s, H and
+// the buffers are 16-aligned; j_begin only shifts where the first block
+// starts.
+template <int R>
+__device__ void seg_pass(const BpeTables &T, const BpeWork &W, long long seg, long long s,
+                         long long e, long long j_begin, long long r, DpPass<R> &P,
+                         unsigned *ringf, bool &exact) {
+    const long long nb = W.tot[1] + 1;
+    long long next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
+    unsigned short *halo = W.halo + seg * (long long)W.H;
+    const long long h0 = s - W.H;
+    const unsigned N_ID = (unsigned)T.V;
+    for (long long j0 = j_begin & ~15ll; j0 < e; j0 += 16) {
+        const uint4 sv = *reinterpret_cast<const uint4 *>(W.sym + j0);
+        const unsigned long long s_lo = ((unsigned long long)sv.y << 32) | sv.x;
+        const unsigned long long s_hi = ((unsigned long long)sv.w << 32) | sv.z;
+        // four values per 64-bit word; 0xFFFF: no value
+        unsigned long long o0 = ~0ull, o1 = ~0ull, o2 = ~0ull, o3 = ~0ull;
+        const int q0 = (j0 < j_begin) ? (int)(j_begin - j0) : 0;
+        const int q1 = (e - j0 < 16) ? (int)(e - j0) : 16;
+#pragma unroll 1
+        for (int q = q0; q < q1; ++q) {
+            const long long j = j0 + q;
+            while (j == next_b) {
+                dp_reset(T, P);
+                ++r;
+                next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
+                if (j < s) exact = true;  // a record starts in the halo
+            }
+            const unsigned c =
+                (unsigned)((q < 8 ? s_lo >> (8 * q) : s_hi >> (8 * (q - 8))) & 0xFFu);
+            unsigned L, t;
+            if (c >= 4) {
+                L = 1;
+                t = N_ID;
+                dp_reset(T, P);
+                if (j < s) exact = true;  // a word starts after it, before the segment
+            } else {
+                const unsigned pk = dp_step<R>(T, P, j, c);
+                L = pk >> 16;
+                t = pk & 0xFFFFu;
+            }
+            P.ring[(j & (R - 1)) * kDpThreads] = (unsigned short)t;
+            if (j >= s) {
+                const long long back = j - (long long)L;
+                const unsigned F = back < s ? ((unsigned)(s - 1 - back) << 24) | 1u
+                                            : ringf[(back & (R - 1)) * kDpThreads] + 1u;
+                ringf[(j & (R - 1)) * kDpThreads] = F;
+            }
+            const int sh = 16 * (q & 3);
+            const unsigned long long keep = ~(0xFFFFull << sh), v = (unsigned long long)t << sh;
+            const int g = q >> 2;
+            if (g == 0) o0 = (o0 & keep) | v;
+            if (g == 1) o1 = (o1 & keep) | v;
+            if (g == 2) o2 = (o2 & keep) | v;
+            if (g == 3) o3 = (o3 & keep) | v;
+        }
+        const uint4 v0 = make_uint4((unsigned)o0, (unsigned)(o0 >> 32), (unsigned)o1,
+                                    (unsigned)(o1 >> 32));
+        const uint4 v1 = make_uint4((unsigned)o2, (unsigned)(o2 >> 32), (unsigned)o3,
+                                    (unsigned)(o3 >> 32));
+        uint4 *dst = (j0 >= s) ? reinterpret_cast<uint4 *>(W.tok + j0)
+                               : reinterpret_cast<uint4 *>(halo + (j0 - h0));
+        if (j0 >= s || W.H > 0) {
+            dst[0] = v0;
+            dst[1] = v1;
+        }
     }
-    for (int i = threadIdx.x; i < 4096; i += blockDim.x) n6[i] = G.node6[i];
-    for (int i = threadIdx.x; i < kKmTotal; i += blockDim.x) km[i] = G.kmtok[i];
-    __syncthreads();
-    BpeTables T = G;
-    T.child = c;
-    T.tok = t;
-    T.node6 = n6;
-    T.kmtok = km;
-    return T;
+    if (j_begin < s) {
+        // halo positions before the pass began hold no value
+        for (long long x = h0; x < (j_begin & ~15ll); ++x) halo[x - h0] = (unsigned short)kNone16;
+    }
+    // the map: entry u (chain from e - 1 - u) -> (exit offset, tokens)
+    unsigned first = 0xFFFFFFFFu;
+    bool same = true;
+    for (int u = 0; u < T.lmax; ++u) {
+        const long long p = e - 1 - u;
+        const unsigned F = (p >= s) ? ringf[(p & (R - 1)) * kDpThreads]
+                                    : ((unsigned)(s - 1 - p) << 24);
+        const unsigned v = F >> 24;
+        W.map_v[seg * 32 + u] = (uint8_t)v;
+        W.map_c[seg * 32 + u] = F & 0xFFFFFFu;
+        if (u == 0) first = v;
+        else if (v != first) same = false;
+    }
+    W.const_v[seg] = same ? (uint8_t)first : (uint8_t)0xFF;
 }
 
-// The prefix DP over one segment (thread per segment), started lmax..H
-// symbols before it unless a word starts closer.
-__global__ void __launch_bounds__(256) bpe_dp_kernel(BpeTables G, bool smem, BpeWork W) {
-    const BpeTables T = stage_tables(G, smem);
-    const long long seg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// The merge pass over one segment (thread per segment), started H symbols
+// before it unless a word starts closer.
+template <int R>
+__global__ void __launch_bounds__(kDpThreads) bpe_dp_kernel(BpeTables T, BpeWork W) {
+    __shared__ unsigned short ring_t[R * kDpThreads];
+    __shared__ unsigned ring_f[R * kDpThreads];
+    const long long seg = blockIdx.x * (long long)kDpThreads + threadIdx.x;
     if (dev_failed(W.status)) return;
     const long long n_sym = W.tot[0], n_rec = W.tot[1];
     if (n_rec + 1 > W.offsets_cap) {
@@ -316,193 +396,195 @@ __global__ void __launch_bounds__(256) bpe_dp_kernel(BpeTables G, bool smem, Bpe
         exact = true;
     }
     while (r + 1 < nb && W.rec_off[r + 1] <= a) ++r;  // empty records at a
-    long long next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
-    unsigned short ring[32];
-    unsigned long long reg = 0;
-    int wd = 0;
-    uint8_t *halo = W.halo + seg * (long long)W.H;
-    const long long h0 = s - W.H;  // first halo position (a multiple of 16)
-    // 16 symbols per load and 16 lengths per store: s, H and the buffers are
-    // 16-byte aligned; a record start inside the halo only shifts where the
-    // pass begins within its 16-symbol block
-    for (long long j0 = (a > h0 ? a : h0) & ~15ll; j0 < e; j0 += 16) {
-        const uint4 sv = *reinterpret_cast<const uint4 *>(W.sym + j0);
-        const unsigned long long s_lo = ((unsigned long long)sv.y << 32) | sv.x;
-        const unsigned long long s_hi = ((unsigned long long)sv.w << 32) | sv.z;
-        unsigned long long l_lo = 0, l_hi = 0;
-        const int q0 = (j0 < a) ? (int)(a - j0) : 0;
-        const int q1 = (e - j0 < 16) ? (int)(e - j0) : 16;
-#pragma unroll 1
-        for (int q = q0; q < q1; ++q) {
-            const long long j = j0 + q;
-            while (j == next_b) {
-                wd = 0;
-                reg = 0;
-                ++r;
-                next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
-            }
-            const unsigned c = (unsigned)((q < 8 ? s_lo >> (8 * q) : s_hi >> (8 * (q - 8))) & 0xFFu);
-            unsigned L, t;
-            if (c >= 4) {
-                L = 1;
-                t = (unsigned)T.V;
-                wd = 0;
-                reg = 0;
-                if (j < s) exact = true;  // a word starts after it, before the segment
-            } else {
-                reg = (reg << 2) | c;
-                if (wd < 63) ++wd;
-                const unsigned pk = dp_step(T, reg, wd, j, ring);
-                L = pk >> 16;
-                t = pk & 0xFFFFu;
-            }
-            ring[j & 31] = (unsigned short)t;
-            if (q < 8) l_lo |= (unsigned long long)L << (8 * q);
-            else l_hi |= (unsigned long long)L << (8 * (q - 8));
-        }
-        const uint4 lv = make_uint4((unsigned)l_lo, (unsigned)(l_lo >> 32), (unsigned)l_hi,
-                                    (unsigned)(l_hi >> 32));
-        if (j0 >= s) *reinterpret_cast<uint4 *>(W.len + j0) = lv;
-        else if (W.H > 0) *reinterpret_cast<uint4 *>(halo + (j0 - h0)) = lv;
-    }
-    if (a > h0) {
-        // halo positions before the pass began hold 0 (no value)
-        for (long long x = h0; x < (a & ~15ll); ++x) halo[x - h0] = 0;
-    }
+    DpPass<R> P;
+    P.ring = ring_t + threadIdx.x;
+    dp_reset(T, P);
+    seg_pass<R>(T, W, seg, s, e, a, r, P, ring_f + threadIdx.x, exact);
     W.flags[seg] = exact ? 1 : 0;
 }
 
 // A segment whose pass did not start exactly is correct if its halo agrees
-// with its left neighbour's values over lmax consecutive symbols.
-__global__ void bpe_sync_kernel(BpeTables G, BpeWork W) {
+// with its left neighbour's values over lmax consecutive symbols; the others
+// are marked for repair.
+__global__ void bpe_sync_kernel(BpeTables T, BpeWork W) {
     const long long seg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (seg >= W.max_seg) return;
     if (dev_failed(W.status)) return;
     const long long n_sym = W.tot[0];
     const long long s = seg * W.S;
-    if (seg == 0 || s >= n_sym || W.flags[seg]) return;
-    const uint8_t *halo = W.halo + seg * (long long)W.H;
-    int run = 0;
-    for (long long j = s - W.H; j < s; ++j) {
-        const uint8_t v = halo[j - (s - W.H)];
-        run = (v != 0 && v == W.len[j]) ? run + 1 : 0;
-        if (run >= G.lmax) return;
+    uint8_t bad = 0;
+    if (seg > 0 && s < n_sym && !W.flags[seg]) {
+        const unsigned short *halo = W.halo + seg * (long long)W.H;
+        int run = 0;
+        bad = 1;
+        for (long long j = s - W.H; j < s; ++j) {
+            const unsigned short v = halo[j - (s - W.H)];
+            run = (v != kNone16 && v == W.tok[j]) ? run + 1 : 0;
+            if (run >= T.lmax) {
+                bad = 0;
+                break;
+            }
+        }
+        if (bad) atomicAdd(W.n_bad, 1);
     }
-    const int q = atomicAdd(W.bad, 1);
-    W.bad[1 + q] = (int)seg;
+    W.bad[seg] = bad;
 }
 
-// Exact recomputation, in order, of the segments that did not sync (rare):
-// rebuild the DP state at the segment start from the (correct) values to its
-// left, recompute the whole segment, then re-check the next one against the
-// new values and continue into it if it no longer syncs.
-__global__ void bpe_repair_kernel(BpeTables T, BpeWork W) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (dev_failed(W.status)) return;
-    const int nbad = W.bad[0];
-    if (nbad == 0) return;
-    int *list = W.bad + 1;
-    for (int i = 1; i < nbad; ++i) {  // insertion sort (short list)
-        const int v = list[i];
-        int k = i - 1;
-        while (k >= 0 && list[k] > v) {
-            list[k + 1] = list[k];
-            --k;
-        }
-        list[k + 1] = v;
+// The segments to repair, in order, each with its region: the last exact
+// segment at or before it.  Regions are independent (no chain of
+// dependencies crosses an exact segment), so each region's segments are
+// repaired by one thread, regions in parallel.  A pair scan over the
+// segments (count of marked segments, last exact segment) gives both.
+struct CntMax {
+    long long c, m;
+};
+__device__ __forceinline__ CntMax cm_combine(CntMax a, CntMax b) {
+    return CntMax{a.c + b.c, a.m > b.m ? a.m : b.m};
+}
+__device__ __forceinline__ CntMax cm_item(const BpeWork &W, long long i) {
+    if (i >= W.max_seg) return CntMax{0, -1};
+    return CntMax{W.bad[i], (i == 0 || W.flags[i]) ? i : -1};
+}
+// exclusive block scan of CntMax (identity {0, -1}); *total gets the block's reduction
+__device__ __forceinline__ CntMax block_excl_scan_cm(CntMax v, CntMax *total) {
+    __shared__ long long wc[kScanThreads / 32], wm[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    CntMax x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        CntMax y{__shfl_up_sync(0xffffffffu, x.c, o), __shfl_up_sync(0xffffffffu, x.m, o)};
+        if (lane >= o) x = cm_combine(y, x);
     }
+    if (lane == 31) {
+        wc[warp] = x.c;
+        wm[warp] = x.m;
+    }
+    __syncthreads();
+    CntMax off{0, -1}, all{0, -1};
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        const CntMax ww{wc[w], wm[w]};
+        if (w < warp) off = cm_combine(off, ww);
+        all = cm_combine(all, ww);
+    }
+    __syncthreads();
+    *total = all;
+    // exclusive within the warp: shift the inclusive value up by one lane
+    CntMax ex{__shfl_up_sync(0xffffffffu, x.c, 1), __shfl_up_sync(0xffffffffu, x.m, 1)};
+    if (lane == 0) ex = CntMax{0, -1};
+    return cm_combine(off, ex);
+}
+
+__global__ void __launch_bounds__(kScanThreads) bpe_rep_reduce(BpeWork W) {
+    if (*W.n_bad == 0) return;
+    const long long i0 = (blockIdx.x * (long long)kScanThreads + threadIdx.x) * kScanItems;
+    CntMax v{0, -1};
+    for (int q = 0; q < kScanItems; ++q) v = cm_combine(v, cm_item(W, i0 + q));
+    CntMax total;
+    block_excl_scan_cm(v, &total);
+    if (threadIdx.x == 0) {
+        W.rep_sums[2 * blockIdx.x] = total.c;
+        W.rep_sums[2 * blockIdx.x + 1] = total.m;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) bpe_rep_top(BpeWork W, long long n_blocks) {
+    if (*W.n_bad == 0) return;
+    CntMax carry{0, -1};
+    for (long long b0 = 0; b0 < n_blocks; b0 += kScanThreads) {
+        const long long b = b0 + threadIdx.x;
+        const CntMax v = (b < n_blocks) ? CntMax{W.rep_sums[2 * b], W.rep_sums[2 * b + 1]}
+                                        : CntMax{0, -1};
+        CntMax total;
+        const CntMax ex = block_excl_scan_cm(v, &total);
+        if (b < n_blocks) {
+            const CntMax pre = cm_combine(carry, ex);
+            W.rep_sums[2 * b] = pre.c;
+            W.rep_sums[2 * b + 1] = pre.m;
+        }
+        carry = cm_combine(carry, total);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) bpe_rep_down(BpeWork W) {
+    if (*W.n_bad == 0) return;
+    const long long i0 = (blockIdx.x * (long long)kScanThreads + threadIdx.x) * kScanItems;
+    CntMax v{0, -1};
+    for (int q = 0; q < kScanItems; ++q) v = cm_combine(v, cm_item(W, i0 + q));
+    CntMax total;
+    CntMax run = cm_combine(CntMax{W.rep_sums[2 * blockIdx.x], W.rep_sums[2 * blockIdx.x + 1]},
+                            block_excl_scan_cm(v, &total));
+    for (int q = 0; q < kScanItems; ++q) {
+        const CntMax it = cm_item(W, i0 + q);
+        run = cm_combine(run, CntMax{0, it.m});  // the region includes the item itself
+        if (it.c) {
+            W.rep_list[run.c] = (int)(i0 + q);
+            W.rep_region[run.c] = (int)run.m;
+        }
+        run.c += it.c;
+    }
+}
+
+// Exact recomputation of the marked segments.  One thread per region (the
+// thread of the region's first listed segment) takes its segments in order:
+// it rebuilds the pass state at the segment start from the (correct) values
+// to its left, recomputes the segment (values and map), then re-checks the
+// next segment against the new values and continues into it if it no longer
+// agrees, up to the next exact segment.  Work per thread is bounded by its
+// region; a region is one run of dependent segments.
+template <int R>
+__global__ void __launch_bounds__(kDpThreads) bpe_repair_kernel(BpeTables T, BpeWork W) {
+    __shared__ unsigned short ring_t[R * kDpThreads];
+    __shared__ unsigned ring_f[R * kDpThreads];
+    const int nbad = *W.n_bad;
+    const long long i = blockIdx.x * (long long)kDpThreads + threadIdx.x;
+    if (nbad == 0 || i >= nbad) return;
+    if (dev_failed(W.status)) return;
+    const int region = W.rep_region[i];
+    if (i > 0 && W.rep_region[i - 1] == region) return;  // not the region's first
     const long long n_sym = W.tot[0], nb = W.tot[1] + 1;
+    DpPass<R> P;
+    P.ring = ring_t + threadIdx.x;
+    unsigned *ringf = ring_f + threadIdx.x;
     long long done_until = 0;  // symbols below this are final
-    for (int i = 0; i < nbad; ++i) {
-        long long seg = list[i];
+    for (long long k = i; k < nbad && W.rep_region[k] == region; ++k) {
+        long long seg = W.rep_list[k];
         long long s = seg * W.S;
         if (s < done_until) continue;
-        // DP state at s from the values to its left
-        unsigned short ring[32];
-        unsigned long long reg = 0;
-        int wd = 0;
-        long long r = rec_upper(W.rec_off, nb, s);
-        while (r + 1 < nb && W.rec_off[r + 1] <= s) ++r;
-        const long long ws = W.rec_off[r];
-        long long x = s - 1;
-        while (x >= ws && x >= s - 63 && W.sym[x] < 4) --x;
-        // symbols (x, s) are the word so far (capped at 63)
-        for (long long y = x + 1; y < s; ++y) {
-            reg = (reg << 2) | W.sym[y];
-            ++wd;
-        }
-        for (long long y = (s - 32 > 0 ? s - 32 : 0); y < s; ++y)
-            ring[y & 31] = (W.sym[y] >= 4) ? (unsigned short)T.V
-                                           : (unsigned short)token_at(T, W.sym, y, W.len[y]);
-        long long next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
         while (true) {
-            const long long e = (s + W.S < n_sym) ? s + W.S : n_sym;
-            for (long long j = s; j < e; ++j) {
-                while (j == next_b) {
-                    wd = 0;
-                    reg = 0;
-                    ++r;
-                    next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
-                }
-                const unsigned c = W.sym[j];
-                unsigned L, t;
-                if (c >= 4) {
-                    L = 1;
-                    t = (unsigned)T.V;
-                    wd = 0;
-                    reg = 0;
-                } else {
-                    reg = (reg << 2) | c;
-                    if (wd < 63) ++wd;
-                    const unsigned pk = dp_step(T, reg, wd, j, ring);
-                    L = pk >> 16;
-                    t = pk & 0xFFFFu;
-                }
-                ring[j & 31] = (unsigned short)t;
-                W.len[j] = (uint8_t)L;
+            // pass state at s from the values to its left
+            long long r = rec_upper(W.rec_off, nb, s);
+            while (r + 1 < nb && W.rec_off[r + 1] <= s) ++r;
+            const long long ws = W.rec_off[r];
+            long long x = s - 1;
+            while (x >= ws && x >= s - 63 && W.sym[x] < 4) --x;
+            // symbols (x, s) are the word so far (capped at 63)
+            dp_reset(T, P);
+            const long long from = (s - (x + 1) > T.lmax) ? s - T.lmax : x + 1;
+            for (long long y = from; y < s; ++y) {
+                P.state = node_next(P.nd, W.sym[y]);
+                P.nd = __ldg(T.node + P.state);
             }
+            P.wd = (int)(s - (x + 1));
+            for (long long y = (s - R > 0 ? s - R : 0); y < s; ++y)
+                P.ring[(y & (R - 1)) * kDpThreads] = W.tok[y];
+            const long long e = (s + W.S < n_sym) ? s + W.S : n_sym;
+            bool exact = true;
+            seg_pass<R>(T, W, seg, s, e, s, r, P, ringf, exact);
             done_until = e;
             ++seg;
             s = seg * W.S;
             if (s >= n_sym || W.flags[seg]) break;
             // does the next segment's fresh pass agree with the new values?
-            const uint8_t *halo = W.halo + seg * (long long)W.H;
+            const unsigned short *halo = W.halo + seg * (long long)W.H;
             int run = 0;
             bool ok = false;
             for (long long j = s - W.H; j < s && !ok; ++j) {
-                const uint8_t v = halo[j - (s - W.H)];
-                run = (v != 0 && v == W.len[j]) ? run + 1 : 0;
+                const unsigned short v = halo[j - (s - W.H)];
+                run = (v != kNone16 && v == W.tok[j]) ? run + 1 : 0;
                 ok = run >= T.lmax;
             }
             if (ok) break;
         }
     }
-}
-
-// Warp per segment, lane u = entry offset: walk the chain from symbol
-// end - 1 - u down past the segment start.
-__global__ void bpe_maps_kernel(BpeTables G, BpeWork W) {
-    const long long seg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const int u = threadIdx.x & 31;
-    if (dev_failed(W.status)) return;
-    const long long n_sym = W.tot[0];
-    const long long s = seg * W.S;
-    if (s >= n_sym) return;
-    const long long e_end = (s + W.S < n_sym) ? s + W.S : n_sym;
-    long long e = e_end - 1 - u;
-    unsigned cnt = 0;
-    if (u < G.lmax) {
-        while (e >= s) {
-            e -= W.len[e];
-            ++cnt;
-        }
-    }
-    const unsigned v = (unsigned)(s - 1 - e);
-    W.map_v[seg * 32 + u] = (uint8_t)v;
-    W.map_c[seg * 32 + u] = (unsigned short)cnt;
-    const unsigned mine = (u < G.lmax) ? v : 0xFFFFFFFFu;
-    const unsigned first = __shfl_sync(0xffffffffu, v, 0);
-    const bool same = __all_sync(0xffffffffu, mine == 0xFFFFFFFFu || mine == first);
-    if (u == 0) W.const_v[seg] = same ? (uint8_t)first : (uint8_t)0xFF;
 }
 
 // The true entry of every segment: the exit of its right neighbour, found
@@ -526,7 +608,6 @@ __global__ void bpe_entries_kernel(BpeTables G, BpeWork W) {
     W.entry[seg] = (uint8_t)u;
     W.count[seg] = W.map_c[seg * 32 + u];
 }
-
 // Exclusive scan of the per-segment counts: block sums, one block over the
 // block sums, then per-block rescan.
 __device__ __forceinline__ long long block_excl_scan(long long v, long long *total) {
@@ -592,73 +673,29 @@ __global__ void __launch_bounds__(kScanThreads) bpe_scan_down(BpeWork W) {
         }
 }
 
-// Thread per segment walks its chain (from its entry, backwards) and marks
-// the token ends in a bitmap, one bit per symbol, in global memory; then each
-// warp emits its 32 segments one after another with lane w taking bitmap word
-// w (symbols 32w..32w+31), so the warp writes one contiguous run of ids.
-__global__ void __launch_bounds__(256) bpe_emit_kernel(BpeTables G, bool smem, BpeWork W) {
-    const BpeTables T = stage_tables(G, smem);
-    const int lane = threadIdx.x & 31;
+// Thread per segment: walk its chain from the true entry backwards and write
+// each token's id at its place, last first (the segment's ids are one
+// contiguous run of the output).
+__global__ void __launch_bounds__(256) bpe_emit_kernel(BpeTables T, BpeWork W) {
     const long long seg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (dev_failed(W.status)) return;
     const long long n_sym = W.tot[0];
     const long long n_seg = (n_sym + W.S - 1) / W.S;
-    const int words = (W.S + 31) / 32;
-    if (seg < n_seg) {
-        const long long s = seg * W.S;
-        const long long e_end = (s + W.S < n_sym) ? s + W.S : n_sym;
-        unsigned *bits = W.bits + seg * words;
-        long long e = e_end - 1 - W.entry[seg];
-        int cw = words - 1;
-        unsigned acc = 0;
-        while (e >= s) {
-            const int x = (int)(e - s);
-            while ((x >> 5) < cw) {
-                bits[cw--] = acc;
-                acc = 0;
-            }
-            acc |= 1u << (x & 31);
-            e -= W.len[e];
-        }
-        for (; cw >= 0; --cw) {
-            bits[cw] = acc;
-            acc = 0;
-        }
-    }
-    __syncwarp();
-    const long long seg0 = seg - lane;
-    for (int i = 0; i < 32; ++i) {
-        const long long sg = seg0 + i;
-        if (sg >= n_seg) break;
-        const long long s = sg * W.S;
-        const unsigned *bits = W.bits + sg * words;
-        long long out = W.base[sg];
-        for (int w0 = 0; w0 < words; w0 += 32) {
-            const int w = w0 + lane;
-            const unsigned wb = (w < words) ? bits[w] : 0u;
-            const unsigned c = __popc(wb);
-            unsigned x = c;  // inclusive scan of the counts over the warp
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            long long pos = out + (x - c);
-            unsigned m = wb;
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const long long j = s + 32ll * w + b;
-                const unsigned id = (W.sym[j] >= 4) ? (unsigned)T.V : token_at(T, W.sym, j, W.len[j]);
-                if (pos >= 0 && pos < W.out_cap) W.out[pos] = (int)id;
-                ++pos;
-            }
-            out += __shfl_sync(0xffffffffu, x, 31);
-        }
+    if (seg >= n_seg) return;
+    const long long s = seg * W.S;
+    const long long e_end = (s + W.S < n_sym) ? s + W.S : n_sym;
+    long long e = e_end - 1 - W.entry[seg];
+    long long pos = W.base[seg] + W.count[seg];
+    while (e >= s) {
+        const unsigned t = W.tok[e];
+        --pos;
+        if (pos >= 0 && pos < W.out_cap) W.out[pos] = (int)t;
+        e -= __ldg(T.tok_len + t);
     }
 }
 
 // Record starts (in symbols) -> record starts (in ids), in place.
-__global__ void bpe_offsets_kernel(BpeWork W) {
+__global__ void bpe_offsets_kernel(BpeTables T, BpeWork W) {
     if (dev_failed(W.status)) return;
     const long long n_sym = W.tot[0], nb = W.tot[1] + 1;
     const long long total = W.base[W.max_seg];
@@ -673,7 +710,7 @@ __global__ void bpe_offsets_kernel(BpeWork W) {
             off = W.base[seg];
             long long e = rho - 1, c = 0;
             while (e >= s) {
-                e -= W.len[e];
+                e -= __ldg(T.tok_len + W.tok[e]);
                 ++c;
             }
             off += c;
@@ -687,23 +724,21 @@ __global__ void bpe_offsets_kernel(BpeWork W) {
 // ======================================================================= host
 
 struct BpeState {
-    int M = 0, V = 0, lmax = 1, n_nodes = 1;  // n_nodes: deep trie nodes
-    uint2 *d_child = nullptr;
-    unsigned short *d_tok = nullptr;
-    unsigned short *d_node6 = nullptr;
-    unsigned short *d_kmtok = nullptr;
+    int M = 0, V = 0, lmax = 1, n_nodes = 1;
+    uint4 *d_node = nullptr;
+    uint8_t *d_tok_len = nullptr;
     unsigned *d_compat = nullptr;
     int S = 1024, H = 64;
 
     // workspace
     long long cap_bytes = -1;
-    uint8_t *d_sym = nullptr, *d_len = nullptr, *d_halo = nullptr, *d_flags = nullptr;
+    uint8_t *d_sym = nullptr, *d_flags = nullptr, *d_bad = nullptr;
+    unsigned short *d_tok = nullptr, *d_halo = nullptr;
     uint8_t *d_map_v = nullptr, *d_const = nullptr, *d_entry = nullptr;
-    unsigned short *d_map_c = nullptr;
+    unsigned *d_map_c = nullptr;
     unsigned *d_count = nullptr;
-    long long *d_base = nullptr, *d_bsums = nullptr, *d_tot = nullptr;
-    int *d_bad = nullptr;
-    unsigned *d_bits = nullptr;
+    long long *d_base = nullptr, *d_bsums = nullptr, *d_rsums = nullptr, *d_tot = nullptr;
+    int *d_nbad = nullptr, *d_rep_list = nullptr, *d_rep_region = nullptr;
     long long seg_cap = 0;
     int ws_S = 0, ws_H = 0;
 };
@@ -711,26 +746,16 @@ struct BpeState {
 namespace {
 
 void free_workspace(BpeState *b) {
-    cudaFree(b->d_sym);
-    cudaFree(b->d_len);
-    cudaFree(b->d_halo);
-    cudaFree(b->d_flags);
-    cudaFree(b->d_map_v);
-    cudaFree(b->d_const);
-    cudaFree(b->d_entry);
-    cudaFree(b->d_map_c);
-    cudaFree(b->d_count);
-    cudaFree(b->d_base);
-    cudaFree(b->d_bsums);
-    cudaFree(b->d_tot);
-    cudaFree(b->d_bad);
-    cudaFree(b->d_bits);
-    b->d_bits = nullptr;
-    b->d_sym = b->d_len = b->d_halo = b->d_flags = b->d_map_v = b->d_const = b->d_entry = nullptr;
-    b->d_map_c = nullptr;
-    b->d_count = nullptr;
-    b->d_base = b->d_bsums = b->d_tot = nullptr;
-    b->d_bad = nullptr;
+    void *p[] = {b->d_sym, b->d_flags, b->d_bad, b->d_tok, b->d_halo, b->d_map_v, b->d_const,
+                 b->d_entry, b->d_map_c, b->d_count, b->d_base, b->d_bsums, b->d_rsums, b->d_tot,
+                 b->d_nbad, b->d_rep_list, b->d_rep_region};
+    for (void *q : p) cudaFree(q);
+    b->d_sym = b->d_flags = b->d_bad = nullptr;
+    b->d_tok = b->d_halo = nullptr;
+    b->d_map_v = b->d_const = b->d_entry = nullptr;
+    b->d_map_c = b->d_count = nullptr;
+    b->d_base = b->d_bsums = b->d_rsums = b->d_tot = nullptr;
+    b->d_nbad = b->d_rep_list = b->d_rep_region = nullptr;
     b->cap_bytes = -1;
     b->seg_cap = 0;
 }
@@ -753,16 +778,30 @@ dnatok_status ensure_bpe_workspace(dnatok_handle *h, long long n_bytes, cudaStre
     const long long cap = n_bytes + n_bytes / 8 + 4096;
     const long long nseg = (cap + b->S - 1) / b->S + 1;
     const long long nblk = scan_blocks(nseg) + 1;
-    size_t sz[] = {(size_t)cap + 16, (size_t)cap + 16, (size_t)(nseg * b->H + 16), (size_t)nseg,
-                   (size_t)nseg * 32, (size_t)nseg, (size_t)nseg, (size_t)nseg * 32 * 2,
-                   (size_t)nseg * 4, (size_t)(nseg + 1) * 8, (size_t)nblk * 8, 16,
-                   (size_t)(nseg + 1) * 4, (size_t)nseg * 4 * ((b->S + 31) / 32) + 16};
-    void **ptr[] = {(void **)&b->d_sym,   (void **)&b->d_len,   (void **)&b->d_halo,
-                    (void **)&b->d_flags, (void **)&b->d_map_v, (void **)&b->d_const,
-                    (void **)&b->d_entry, (void **)&b->d_map_c, (void **)&b->d_count,
-                    (void **)&b->d_base,  (void **)&b->d_bsums, (void **)&b->d_tot,
-                    (void **)&b->d_bad,   (void **)&b->d_bits};
-    for (int i = 0; i < 14; ++i) {
+    size_t sz[] = {(size_t)cap + 16,                  // sym
+                   (size_t)nseg,                      // flags
+                   (size_t)nseg,                      // bad
+                   2 * ((size_t)cap + 16),            // tok
+                   2 * ((size_t)nseg * b->H + 16),    // halo
+                   (size_t)nseg * 32,                 // map_v
+                   (size_t)nseg,                      // const
+                   (size_t)nseg,                      // entry
+                   (size_t)nseg * 32 * 4,             // map_c
+                   (size_t)nseg * 4,                  // count
+                   (size_t)(nseg + 1) * 8,            // base
+                   (size_t)nblk * 8,                  // block sums
+                   (size_t)nblk * 16,                 // repair listing block sums
+                   16,                                // tot
+                   16,                                // n_bad
+                   (size_t)nseg * 4,                  // repair list
+                   (size_t)nseg * 4};                 // repair regions
+    void **ptr[] = {(void **)&b->d_sym,     (void **)&b->d_flags,   (void **)&b->d_bad,
+                    (void **)&b->d_tok,     (void **)&b->d_halo,    (void **)&b->d_map_v,
+                    (void **)&b->d_const,   (void **)&b->d_entry,   (void **)&b->d_map_c,
+                    (void **)&b->d_count,   (void **)&b->d_base,    (void **)&b->d_bsums,
+                    (void **)&b->d_rsums,   (void **)&b->d_tot,     (void **)&b->d_nbad,
+                    (void **)&b->d_rep_list, (void **)&b->d_rep_region};
+    for (int i = 0; i < 17; ++i) {
         e = cudaMalloc(ptr[i], sz[i]);
         if (e != cudaSuccess) {
             free_workspace(b);
@@ -774,11 +813,6 @@ dnatok_status ensure_bpe_workspace(dnatok_handle *h, long long n_bytes, cudaStre
     b->ws_S = b->S;
     b->ws_H = b->H;
     return DNATOK_OK;
-}
-
-size_t trie_smem_bytes(const BpeState *b) {
-    return (size_t)b->n_nodes * (sizeof(uint2) + sizeof(unsigned short)) +
-           sizeof(unsigned short) * (4096 + kKmTotal) + 16;
 }
 
 }  // namespace
@@ -884,82 +918,84 @@ dnatok_status bpe_create(dnatok_handle *h, const int32_t *merges, int32_t n_merg
             cleanup();
             return fail(h, DNATOK_ERR_TABLE, "BPE tokens longer than 32 bases are not supported");
         }
-    // trie over reversed strings of self-encoding tokens
+    // Aho-Corasick automaton over the strings of the self-encoding tokens:
+    // trie (node 0 = root), failure links by breadth-first order, complete
+    // transitions, and for every node the list of its candidates -- the
+    // self-encoding tokens that are suffixes of its string, longest first.
     std::vector<unsigned> ch(4, 0);
-    std::vector<unsigned short> tk(1, (unsigned short)kNoTok);
+    std::vector<int> term(1, -1), depth(1, 0);
     int lmax = 1;
     for (int t = 0; t < V; ++t) {
         if (!self[t]) continue;
         lmax = std::max(lmax, len[t]);
         unsigned node = 0;
         for (int d = 0; d < len[t]; ++d) {
-            const unsigned c = str[t][len[t] - 1 - d];
+            const unsigned c = str[t][d];
             if (!ch[node * 4 + c]) {
-                ch[node * 4 + c] = (unsigned)tk.size();
-                tk.push_back((unsigned short)kNoTok);
+                ch[node * 4 + c] = (unsigned)term.size();
+                term.push_back(-1);
+                depth.push_back(depth[node] + 1);
                 ch.insert(ch.end(), {0, 0, 0, 0});
             }
             node = ch[node * 4 + c];
         }
-        tk[node] = (unsigned short)t;
+        term[node] = t;
     }
-    if (tk.size() > 65535) {
+    const size_t N = term.size();
+    if (N >= 0xFFFF) {
         cleanup();
-        return fail(h, DNATOK_ERR_TABLE, "BPE token trie exceeds 65535 nodes");
+        return fail(h, DNATOK_ERR_TABLE, "BPE token automaton exceeds 65534 nodes");
     }
-    // Split the lookup: tokens of 1..5 bases in direct tables by their code
-    // (last base in the low bits); the 6-base suffix indexes node6, which
-    // points into the part of the trie at depth >= 6 (renumbered from 1).
-    std::vector<unsigned short> kmtok(kKmTotal, (unsigned short)kNoTok);
-    std::vector<unsigned short> node6(4096, 0);
-    std::vector<int> depth(tk.size(), 0), deep_id(tk.size(), 0);
-    std::vector<unsigned> code(tk.size(), 0);
-    std::vector<unsigned> order(1, 0);  // BFS over the full trie
-    int n_deep = 1;                     // deep index 0 = none
+    std::vector<unsigned> fail_(N, 0), delta(N * 4, 0), order;
+    order.reserve(N);
+    order.push_back(0);
     for (size_t qi = 0; qi < order.size(); ++qi) {
         const unsigned u = order[qi];
-        if (depth[u] >= 6) deep_id[u] = n_deep++;
-        if (depth[u] >= 1 && depth[u] <= 5 && tk[u] != kNoTok) kmtok[km_off(depth[u]) + code[u]] = tk[u];
         for (unsigned c = 0; c < 4; ++c) {
             const unsigned v = ch[u * 4 + c];
-            if (!v) continue;
-            depth[v] = depth[u] + 1;
-            // reversed path: the d-th symbol back from the end lands at bits 2(d-1)
-            code[v] = depth[v] <= 6 ? code[u] | (c << (2 * (depth[v] - 1))) : code[u];
-            order.push_back(v);
+            if (v) {
+                fail_[v] = (u == 0) ? 0 : delta[fail_[u] * 4 + c];
+                delta[u * 4 + c] = v;
+                order.push_back(v);
+            } else {
+                delta[u * 4 + c] = (u == 0) ? 0 : delta[fail_[u] * 4 + c];
+            }
         }
     }
-    std::vector<uint2> child(n_deep, make_uint2(0, 0));
-    std::vector<unsigned short> dtok(n_deep, (unsigned short)kNoTok);
-    for (size_t u = 0; u < tk.size(); ++u) {
-        if (depth[u] < 6) continue;
-        const int id = deep_id[u];
-        if (depth[u] == 6) node6[code[u]] = (unsigned short)id;
-        dtok[id] = tk[u];
-        unsigned cc[4];
-        for (int c = 0; c < 4; ++c) cc[c] = ch[u * 4 + c] ? (unsigned)deep_id[ch[u * 4 + c]] : 0u;
-        child[id].x = cc[0] | (cc[1] << 16);
-        child[id].y = cc[2] | (cc[3] << 16);
+    // dict[u]: the nearest proper suffix node that is a token (or none)
+    std::vector<unsigned> dict(N, kNone16);
+    for (size_t qi = 1; qi < order.size(); ++qi) {
+        const unsigned u = order[qi], f = fail_[u];
+        dict[u] = (f != 0 && term[f] >= 0) ? f : dict[f];
     }
+    std::vector<uint4> rec(N);
+    for (size_t u = 0; u < N; ++u) {
+        const unsigned c1 = (term[u] >= 0) ? (unsigned)u : dict[u];
+        const unsigned c2 = (c1 != kNone16) ? dict[c1] : kNone16;
+        const unsigned c3 = (c2 != kNone16) ? dict[c2] : kNone16;
+        const unsigned t1 = c1 != kNone16 ? (unsigned)term[c1] : kNone16;
+        const unsigned t2 = c2 != kNone16 ? (unsigned)term[c2] : kNone16;
+        const unsigned l1 = c1 != kNone16 ? (unsigned)depth[c1] : 0u;
+        const unsigned l2 = c2 != kNone16 ? (unsigned)depth[c2] : 0u;
+        rec[u].x = delta[u * 4 + 0] | (delta[u * 4 + 1] << 16);
+        rec[u].y = delta[u * 4 + 2] | (delta[u * 4 + 3] << 16);
+        rec[u].z = t1 | (t2 << 16);
+        rec[u].w = l1 | (l2 << 6) | (c3 << 16);
+    }
+    std::vector<uint8_t> tl(V + 1);
+    for (int t = 0; t < V; ++t) tl[t] = (uint8_t)std::min(len[t], 255);
+    tl[V] = 1;  // N_ID
     b->lmax = lmax;
-    b->n_nodes = n_deep;
+    b->n_nodes = (int)N;
     b->H = std::max(64, ((4 * lmax + 15) / 16) * 16);
     const unsigned long long nbits = (unsigned long long)V * V;
     const size_t cwords = (size_t)((nbits + 31) / 32) + 2;
-    e = cudaMalloc(&b->d_child, sizeof(uint2) * n_deep);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tok, sizeof(unsigned short) * n_deep);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_node6, sizeof(unsigned short) * 4096);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_kmtok, sizeof(unsigned short) * kKmTotal);
+    e = cudaMalloc(&b->d_node, sizeof(uint4) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tok_len, V + 1);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_compat, cwords * 4);
     if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_child, child.data(), sizeof(uint2) * n_deep, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_tok, dtok.data(), sizeof(unsigned short) * n_deep, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_node6, node6.data(), sizeof(unsigned short) * 4096, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_kmtok, kmtok.data(), sizeof(unsigned short) * kKmTotal,
-                       cudaMemcpyHostToDevice);
+        e = cudaMemcpy(b->d_node, rec.data(), sizeof(uint4) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tok_len, tl.data(), V + 1, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_compat, 0, cwords * 4);
     if (e == cudaSuccess) {
         const long long threads = (long long)V * ((V + 31) / 32);
@@ -977,10 +1013,8 @@ void bpe_destroy(dnatok_handle *h) {
     BpeState *b = h->bpe;
     if (!b) return;
     free_workspace(b);
-    cudaFree(b->d_child);
-    cudaFree(b->d_tok);
-    cudaFree(b->d_node6);
-    cudaFree(b->d_kmtok);
+    cudaFree(b->d_node);
+    cudaFree(b->d_tok_len);
     cudaFree(b->d_compat);
     delete b;
     h->bpe = nullptr;
@@ -1001,27 +1035,27 @@ dnatok_status bpe_set_launch(dnatok_handle *h, int seg_symbols, int halo) {
     return DNATOK_OK;
 }
 
+dnatok_status bpe_get_launch(const dnatok_handle *h, int *seg_symbols, int *halo) {
+    if (!h->bpe) return DNATOK_ERR_STATE;
+    *seg_symbols = h->bpe->S;
+    *halo = h->bpe->H;
+    return DNATOK_OK;
+}
+
 dnatok_status bpe_stats(dnatok_handle *h, long long *out, cudaStream_t s) {
     BpeState *b = h->bpe;
     if (!b) return fail(h, DNATOK_ERR_STATE, "not a BPE handle");
     out[0] = out[1] = out[2] = 0;
-    if (!b->d_tot || !b->d_bad) return DNATOK_OK;  // nothing encoded yet
+    if (!b->d_tot || !b->d_nbad) return DNATOK_OK;  // nothing encoded yet
     long long tot[2] = {0, 0};
     int bad = 0;
     cudaError_t e = cudaMemcpyAsync(tot, b->d_tot, sizeof(tot), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, b->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, b->d_nbad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(h, e, "BPE statistics read");
     out[0] = tot[0];
     out[1] = (tot[0] + b->ws_S - 1) / (b->ws_S > 0 ? b->ws_S : 1);
     out[2] = bad;
-    return DNATOK_OK;
-}
-
-dnatok_status bpe_get_launch(const dnatok_handle *h, int *seg_symbols, int *halo) {
-    if (!h->bpe) return DNATOK_ERR_STATE;
-    *seg_symbols = h->bpe->S;
-    *halo = h->bpe->H;
     return DNATOK_OK;
 }
 
@@ -1040,16 +1074,17 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
                          reinterpret_cast<long long *>(id_offsets_d), offsets_capacity, b->d_tot,
                          nullptr, nullptr, raw ? 0 : 1, raw ? 0 : 1, s);
     if (st != DNATOK_OK) return st;
-    cudaError_t e = cudaMemsetAsync(b->d_bad, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(b->d_nbad, 0, sizeof(int), s);
     if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync");
 
-    BpeTables T{b->V, b->lmax, b->n_nodes, b->d_kmtok, b->d_node6, b->d_child, b->d_tok, b->d_compat};
+    BpeTables T{b->V, b->lmax, b->d_node, b->d_tok_len, b->d_compat};
     BpeWork W;
     std::memset(&W, 0, sizeof(W));
     W.sym = b->d_sym;
-    W.len = b->d_len;
+    W.tok = b->d_tok;
     W.halo = b->d_halo;
     W.flags = b->d_flags;
+    W.bad = b->d_bad;
     W.map_v = b->d_map_v;
     W.map_c = b->d_map_c;
     W.const_v = b->d_const;
@@ -1057,8 +1092,10 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     W.entry = b->d_entry;
     W.base = b->d_base;
     W.block_sums = b->d_bsums;
-    W.bad = b->d_bad;
-    W.bits = b->d_bits;
+    W.rep_sums = b->d_rsums;
+    W.n_bad = b->d_nbad;
+    W.rep_list = b->d_rep_list;
+    W.rep_region = b->d_rep_region;
     W.tot = b->d_tot;
     W.rec_off = reinterpret_cast<long long *>(id_offsets_d);
     W.offsets_cap = offsets_capacity;
@@ -1071,35 +1108,31 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     W.max_seg = (n_bytes + b->S - 1) / b->S;
     if (W.max_seg == 0) W.max_seg = 1;
 
-    const size_t smem = trie_smem_bytes(b);
-    const bool use_smem = smem <= 96 * 1024 + 16;
-    const size_t dyn = use_smem ? smem : 0;
-    static bool attr_done = false;  // once per process: allow the largest trie we stage
-    if (!attr_done) {
-        cudaFuncSetAttribute(bpe_dp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 16);
-        cudaFuncSetAttribute(bpe_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 16);
-        attr_done = true;
-    }
+    const unsigned gdp = (unsigned)((W.max_seg + kDpThreads - 1) / kDpThreads);
     const unsigned g128 = (unsigned)((W.max_seg + 127) / 128);
     const unsigned g256 = (unsigned)((W.max_seg + 255) / 256);
-    bpe_dp_kernel<<<g256, 256, dyn, s>>>(T, use_smem, W);
-    bpe_sync_kernel<<<g128, 128, 0, s>>>(T, W);
-    bpe_repair_kernel<<<1, 32, 0, s>>>(T, W);
-    bpe_maps_kernel<<<(unsigned)((W.max_seg * 32 + 127) / 128), 128, 0, s>>>(T, W);
-    bpe_entries_kernel<<<g128, 128, 0, s>>>(T, W);
     const long long nblk = scan_blocks(W.max_seg);
+    if (b->lmax <= 16) bpe_dp_kernel<16><<<gdp, kDpThreads, 0, s>>>(T, W);
+    else bpe_dp_kernel<32><<<gdp, kDpThreads, 0, s>>>(T, W);
+    bpe_sync_kernel<<<g128, 128, 0, s>>>(T, W);
+    bpe_rep_reduce<<<(unsigned)nblk, kScanThreads, 0, s>>>(W);
+    bpe_rep_top<<<1, kScanThreads, 0, s>>>(W, nblk);
+    bpe_rep_down<<<(unsigned)nblk, kScanThreads, 0, s>>>(W);
+    if (b->lmax <= 16) bpe_repair_kernel<16><<<gdp, kDpThreads, 0, s>>>(T, W);
+    else bpe_repair_kernel<32><<<gdp, kDpThreads, 0, s>>>(T, W);
+    bpe_entries_kernel<<<g128, 128, 0, s>>>(T, W);
     bpe_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, s>>>(W);
     bpe_scan_top<<<1, kScanThreads, 0, s>>>(W, nblk);
     bpe_scan_down<<<(unsigned)nblk, kScanThreads, 0, s>>>(W);
     // the emit takes its positions from the scans: launch it only if they launched
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "BPE kernel launch");
-    bpe_emit_kernel<<<g256, 256, dyn, s>>>(T, use_smem, W);
+    bpe_emit_kernel<<<g256, 256, 0, s>>>(T, W);
     const long long nrec_bound = raw ? n_seq + 1 : offsets_capacity;
     long long og = (nrec_bound + 255) / 256;
     if (og > 4096) og = 4096;
     if (og < 1) og = 1;
-    bpe_offsets_kernel<<<(unsigned)og, 256, 0, s>>>(W);
+    bpe_offsets_kernel<<<(unsigned)og, 256, 0, s>>>(T, W);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "BPE kernel launch");
     return DNATOK_OK;

@@ -142,6 +142,32 @@ def test_table_validation(P):
     assert ei.value.status == -2
 
 
+def test_periodic_runs_force_repair(P):
+    """Long runs of A under (A,A), (AA,AA), (AAAA,AAAA): the tokens repeat
+    every 8 bases from the word start, and a word starting at an odd offset
+    puts every mid-word pass out of phase, so its halo never agrees and the
+    segments go through the exact repair, run after run (regions of several
+    records in parallel).  Ids and offsets must still equal the oracle's."""
+    m = np.array([[0, 0], [4, 4], [5, 5], [1, 0], [2, 3]], np.int32)
+    rng = np.random.default_rng(17)
+    recs = []
+    for i in range(12):
+        head = bytes(rng.choice(np.frombuffer(b"CGT", np.uint8), size=int(rng.integers(1, 8))))
+        recs.append(head + b"A" * int(rng.integers(3000, 40000)) + b"GTCA" * int(rng.integers(0, 50)))
+    recs.append(b"A" * 70001)
+    data = np.frombuffer(b"".join(recs), np.uint8)
+    offs = np.concatenate([[0], np.cumsum([len(r) for r in recs])]).astype(np.int64)
+    want = oracle.encode(data, oracle.BPE, seq_offsets=offs, merges=m)
+    for launch in [None, (64, 16), (256, 64), (1024, 0)]:
+        with P.Tokenizer(P.BPE, merges=m) as tok:
+            if launch:
+                P.binding.dnatok_set_bpe_launch(tok.h, *launch)
+            got = tok.encode_host(data, offs)
+            stats = P.binding.dnatok_bpe_stats(tok.h)
+        check(got, want, "launch %s" % (launch,))
+        assert stats["repaired_segments"] > 0, stats
+
+
 def test_full_size_1gib_every_record(P, merges4096):
     """512 x 2 Mb uppercase ACGT (1 GiB), the default launch: every record's
     ids equal the oracle's encoding of that record, element by element, and
