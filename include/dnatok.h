@@ -561,6 +561,23 @@ DNATOK_API dnatok_status dnatok_autotune(dnatok_handle *h, const uint8_t *bytes_
  * enable = 0 sends every encode straight to the general kernel.  Default 1. */
 DNATOK_API dnatok_status dnatok_set_direct(dnatok_handle *h, int32_t enable);
 
+/* How long a look-back wait of the general kernel polls before it gives up
+ * (each poll is followed by a sleep of up to about a microsecond): after
+ * that many polls the kernel records a timeout and returns, and
+ * dnatok_sync() reports DNATOK_ERR_TIMEOUT.  0 restores the default (about
+ * four million polls).  Lower it to bound how long a stalled launch can
+ * hold the GPU; tests lower it to see the timeout come back quickly. */
+DNATOK_API dnatok_status dnatok_set_wait_limit(dnatok_handle *h, int64_t polls);
+
+/* Fault injection, for testing the bounded waits: the next launch of the
+ * general kernel on this handle leaves look-back chunk `chunk` (chunks of
+ * tiles_per_chunk x tile_bytes input bytes, counted from 0) unprocessed, so
+ * the look-back of the chunk after it waits on a descriptor that is never
+ * published and runs out (DNATOK_ERR_TIMEOUT from dnatok_sync; the
+ * outputs of that launch are undefined).  -1 cancels.  Affects one launch.
+ * (No counterpart in the paper.) */
+DNATOK_API dnatok_status dnatok_inject_lookback_stall(dnatok_handle *h, int64_t chunk);
+
 /* BPE handles: symbols per segment of the merge pass (64..65536, a multiple
  * of 16, at least twice the longest token) and the halo each segment's pass
  * starts before it (0..seg_symbols, a multiple of 16).  A segment whose

@@ -119,6 +119,8 @@ def lib():
             "dnatok_get_bpe_launch": (_ST, [_P, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
             "dnatok_bpe_stats": (_ST, [_P, ctypes.POINTER(_I64), _P]),
+            "dnatok_set_wait_limit": (_ST, [_P, _I64]),
+            "dnatok_inject_lookback_stall": (_ST, [_P, _I64]),
             "dnatok_graph_begin": (_ST, [_P, _P]),
             "dnatok_graph_end": (_ST, [_P, _P, ctypes.POINTER(_P)]),
             "dnatok_graph_launch": (_ST, [_P, _P]),
@@ -290,6 +292,14 @@ def dnatok_get_bpe_launch(h) -> tuple:
     a, b = ctypes.c_int32(), ctypes.c_int32()
     check(lib().dnatok_get_bpe_launch(h, ctypes.byref(a), ctypes.byref(b)), h)
     return (a.value, b.value)
+
+
+def dnatok_set_wait_limit(h, polls: int) -> None:
+    check(lib().dnatok_set_wait_limit(h, polls), h)
+
+
+def dnatok_inject_lookback_stall(h, chunk: int) -> None:
+    check(lib().dnatok_inject_lookback_stall(h, chunk), h)
 
 
 def dnatok_bpe_stats(h, stream: int = 0) -> dict:

@@ -75,7 +75,7 @@ dnatok_status next_epoch(dnatok_handle *h, cudaStream_t s, unsigned *epoch) {
     h->epoch++;
     if ((h->epoch & ((1u << kEpochBits) - 1)) == 0) {  // epoch wrap: forget every old descriptor
         cudaError_t e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * h->desc_cap, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_gate, 0, 2 * sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_gate, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
         h->epoch++;
     }
@@ -113,6 +113,9 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
     p.start_boundary = start_boundary;
     p.end_boundary = end_boundary;
     p.head_pad = (int)((uintptr_t)bytes & 15u);
+    p.spin_limit = h->spin_limit;
+    p.skip_chunk = h->skip_chunk;
+    h->skip_chunk = -1;  // one launch only
     p.lut_keeps_bases = 1;
     for (const char *c = "ACGTacgt"; *c; ++c)
         if (h->lut_host[(unsigned char)*c] < 0) p.lut_keeps_bases = 0;
@@ -222,8 +225,8 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
     if (e == cudaSuccess) e = cudaMemset(h->d_counter, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_gate, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(h->d_gate, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_gate, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(h->d_gate, 0, sizeof(unsigned));
     if (e == cudaSuccess && mode == DNATOK_KMER_TABLE) {
         e = cudaMalloc(&h->d_klut, sizeof(int32_t) * (size_t)n_index);
         if (e == cudaSuccess)
@@ -462,6 +465,18 @@ dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg) 
 dnatok_status dnatok_set_direct(dnatok_handle *h, int32_t enable) {
     if (!h || (enable != 0 && enable != 1)) return DNATOK_ERR_ARG;
     h->direct = enable != 0;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_set_wait_limit(dnatok_handle *h, int64_t polls) {
+    if (!h || polls < 0) return DNATOK_ERR_ARG;
+    h->spin_limit = polls == 0 ? kSpinLimit : polls;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_inject_lookback_stall(dnatok_handle *h, int64_t chunk) {
+    if (!h || chunk < -1) return DNATOK_ERR_ARG;
+    h->skip_chunk = chunk;
     return DNATOK_OK;
 }
 

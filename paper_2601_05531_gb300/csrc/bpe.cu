@@ -61,6 +61,7 @@ constexpr int kDpThreads = 128;     // threads (segments) per block of the merge
 struct BpeTables {
     int V;                 // 4 + M token ids; N_ID = V
     int lmax;              // longest self-encoding token
+    int n_nodes;           // automaton nodes
     const uint4 *node;     // automaton, node 0 = root (empty string)
     const uint8_t *tok_len;  // V + 1 entries (N_ID has length 1)
     const unsigned *compat;  // V x V bits, row = left token
@@ -117,25 +118,33 @@ __device__ __forceinline__ long long rec_upper(const long long *rec_off, long lo
     return lo;
 }
 
+// Node records: from the copy in dynamic shared memory (SM) or from global
+// memory through the read-only cache.
+extern __shared__ __align__(16) uint4 bpe_dyn[];
+template <bool SM>
+__device__ __forceinline__ uint4 node_at(const BpeTables &T, unsigned i) {
+    if (SM) return bpe_dyn[i];
+    return __ldg(T.node + i);
+}
+
 // The state of one left-to-right pass: automaton node (and its record), the
 // word length so far (capped at 63), and a ring of the last R token ids in
-// shared memory (column `tid` of an R x kDpThreads array).
-template <int R>
+// shared memory (column `tid` of an R x NT array).
 struct DpPass {
     uint4 nd;               // record of the current node
     unsigned state;
     int wd;
-    unsigned short *ring;   // ring[i * kDpThreads]
+    unsigned short *ring;   // ring[i * NT]
 };
 
 // One step at symbol j (a base c): move the automaton, then take the first
 // candidate (longest first) that starts the word or is compatible with the
 // token before it.  The single base at the end of every list is taken
 // without a check (no other candidate fits).  Returns (length << 16) | token.
-template <int R>
-__device__ __forceinline__ unsigned dp_step(const BpeTables &T, DpPass<R> &P, long long j, unsigned c) {
+template <int R, int NT, bool SM>
+__device__ __forceinline__ unsigned dp_step(const BpeTables &T, DpPass &P, long long j, unsigned c) {
     P.state = node_next(P.nd, c);
-    P.nd = __ldg(T.node + P.state);
+    P.nd = node_at<SM>(T, P.state);
     if (P.wd < 63) ++P.wd;
     const int wd = P.wd;
     unsigned t1 = P.nd.z & 0xFFFFu, t2 = P.nd.z >> 16;
@@ -143,8 +152,8 @@ __device__ __forceinline__ unsigned dp_step(const BpeTables &T, DpPass<R> &P, lo
     // both candidates' checks are issued before either is used
     const bool n1 = (l1 != wd) && (l1 > 1);
     const bool n2 = (t2 != kNone16) && (l2 != wd) && (l2 > 1);
-    const unsigned a1 = n1 ? P.ring[((j - l1) & (R - 1)) * kDpThreads] : 0u;
-    const unsigned a2 = n2 ? P.ring[((j - l2) & (R - 1)) * kDpThreads] : 0u;
+    const unsigned a1 = n1 ? P.ring[((j - l1) & (R - 1)) * NT] : 0u;
+    const unsigned a2 = n2 ? P.ring[((j - l2) & (R - 1)) * NT] : 0u;
     const bool ok1 = !n1 || compat_bit(T.compat, T.V, a1, t1);
     const bool ok2 = !n2 || compat_bit(T.compat, T.V, a2, t2);
     if (ok1) return ((unsigned)l1 << 16) | t1;
@@ -153,18 +162,18 @@ __device__ __forceinline__ unsigned dp_step(const BpeTables &T, DpPass<R> &P, lo
     unsigned nx = P.nd.w >> 16;
     unsigned last = ((unsigned)l2 << 16) | t2;
     for (int guard = 0; nx != kNone16 && guard < kMaxTokLen; ++guard) {
-        const uint4 q = __ldg(T.node + nx);
+        const uint4 q = node_at<SM>(T, nx);
         t1 = q.z & 0xFFFFu;
         t2 = q.z >> 16;
         l1 = (int)(q.w & 63u);
         l2 = (int)((q.w >> 6) & 63u);
         if (l1 == wd || l1 == 1 ||
-            compat_bit(T.compat, T.V, P.ring[((j - l1) & (R - 1)) * kDpThreads], t1))
+            compat_bit(T.compat, T.V, P.ring[((j - l1) & (R - 1)) * NT], t1))
             return ((unsigned)l1 << 16) | t1;
         last = ((unsigned)l1 << 16) | t1;
         if (t2 == kNone16) break;
         if (l2 == wd || l2 == 1 ||
-            compat_bit(T.compat, T.V, P.ring[((j - l2) & (R - 1)) * kDpThreads], t2))
+            compat_bit(T.compat, T.V, P.ring[((j - l2) & (R - 1)) * NT], t2))
             return ((unsigned)l2 << 16) | t2;
         last = ((unsigned)l2 << 16) | t2;
         nx = q.w >> 16;
@@ -172,10 +181,10 @@ __device__ __forceinline__ unsigned dp_step(const BpeTables &T, DpPass<R> &P, lo
     return last;  // unreachable for a valid table (the single base always fits)
 }
 
-template <int R>
-__device__ __forceinline__ void dp_reset(const BpeTables &T, DpPass<R> &P) {
+template <bool SM>
+__device__ __forceinline__ void dp_reset(const BpeTables &T, DpPass &P) {
     P.state = 0;
-    P.nd = __ldg(T.node);
+    P.nd = node_at<SM>(T, 0);
     P.wd = 0;
 }
 
@@ -286,9 +295,9 @@ __global__ void bpe_compat_kernel(RankHash h, const uint8_t *pool, const int *po
 // before s.  16 symbols per load and 16 values per pair of stores: s, H and
 // the buffers are 16-aligned; j_begin only shifts where the first block
 // starts.
-template <int R>
+template <int R, int NT, bool SM>
 __device__ void seg_pass(const BpeTables &T, const BpeWork &W, long long seg, long long s,
-                         long long e, long long j_begin, long long r, DpPass<R> &P,
+                         long long e, long long j_begin, long long r, DpPass &P,
                          unsigned *ringf, bool &exact) {
     const long long nb = W.tot[1] + 1;
     long long next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
@@ -307,7 +316,7 @@ __device__ void seg_pass(const BpeTables &T, const BpeWork &W, long long seg, lo
         for (int q = q0; q < q1; ++q) {
             const long long j = j0 + q;
             while (j == next_b) {
-                dp_reset(T, P);
+                dp_reset<SM>(T, P);
                 ++r;
                 next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
                 if (j < s) exact = true;  // a record starts in the halo
@@ -318,19 +327,19 @@ __device__ void seg_pass(const BpeTables &T, const BpeWork &W, long long seg, lo
             if (c >= 4) {
                 L = 1;
                 t = N_ID;
-                dp_reset(T, P);
+                dp_reset<SM>(T, P);
                 if (j < s) exact = true;  // a word starts after it, before the segment
             } else {
-                const unsigned pk = dp_step<R>(T, P, j, c);
+                const unsigned pk = dp_step<R, NT, SM>(T, P, j, c);
                 L = pk >> 16;
                 t = pk & 0xFFFFu;
             }
-            P.ring[(j & (R - 1)) * kDpThreads] = (unsigned short)t;
+            P.ring[(j & (R - 1)) * NT] = (unsigned short)t;
             if (j >= s) {
                 const long long back = j - (long long)L;
                 const unsigned F = back < s ? ((unsigned)(s - 1 - back) << 24) | 1u
-                                            : ringf[(back & (R - 1)) * kDpThreads] + 1u;
-                ringf[(j & (R - 1)) * kDpThreads] = F;
+                                            : ringf[(back & (R - 1)) * NT] + 1u;
+                ringf[(j & (R - 1)) * NT] = F;
             }
             const int sh = 16 * (q & 3);
             const unsigned long long keep = ~(0xFFFFull << sh), v = (unsigned long long)t << sh;
@@ -360,7 +369,7 @@ __device__ void seg_pass(const BpeTables &T, const BpeWork &W, long long seg, lo
     bool same = true;
     for (int u = 0; u < T.lmax; ++u) {
         const long long p = e - 1 - u;
-        const unsigned F = (p >= s) ? ringf[(p & (R - 1)) * kDpThreads]
+        const unsigned F = (p >= s) ? ringf[(p & (R - 1)) * NT]
                                     : ((unsigned)(s - 1 - p) << 24);
         const unsigned v = F >> 24;
         W.map_v[seg * 32 + u] = (uint8_t)v;
@@ -371,36 +380,50 @@ __device__ void seg_pass(const BpeTables &T, const BpeWork &W, long long seg, lo
     W.const_v[seg] = same ? (uint8_t)first : (uint8_t)0xFF;
 }
 
-// The merge pass over one segment (thread per segment), started H symbols
-// before it unless a word starts closer.
-template <int R>
-__global__ void __launch_bounds__(kDpThreads) bpe_dp_kernel(BpeTables T, BpeWork W) {
-    __shared__ unsigned short ring_t[R * kDpThreads];
-    __shared__ unsigned ring_f[R * kDpThreads];
-    const long long seg = blockIdx.x * (long long)kDpThreads + threadIdx.x;
+// The merge pass, one segment per thread, started H symbols before it unless
+// a word starts closer.  Persistent: NT threads per block, one block per SM,
+// each thread takes segments tid, tid + grid threads, ...  Dynamic shared
+// memory holds the automaton's node records (SM; 16 bytes each, loaded once
+// per block) and the two rings of every thread.
+template <int R, int NT, bool SM>
+__global__ void __launch_bounds__(NT, 1) bpe_dp_kernel(BpeTables T, BpeWork W) {
+    const int n_node_words = SM ? T.n_nodes : 0;
+    unsigned short *ring_t = reinterpret_cast<unsigned short *>(bpe_dyn + n_node_words);
+    unsigned *ring_f = reinterpret_cast<unsigned *>(ring_t + R * NT);
+    if (SM) {
+        for (int i = threadIdx.x; i < T.n_nodes; i += NT) bpe_dyn[i] = __ldg(T.node + i);
+        __syncthreads();
+    }
     if (dev_failed(W.status)) return;
     const long long n_sym = W.tot[0], n_rec = W.tot[1];
     if (n_rec + 1 > W.offsets_cap) {
-        if (seg == 0) set_dev_status(W.status, DEV_CAPACITY);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_dev_status(W.status, DEV_CAPACITY);
         return;
     }
-    const long long s = seg * W.S;
-    if (s >= n_sym) return;
-    const long long e = (s + W.S < n_sym) ? s + W.S : n_sym;
     const long long nb = n_rec + 1;
-    long long r = rec_upper(W.rec_off, nb, s);
-    long long a = s - W.H;
-    bool exact = false;
-    if (a <= W.rec_off[r]) {
-        a = W.rec_off[r];
-        exact = true;
+    for (long long seg = blockIdx.x * (long long)NT + threadIdx.x; seg * W.S < n_sym;
+         seg += (long long)gridDim.x * NT) {
+        const long long s = seg * W.S;
+        const long long e = (s + W.S < n_sym) ? s + W.S : n_sym;
+        long long r = rec_upper(W.rec_off, nb, s);
+        long long a = s - W.H;
+        bool exact = false;
+        if (a <= W.rec_off[r]) {
+            a = W.rec_off[r];
+            exact = true;
+        }
+        while (r + 1 < nb && W.rec_off[r + 1] <= a) ++r;  // empty records at a
+        DpPass P;
+        P.ring = ring_t + threadIdx.x;
+        dp_reset<SM>(T, P);
+        seg_pass<R, NT, SM>(T, W, seg, s, e, a, r, P, ring_f + threadIdx.x, exact);
+        W.flags[seg] = exact ? 1 : 0;
     }
-    while (r + 1 < nb && W.rec_off[r + 1] <= a) ++r;  // empty records at a
-    DpPass<R> P;
-    P.ring = ring_t + threadIdx.x;
-    dp_reset(T, P);
-    seg_pass<R>(T, W, seg, s, e, a, r, P, ring_f + threadIdx.x, exact);
-    W.flags[seg] = exact ? 1 : 0;
+}
+
+template <int R, int NT, bool SM>
+size_t dp_smem_bytes(int n_nodes) {
+    return (SM ? (size_t)n_nodes * sizeof(uint4) : 0) + (size_t)R * NT * (2 + 4);
 }
 
 // A segment whose pass did not start exactly is correct if its halo agrees
@@ -532,6 +555,7 @@ __global__ void __launch_bounds__(kScanThreads) bpe_rep_down(BpeWork W) {
 // region; a region is one run of dependent segments.
 template <int R>
 __global__ void __launch_bounds__(kDpThreads) bpe_repair_kernel(BpeTables T, BpeWork W) {
+    // global node records (repairs are rare); rings in static shared memory
     __shared__ unsigned short ring_t[R * kDpThreads];
     __shared__ unsigned ring_f[R * kDpThreads];
     const int nbad = *W.n_bad;
@@ -541,7 +565,7 @@ __global__ void __launch_bounds__(kDpThreads) bpe_repair_kernel(BpeTables T, Bpe
     const int region = W.rep_region[i];
     if (i > 0 && W.rep_region[i - 1] == region) return;  // not the region's first
     const long long n_sym = W.tot[0], nb = W.tot[1] + 1;
-    DpPass<R> P;
+    DpPass P;
     P.ring = ring_t + threadIdx.x;
     unsigned *ringf = ring_f + threadIdx.x;
     long long done_until = 0;  // symbols below this are final
@@ -557,18 +581,18 @@ __global__ void __launch_bounds__(kDpThreads) bpe_repair_kernel(BpeTables T, Bpe
             long long x = s - 1;
             while (x >= ws && x >= s - 63 && W.sym[x] < 4) --x;
             // symbols (x, s) are the word so far (capped at 63)
-            dp_reset(T, P);
+            dp_reset<false>(T, P);
             const long long from = (s - (x + 1) > T.lmax) ? s - T.lmax : x + 1;
             for (long long y = from; y < s; ++y) {
                 P.state = node_next(P.nd, W.sym[y]);
-                P.nd = __ldg(T.node + P.state);
+                P.nd = node_at<false>(T, P.state);
             }
             P.wd = (int)(s - (x + 1));
             for (long long y = (s - R > 0 ? s - R : 0); y < s; ++y)
                 P.ring[(y & (R - 1)) * kDpThreads] = W.tok[y];
             const long long e = (s + W.S < n_sym) ? s + W.S : n_sym;
             bool exact = true;
-            seg_pass<R>(T, W, seg, s, e, s, r, P, ringf, exact);
+            seg_pass<R, kDpThreads, false>(T, W, seg, s, e, s, r, P, ringf, exact);
             done_until = e;
             ++seg;
             s = seg * W.S;
@@ -1059,6 +1083,40 @@ dnatok_status bpe_stats(dnatok_handle *h, long long *out, cudaStream_t s) {
     return DNATOK_OK;
 }
 
+// The merge pass launch: ring depth by the longest token, the node table in
+// shared memory when it fits beside the rings, one persistent block per SM.
+template <int R, int NT, bool SM>
+static cudaError_t launch_dp_as(const BpeTables &T, const BpeWork &W, int sm_count,
+                                cudaStream_t s) {
+    const size_t smem = dp_smem_bytes<R, NT, SM>(T.n_nodes);
+    static size_t attr = 0;
+    if (attr < smem) {
+        const cudaError_t e = cudaFuncSetAttribute(bpe_dp_kernel<R, NT, SM>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    long long grid = (W.max_seg + NT - 1) / NT;
+    if (grid > sm_count) grid = sm_count;
+    if (grid < 1) grid = 1;
+    bpe_dp_kernel<R, NT, SM><<<(unsigned)grid, NT, smem, s>>>(T, W);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_dp(dnatok_handle *h, const BpeTables &T, const BpeWork &W,
+                             cudaStream_t s) {
+    constexpr size_t kSmemMax = 220 * 1024;
+    if (T.lmax <= 16) {
+        if (dp_smem_bytes<16, 1024, true>(T.n_nodes) <= kSmemMax)
+            return launch_dp_as<16, 1024, true>(T, W, h->sm_count, s);
+        return launch_dp_as<16, 1024, false>(T, W, h->sm_count, s);
+    }
+    if (dp_smem_bytes<32, 512, true>(T.n_nodes) <= kSmemMax)
+        return launch_dp_as<32, 512, true>(T, W, h->sm_count, s);
+    return launch_dp_as<32, 512, false>(T, W, h->sm_count, s);
+}
+
 dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
                          const int64_t *seq_offsets_d, int64_t n_seq, int32_t *ids_out_d,
                          int64_t ids_capacity, int64_t *id_offsets_d, int64_t offsets_capacity,
@@ -1077,7 +1135,7 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     cudaError_t e = cudaMemsetAsync(b->d_nbad, 0, sizeof(int), s);
     if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync");
 
-    BpeTables T{b->V, b->lmax, b->d_node, b->d_tok_len, b->d_compat};
+    BpeTables T{b->V, b->lmax, b->n_nodes, b->d_node, b->d_tok_len, b->d_compat};
     BpeWork W;
     std::memset(&W, 0, sizeof(W));
     W.sym = b->d_sym;
@@ -1112,8 +1170,8 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     const unsigned g128 = (unsigned)((W.max_seg + 127) / 128);
     const unsigned g256 = (unsigned)((W.max_seg + 255) / 256);
     const long long nblk = scan_blocks(W.max_seg);
-    if (b->lmax <= 16) bpe_dp_kernel<16><<<gdp, kDpThreads, 0, s>>>(T, W);
-    else bpe_dp_kernel<32><<<gdp, kDpThreads, 0, s>>>(T, W);
+    e = launch_dp(h, T, W, s);
+    if (e != cudaSuccess) return fail_cuda(h, e, "BPE merge pass launch");
     bpe_sync_kernel<<<g128, 128, 0, s>>>(T, W);
     bpe_rep_reduce<<<(unsigned)nblk, kScanThreads, 0, s>>>(W);
     bpe_rep_top<<<1, kScanThreads, 0, s>>>(W, nblk);

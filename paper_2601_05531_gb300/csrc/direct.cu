@@ -7,13 +7,12 @@
 // record offsets without looking at the data: token m of record r goes to
 // id_offsets[r] + m.  Then the whole encode is embarrassingly parallel --
 // no scan across tiles, no look-back:
-//   1. direct_kmer_kernel: CTA 0 validates seq_offsets and writes id_offsets
-//      and totals from the record lengths (the record plan) and raises a
-//      flag; the other CTAs stream the bytes (16-byte loads, SWAR
-//      classification), wait for the flag before their first store, write
-//      the ids, and raise the gate when they meet a byte below 0x21
-//      (single-nucleotide ids and symbols need no plan: direct_byte_kernel);
-//   2. the general tile kernel is launched behind it gated on that flag: it
+//   1. direct_plan_kernel (one block) validates seq_offsets and writes
+//      id_offsets and totals from the record lengths;
+//   2. direct_kernel streams 16 KiB tiles (16-byte loads, SWAR classification
+//      as in the tile kernel), writes the ids, and flags the launch when it
+//      meets a byte below 0x21;
+//   3. the general tile kernel is launched behind it gated on that flag: it
 //      runs (and rewrites every output) only when the direct path's premise
 //      failed, and exits at once otherwise.
 // Paper: Algorithm 2's byte -> id gather and MapKmer, with the k-mer id in
@@ -26,7 +25,8 @@ namespace dnatok {
 namespace {
 
 constexpr int kDThreads = 256;
-constexpr int kPlanTile = 4096;  // records per pass of the record plan
+constexpr int kPlanThreads = 1024;
+constexpr int kPlanTile = 4096;  // records per pass of the plan kernel
 
 struct DirectParams {
     const uint8_t *base;       // bytes rounded down to 16
@@ -38,7 +38,6 @@ struct DirectParams {
     long long *offsets_out;    // id offsets (n_seq + 1)
     long long *totals_out;     // or null
     unsigned *gate;            // set to `epoch` when the general path must run
-    unsigned *ready;           // set to `epoch` once the record plan is written (k-mers)
     unsigned epoch;
     int k;
     unsigned long long kinv;   // ceil(2^64 / k) for k >= 2: floor(x / k) = umulhi(x, kinv)
@@ -55,22 +54,36 @@ __device__ __forceinline__ void raise_gate(const DirectParams &q) {
     if (*(volatile unsigned *)q.gate != q.epoch) *(volatile unsigned *)q.gate = q.epoch;
 }
 
-// The record plan: id offsets from the record lengths (ceil(L / k) each), in
-// passes of kPlanTile records staged through shared memory (`sv`, kPlanTile
-// + 1 entries; `wsum`, one entry per warp), loaded and stored coalesced.
-// Any malformed offset raises the gate, which sends the encode to the
-// general path (which reports it).  Run by one block of NT threads; it then
-// publishes the plan (q.ready = epoch, release order after every offset).
-template <int NT>
-__device__ void plan_records(const DirectParams &q, long long *sv, long long *wsum) {
-    constexpr int kPer = kPlanTile / NT;
+// id offsets from the record lengths; any malformed offset sends the encode
+// to the general path (which reports it).  One block (the direct kernel's
+// CTAs start while it runs): passes of kPlanTile records, each loaded and
+// stored coalesced through shared memory, one pass for up to 4096 records.
+__global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams q) {
+    constexpr int kPer = kPlanTile / kPlanThreads;
+    __shared__ long long s_v[kPlanTile + 1];
+    __shared__ long long wsum[kPlanThreads / 32];
+    pdl_launch_dependents();  // the direct kernel may start loading its input now
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = q.n_seq;
     bool bad = false;
     long long carry = 0;  // tokens of the records before this pass
     for (long long r0 = 0; r0 < n; r0 += kPlanTile) {
         const int cnt = (n - r0 < kPlanTile) ? (int)(n - r0) : kPlanTile;
-        for (int i = tid; i <= cnt; i += NT) sv[i] = __ldg(q.so + r0 + i);
+        {
+            // every load of the pass in flight at once
+            constexpr int kLd = (kPlanTile + 1 + kPlanThreads - 1) / kPlanThreads;
+            long long v[kLd];
+#pragma unroll
+            for (int it = 0; it < kLd; ++it) {
+                const int i = tid + it * kPlanThreads;
+                v[it] = (i <= cnt) ? __ldg(q.so + r0 + i) : 0;
+            }
+#pragma unroll
+            for (int it = 0; it < kLd; ++it) {
+                const int i = tid + it * kPlanThreads;
+                if (i <= cnt) s_v[i] = v[it];
+            }
+        }
         __syncthreads();
         long long t[kPer], sum = 0;
 #pragma unroll
@@ -78,7 +91,7 @@ __device__ void plan_records(const DirectParams &q, long long *sv, long long *ws
             const int i = tid * kPer + j;
             t[j] = 0;
             if (i < cnt) {
-                const long long L = sv[i + 1] - sv[i];
+                const long long L = s_v[i + 1] - s_v[i];
                 if (L < 0) bad = true;
                 t[j] = rec_tokens(q, L);
                 sum += t[j];
@@ -90,63 +103,36 @@ __device__ void plan_records(const DirectParams &q, long long *sv, long long *ws
             if (lane >= o) x += y;
         }
         if (lane == 31) wsum[warp] = x;
-        __syncthreads();  // every sv read above is done, wsum is complete
+        __syncthreads();  // every s_v read above is done, wsum is complete
         long long pre = carry, tot = 0;
 #pragma unroll
-        for (int w = 0; w < NT / 32; ++w) {
+        for (int w = 0; w < kPlanThreads / 32; ++w) {
             if (w < warp) pre += wsum[w];
             tot += wsum[w];
         }
         long long run = pre + x - sum;
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            sv[tid * kPer + j] = run;
+            s_v[tid * kPer + j] = run;
             run += t[j];
         }
         __syncthreads();
-        for (int i = tid; i < cnt; i += NT) q.offsets_out[r0 + i] = sv[i];
+        for (int i = tid; i < cnt; i += kPlanThreads) q.offsets_out[r0 + i] = s_v[i];
         carry += tot;
-        __syncthreads();  // sv and wsum are reused by the next pass
+        __syncthreads();  // s_v and wsum are reused by the next pass
     }
     if (tid == 0 && (__ldg(q.so) != 0 || __ldg(q.so + n) != q.n)) bad = true;
-    bad = __syncthreads_or(bad);
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) raise_gate(q);
+        return;
+    }
     if (tid == 0) {
-        if (bad) {
-            raise_gate(q);
-        } else {
-            q.offsets_out[n] = carry;
-            if (q.totals_out) {
-                q.totals_out[0] = carry;
-                q.totals_out[1] = n;
-            }
+        q.offsets_out[n] = carry;
+        if (q.totals_out) {
+            q.totals_out[0] = carry;
+            q.totals_out[1] = n;
         }
     }
-    __syncthreads();  // every offset of the block is written
-    if (tid == 0) {
-        __threadfence();
-        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(q.ready), "r"(q.epoch) : "memory");
-    }
-}
-
-// Wait (one warp) until the record plan of this launch is published; false
-// if the wait ran out (the caller then raises the gate: the general path
-// redoes the encode).
-__device__ __forceinline__ bool wait_plan(const DirectParams &q) {
-    unsigned v = 0u;
-    bool ok = false;
-    if ((threadIdx.x & 31) == 0) {
-        for (long long i = 0; i < kSpinLimit; ++i) {
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(q.ready) : "memory");
-            if (v == q.epoch) {
-                ok = true;
-                break;
-            }
-            __nanosleep(i < 64 ? 32 : 256);
-        }
-    }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (ok) asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(q.ready) : "memory");
-    return ok;
 }
 
 __device__ __forceinline__ unsigned dcodes4(unsigned x) { return ((x >> 1) ^ (x >> 2)) & 0x03030303u; }
@@ -263,7 +249,7 @@ struct RecWin {
 
 // Largest r in [0, n] with so[r] <= x, by one warp (32-way probes).  Only
 // reads so[0..n]; on non-monotone offsets it returns some index in range
-// (the record plan rejects those before any result is used).
+// (the plan kernel rejects those before any result is used).
 __device__ __forceinline__ long long warp_rec_search_safe(const long long *so, long long n,
                                                           long long x, int lane) {
     long long lo = 0, hi = n;
@@ -518,31 +504,18 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
     static_assert(K >= 2 && K <= 15, "k-mer length");
     using C = KC<K>;
     constexpr int kSpan = kV * kStep;  // bytes per warp step
-    union Smem {
-        struct {
-            RecWin wins[kSWarps];
-            uint4 ring[kSWarps][kRing][kV][32];
-        } st;
-        struct {
-            long long sv[kPlanTile + 1];
-            long long wsum[kSThreads / 32];
-        } plan;
-    };
-    __shared__ Smem sm;
-    // the general kernel behind this one may be scheduled as our CTAs retire
-    // (it waits on the device for this grid to finish)
+    // the gated general kernel behind this one may be scheduled as our CTAs
+    // retire (it waits on the device for this grid to finish)
     pdl_launch_dependents();
-    if (blockIdx.x == 0) {  // CTA 0 writes the record plan; the others stream
-        plan_records<kSThreads>(q, sm.plan.sv, sm.plan.wsum);
-        return;
-    }
+    __shared__ RecWin wins[kSWarps];
+    __shared__ uint4 ring_s[kSWarps][kRing][kV][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    RecWin &W = sm.st.wins[warp];
-    uint4 *const ring = &sm.st.ring[warp][0][0][lane];  // this lane's slot 0 of stage 0
+    RecWin &W = wins[warp];
+    uint4 *const ring = &ring_s[warp][0][0][lane];  // this lane's slot 0 of stage 0
     const long long lo = q.head_pad, hi = q.head_pad + q.n;  // valid aligned range
     const long long S = (hi + kSpan - 1) / kSpan;
-    const long long nw = (long long)(gridDim.x - 1) * kSWarps;
-    const long long gw = (long long)(blockIdx.x - 1) * kSWarps + warp;
+    const long long nw = (long long)gridDim.x * kSWarps;
+    const long long gw = (long long)blockIdx.x * kSWarps + warp;
     const long long s_begin = gw * S / nw, s_end = (gw + 1) * S / nw;
     if (s_begin >= s_end) return;
     const int n_steps = (int)(s_end - s_begin);
@@ -577,7 +550,7 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
     for (int u = 0; u < kRing - 1; ++u) issue(u);
 
     // The record holding the first step: seq_offsets is input, so this runs
-    // while CTA 0 is still writing the plan.
+    // while the plan kernel (a programmatic predecessor) is still working.
     const long long X0 = s_begin * kSpan - q.head_pad;
     RecState R;
     {
@@ -591,13 +564,9 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
         if (lane == 0) W.s[kWin] = r + kWin <= q.n_seq ? __ldg(q.so + r + kWin) : q.n;
         R.nv = (q.n_seq - r < kWin) ? (int)(q.n_seq - r) : kWin;
     }
-    // id offsets come from the plan (CTA 0): wait for it, then see whether it
+    // id offsets come from the plan kernel: wait for it, then see whether it
     // rejected seq_offsets
-    if (!wait_plan(q)) {
-        if (lane == 0) raise_gate(q);  // the general path redoes the encode
-        cp_async_wait<0>();
-        return;
-    }
+    pdl_wait();
     if (*(volatile const unsigned *)q.gate == q.epoch) {
         cp_async_wait<0>();
         return;
@@ -861,7 +830,6 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
     q.offsets_out = offsets_out;
     q.totals_out = totals_out;
     q.gate = gate;
-    q.ready = gate + 1;
     q.epoch = epoch;
     q.k = k;
     q.kinv = k > 1 ? ~0ull / (unsigned long long)k + 1ull : 0ull;
@@ -883,30 +851,36 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
             direct_byte_kernel<MODE_SYM><<<(unsigned)g2, kDThreads, 0, s>>>(q);
         return cudaGetLastError();
     }
-    // CTA 0 writes the record plan; CTAs 1.. stream the bytes (one wave of
-    // resident CTAs, every streaming warp with at least one step).  No
-    // programmatic dependency on earlier work: the kernel reads nothing it
-    // does not own until the plan flag of this launch is up.
-    static int occ = 0;
-    if (occ == 0) {
-        int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, direct_kmer_kernel<6>, kSThreads, 0) !=
-                cudaSuccess || o < 1)
-            o = 1;
-        occ = o;
+    direct_plan_kernel<<<1, kPlanThreads, 0, s>>>(q);
+    if (n > 0) {
+        // programmatic dependent launch: it starts while the plan runs
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(kDThreads);
+        cfg.stream = s;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr.val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        {
+            // one wave of resident CTAs, every warp with at least one step
+            static int occ = 0;
+            if (occ == 0) {
+                int o = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, direct_kmer_kernel<6>, kSThreads,
+                                                                  0) != cudaSuccess || o < 1)
+                    o = 1;
+                occ = o;
+            }
+            const long long steps = (q.head_pad + n + kV * kStep - 1) / (kV * kStep);
+            long long grid = (long long)sm_count * occ;
+            const long long need = (steps + kSWarps - 1) / kSWarps;
+            if (grid > need) grid = need;
+            cfg.blockDim = dim3(kSThreads);
+            cfg.gridDim = dim3((unsigned)grid);
+            return launch_kmer_k(k, cfg, q);
+        }
     }
-    const long long steps = (q.head_pad + n + kV * kStep - 1) / (kV * kStep);
-    long long grid = (long long)sm_count * occ - 1;
-    const long long need = (steps + kSWarps - 1) / kSWarps;
-    if (grid > need) grid = need;
-    if (grid < 0) grid = 0;
-    cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(kSThreads);
-    cfg.gridDim = dim3((unsigned)(grid + 1));
-    cfg.stream = s;
-    cfg.attrs = nullptr;
-    cfg.numAttrs = 0;
-    return launch_kmer_k(k, cfg, q);
     return cudaGetLastError();
 }
 

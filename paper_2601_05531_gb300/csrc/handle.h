@@ -31,9 +31,11 @@ struct dnatok_handle {
     long long rec_cap = 0;
     unsigned long long *d_counter = nullptr;
     int *d_status = nullptr;
-    unsigned *d_gate = nullptr;  // [0]: direct path -> general path switch, [1]: record plan
-                                 // published (both hold launch epochs)
+    unsigned *d_gate = nullptr;  // direct path -> general path switch (an epoch)
     unsigned epoch = 0;
+
+    long long spin_limit = dnatok::kSpinLimit;  // polls of a look-back wait (dnatok_set_wait_limit)
+    long long skip_chunk = -1;                  // next launch only (dnatok_inject_lookback_stall)
 
     dnatok::LaunchShape shape{16384, 256, 4, 8};
     bool direct = true;  // try the direct path on RAW input (dnatok_set_direct)  // tile, threads, CTAs per SM, tiles per chunk

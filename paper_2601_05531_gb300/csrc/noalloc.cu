@@ -129,6 +129,8 @@ extern "C" DNATOK_API dnatok_status dnatok_encode_kmer_noalloc(
     p.k = k;
     p.head_pad = head_pad;
     p.lut_keeps_bases = 1;
+    p.spin_limit = kSpinLimit;
+    p.skip_chunk = -1;
     p.epoch = 1;
     cudaError_t e;
     if (n_bytes == 0) {

@@ -73,10 +73,10 @@ struct TileParams {
     int lut_keeps_bases;           // MODE_CHAR: the table keeps all of A C G T a c g t
     const unsigned *gate;          // non-null: run only if *gate == gate_epoch
     unsigned gate_epoch;
+    long long spin_limit;          // polls before a look-back wait gives up (DEV_TIMEOUT)
+    long long skip_chunk;          // >= 0: this chunk is left unprocessed (wait-limit tests)
     unsigned *clear_gate;          // non-null (captured launches behind the direct path):
-                                   // clear_gate[1] (the direct kernel's plan flag) is
-                                   // cleared on exit; after a run, the last CTA also
-                                   // clears clear_gate[0] and the
+                                   // after a run, the last CTA clears *clear_gate and the
                                    // chunk descriptors, so the next replay starts clean
 };
 
@@ -331,7 +331,7 @@ static __device__ __noinline__ Agg lookback_counts(const TileParams &p, long lon
                 }
                 if (__all_sync(0xffffffffu, ok)) break;
             }
-            if (++spins > kSpinLimit || dev_failed(p.status)) {
+            if (++spins > p.spin_limit || dev_failed(p.status)) {
                 if (lane == 0) set_dev_status(p.status, DEV_TIMEOUT);
                 return agg_identity();
             }
@@ -376,7 +376,7 @@ static __device__ unsigned lookback_hmap(const TileParams &p, long long t, unsig
             jstar = incl ? 31 - __clz(incl) : -1;
             const unsigned above = (jstar >= 31) ? 0u : (0xffffffffu << (jstar + 1));
             if (!(empty & above)) break;
-            if (++spins > kSpinLimit || dev_failed(p.status)) {
+            if (++spins > p.spin_limit || dev_failed(p.status)) {
                 if (lane == 0) set_dev_status(p.status, DEV_TIMEOUT);
                 return HS_LS;
             }
@@ -403,13 +403,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
     // behind the direct path: run only when it found its premise broken
     if (p.gate) {
         pdl_wait();
-        if (*(volatile const unsigned *)p.gate != p.gate_epoch) {
-            // captured: the epochs are baked into the graph, so the direct
-            // kernel's record-plan flag is cleared for the next replay
-            if (p.clear_gate && blockIdx.x == 0 && threadIdx.x == 0)
-                *(volatile unsigned *)(p.clear_gate + 1) = 0u;
-            return;
-        }
+        if (*(volatile const unsigned *)p.gate != p.gate_epoch) return;
     }
 
     extern __shared__ __align__(128) uint8_t smem[];
@@ -528,6 +522,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
         __syncthreads();
         const long long c = s_chunk;
         if (c >= p.n_chunks) break;
+        if (c == p.skip_chunk) {  // never published: the next chunk's look-back runs out
+            __syncthreads();
+            continue;
+        }
         const long long t0 = c * NSUB;
         const int nt = (int)((p.n_tiles - t0) < NSUB ? (p.n_tiles - t0) : NSUB);
         const long long cbyte0 = t0 * TILE - p.head_pad;  // chunk index of tile t0's byte 0
@@ -1199,10 +1197,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tile_kernel(const TileParams p)
             uint4 *d = reinterpret_cast<uint4 *>(p.desc);
             const long long nw = p.n_chunks * (long long)(sizeof(TileDesc) / sizeof(uint4));
             for (long long i = tid; i < nw; i += NT) d[i] = make_uint4(0u, 0u, 0u, 0u);
-            if (tid == 0) {
-                *(volatile unsigned *)p.clear_gate = 0u;
-                *(volatile unsigned *)(p.clear_gate + 1) = 0u;
-            }
+            if (tid == 0) *(volatile unsigned *)p.clear_gate = 0u;
         }
     }
 }

@@ -146,3 +146,41 @@ def test_autotune_picks_and_caches(env, tmp_path, mode):
     assert got[1].tolist() == want[1].tolist()
     assert np.array_equal(got[0], want[0])
     tok.close()
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_lookback_wait_runs_out_and_handle_recovers(env, fmt):
+    """A look-back wait that can never be satisfied (the chunk before it is
+    left unprocessed by fault injection on the host) gives up after the
+    handle's wait limit: dnatok_sync reports DNATOK_ERR_TIMEOUT within a few
+    seconds, no trap, no hang, and the next encode on the same handle is
+    bit-exact against the oracle again."""
+    import time
+    torch, P = env
+    B = P.binding
+    if fmt == 0:
+        data, offs = synth.markov_batch([300_000, 1, 450_000, 500_000], 0.4, seed=5)
+        want = oracle.encode(data, oracle.KMER, k=6, seq_offsets=offs)
+    else:
+        data, _ = synth.fasta_stream(1_500_000, seed=6, rec_lo=1000, rec_hi=200_000)
+        offs = None
+        want = oracle.encode(data, oracle.KMER, k=6, fmt=oracle.FASTA)
+    with P.Tokenizer(P.KMER, k=6, fmt=fmt) as tok:
+        B.dnatok_set_direct(tok.h, 0)  # the general kernel (the one that looks back)
+        B.dnatok_set_wait_limit(tok.h, 2000)
+        d = torch.from_numpy(data).cuda()
+        so = torch.from_numpy(offs).cuda() if offs is not None else None
+        ids, o, tot = tok.alloc_outputs(len(data), len(offs) - 1 if offs is not None else 1)
+        tok.encode(d, so, ids, o, tot)  # warm: workspace and kernels
+        tok.sync()
+        B.dnatok_inject_lookback_stall(tok.h, 1)
+        t0 = time.time()
+        tok.encode(d, so, ids, o, tot)
+        with pytest.raises(P.DnatokError) as ei:
+            tok.sync()
+        assert ei.value.status == -6, ei.value
+        assert time.time() - t0 < 30
+        B.dnatok_set_wait_limit(tok.h, 0)
+        got = tok.encode_host(data, offs)
+    assert got[1].tolist() == want[1].tolist()
+    assert np.array_equal(got[0], want[0])
