@@ -697,10 +697,100 @@ __global__ void __launch_bounds__(kScanThreads) bpe_scan_down(BpeWork W) {
         }
 }
 
-// Thread per segment: walk its chain from the true entry backwards and write
-// each token's id at its place, last first (the segment's ids are one
-// contiguous run of the output).
-__global__ void __launch_bounds__(256) bpe_emit_kernel(BpeTables T, BpeWork W) {
+// The ids of every segment, in two phases per block of kEmitT segments:
+// (1) each thread walks its segment's chain from the true entry backwards and
+// marks the token ends in a shared-memory bitmap (tok values read in windows
+// of 32 positions, four independent 16-byte loads held in registers, so one
+// global round trip serves about six tokens); (2) each warp then writes its
+// 32 segments one after another: lane w takes bitmap word w (32 positions),
+// a warp scan of the counts gives each lane its output run, and the warp's
+// loads of tok and stores of ids are coalesced.  Segments longer than
+// kEmitMaxS use emit_walk_kernel, which writes each id as it walks.
+constexpr int kEmitT = 128;
+constexpr int kEmitMaxS = 2048;
+
+__device__ __forceinline__ unsigned pick4(const uint4 &v, int i) {
+    return i < 2 ? (i == 0 ? v.x : v.y) : (i == 2 ? v.z : v.w);
+}
+
+// Walk a segment's chain: f(e, t) for every token (end e, id t), last first.
+template <class F>
+__device__ __forceinline__ void walk_chain(const BpeTables &T, const BpeWork &W, long long s,
+                                           long long e, F &&f) {
+    long long wb = 1ll << 62;  // first position of the window held
+    uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+    while (e >= s) {
+        if (e < wb) {
+            wb = e & ~31ll;
+            const uint4 *src = reinterpret_cast<const uint4 *>(W.tok + wb);
+            v0 = src[0];
+            v1 = src[1];
+            v2 = src[2];
+            v3 = src[3];
+        }
+        const int wi = (int)((e - wb) >> 1);  // 32-bit word of the window, 0..15
+        const unsigned w = wi < 8 ? (wi < 4 ? pick4(v0, wi) : pick4(v1, wi - 4))
+                                  : (wi < 12 ? pick4(v2, wi - 8) : pick4(v3, wi - 12));
+        const unsigned t = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+        f(e, t);
+        e -= __ldg(T.tok_len + t);
+    }
+}
+
+__global__ void __launch_bounds__(kEmitT) bpe_emit_kernel(BpeTables T, BpeWork W) {
+    __shared__ unsigned bm[kEmitMaxS / 32][kEmitT + 1];  // [word][segment of the block], padded
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (dev_failed(W.status)) return;
+    const long long n_sym = W.tot[0];
+    const long long n_seg = (n_sym + W.S - 1) / W.S;
+    const int words = (W.S + 31) / 32;
+    const long long seg0 = blockIdx.x * (long long)kEmitT;
+    // 1. token ends of this thread's segment
+    {
+        const long long seg = seg0 + tid;
+        for (int w = 0; w < words; ++w) bm[w][tid] = 0u;
+        if (seg < n_seg) {
+            const long long s = seg * W.S;
+            const long long e_end = (s + W.S < n_sym) ? s + W.S : n_sym;
+            walk_chain(T, W, s, e_end - 1 - W.entry[seg], [&](long long e, unsigned) {
+                const int x = (int)(e - s);
+                bm[x >> 5][tid] |= 1u << (x & 31);
+            });
+        }
+    }
+    __syncthreads();
+    // 2. each warp writes its 32 segments' ids, one segment at a time
+    for (int i = 0; i < 32; ++i) {
+        const int col = warp * 32 + i;
+        const long long seg = seg0 + col;
+        if (seg >= n_seg) break;
+        const long long s = seg * W.S;
+        long long out = W.base[seg];
+        for (int w0 = 0; w0 < words; w0 += 32) {
+            const int w = w0 + lane;
+            const unsigned bits = (w < words) ? bm[w][col] : 0u;
+            const unsigned c = __popc(bits);
+            unsigned x = c;  // inclusive scan of the counts over the warp
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            long long pos = out + (x - c);
+            unsigned m = bits;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const unsigned id = W.tok[s + 32ll * w + b];
+                if (pos >= 0 && pos < W.out_cap) W.out[pos] = (int)id;
+                ++pos;
+            }
+            out += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+}
+
+// Long segments: thread per segment, each id written as the chain is walked.
+__global__ void __launch_bounds__(256) bpe_emit_walk_kernel(BpeTables T, BpeWork W) {
     const long long seg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (dev_failed(W.status)) return;
     const long long n_sym = W.tot[0];
@@ -708,14 +798,11 @@ __global__ void __launch_bounds__(256) bpe_emit_kernel(BpeTables T, BpeWork W) {
     if (seg >= n_seg) return;
     const long long s = seg * W.S;
     const long long e_end = (s + W.S < n_sym) ? s + W.S : n_sym;
-    long long e = e_end - 1 - W.entry[seg];
     long long pos = W.base[seg] + W.count[seg];
-    while (e >= s) {
-        const unsigned t = W.tok[e];
+    walk_chain(T, W, s, e_end - 1 - W.entry[seg], [&](long long, unsigned t) {
         --pos;
         if (pos >= 0 && pos < W.out_cap) W.out[pos] = (int)t;
-        e -= __ldg(T.tok_len + t);
-    }
+    });
 }
 
 // Record starts (in symbols) -> record starts (in ids), in place.
@@ -1185,7 +1272,10 @@ dnatok_status bpe_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     // the emit takes its positions from the scans: launch it only if they launched
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "BPE kernel launch");
-    bpe_emit_kernel<<<g256, 256, 0, s>>>(T, W);
+    if (b->S <= kEmitMaxS)
+        bpe_emit_kernel<<<(unsigned)((W.max_seg + kEmitT - 1) / kEmitT), kEmitT, 0, s>>>(T, W);
+    else
+        bpe_emit_walk_kernel<<<g256, 256, 0, s>>>(T, W);
     const long long nrec_bound = raw ? n_seq + 1 : offsets_capacity;
     long long og = (nrec_bound + 255) / 256;
     if (og > 4096) og = 4096;

@@ -1,11 +1,13 @@
 """The k-mer encode that allocates nothing (dnatok_encode_kmer_noalloc),
-called through the C ABI and compared with dnatok_encode on the same inputs:
-ids, offsets and totals must be identical, on two calls in a row (the second
-call finds the shared scratch array as the first one left it).  Named so that
-pytest collects it last; it passes alone and after the other tests."""
+called through the C ABI and compared with dnatok_encode on the same inputs
+and with the CPU oracle: ids, offsets and totals must be identical, on two
+calls in a row (the second call finds the shared scratch array as the first
+one left it).  Named so that pytest collects it last; it passes alone and
+after the other tests."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -33,6 +35,16 @@ def _inputs(torch, seed, n_seq, lo, hi, pad):
     d = torch.from_numpy(raw).cuda()[pad:]
     so = torch.from_numpy(offs).cuda()
     return d, so, len(data), n_seq
+
+
+def _oracle_same(got, d, so, n, n_seq, k):
+    """The no-allocation results against the CPU oracle's encoding."""
+    data = d.cpu().numpy()[:n] if n else np.zeros(0, np.uint8)
+    want_ids, want_offs = oracle.encode(data, oracle.KMER, k=k, seq_offsets=so.cpu().numpy())
+    ids, offs, tot = got[0].cpu(), got[1].cpu(), got[2].cpu().tolist()
+    assert tot == [len(want_ids), n_seq], (tot, len(want_ids), n_seq)
+    assert offs[: n_seq + 1].tolist() == want_offs.tolist()
+    assert ids[: len(want_ids)].tolist() == want_ids.tolist()
 
 
 def _outputs(torch, cap, n_seq):
@@ -89,6 +101,7 @@ def test_noalloc_matches_encode_twice(env, k):
         want = _with_handle(torch, P, k, d, so, n, n_seq)
         got = _noalloc(torch, P, k, d, so, n, n_seq, want[3])
         _same(got, want[:3])
+        _oracle_same(got, d, so, n, n_seq, k)
 
 
 def test_noalloc_same_input_twice_and_empty(env):
@@ -96,13 +109,17 @@ def test_noalloc_same_input_twice_and_empty(env):
     d, so, n, n_seq = _inputs(torch, 77, 500, 0, 5000, pad=5)
     want = _with_handle(torch, P, 6, d, so, n, n_seq)
     for _ in range(2):
-        _same(_noalloc(torch, P, 6, d, so, n, n_seq, want[3]), want[:3])
+        got = _noalloc(torch, P, 6, d, so, n, n_seq, want[3])
+        _same(got, want[:3])
+        _oracle_same(got, d, so, n, n_seq, 6)
     # zero bytes in three empty records
     e = torch.zeros(1, dtype=torch.uint8, device="cuda")
     so0 = torch.zeros(4, dtype=torch.int64, device="cuda")
     want0 = _with_handle(torch, P, 6, e, so0, 0, 3)
     for _ in range(2):
-        _same(_noalloc(torch, P, 6, e, so0, 0, 3, want0[3]), want0[:3])
+        got = _noalloc(torch, P, 6, e, so0, 0, 3, want0[3])
+        _same(got, want0[:3])
+        _oracle_same(got, e, so0, 0, 3, 6)
 
 
 def test_noalloc_rejects_oversize_before_launch(env):
