@@ -529,30 +529,16 @@ def _served(P, tr, merges, seconds):
             "offered_bytes_per_s": float(tr.sizes.sum() / seconds)}
 
 
-def _serving(torch, P, dev, seconds: float):
-    """Config-5 request trace (Poisson 2000/s, 200 B-1 MB, 30% single-
-    nucleotide / 50% 6-mer / 20% BPE with the 4096-merge table) replayed in
-    real time through the serving loop, and through per-request plain
-    launches (host copy + encode + wait, one request at a time); then the
-    serving loop alone at three times the arrival rate."""
+def _per_request(torch, P, dev, tr, merges):
+    """The same trace through per-request plain launches: each request's
+    host copy, encode and wait, one request at a time, in arrival order."""
     import numpy as np
-    import synth
     B = P.binding
-    tr = synth.request_trace(duration_s=seconds)
     n = len(tr.sizes)
-    m = np.loadtxt(os.path.join(ROOT, "tests", "golden", "bpe_merges_markov45_seed45_4096.txt"),
-                   dtype=np.int32)
-    res = {"requests": n, "offered_bytes_per_s": float(tr.sizes.sum() / seconds),
-           "budget_bytes": 4 << 30,
-           "latency": "both arms: completion seen by the submitting host thread minus the "
-                      "request's arrival time in the trace (queueing and refused submits "
-                      "included)"}
-    res["served"] = _served(P, tr, m, seconds)
-
-    # --- per-request plain launches
     pin = torch.from_numpy(tr.data).pin_memory()
     base = pin.data_ptr()
-    toks_b = {0: P.Tokenizer(P.CHAR), 1: P.Tokenizer(P.KMER, k=6), 2: P.Tokenizer(P.BPE, merges=m)}
+    toks_b = {0: P.Tokenizer(P.CHAR), 1: P.Tokenizer(P.KMER, k=6),
+              2: P.Tokenizer(P.BPE, merges=merges)}
     mx = int(tr.sizes.max())
     for t in toks_b.values():
         t.reserve(mx, 1)
@@ -578,14 +564,35 @@ def _serving(torch, P, dev, seconds: float):
     wall_b = time.perf_counter() - t0
     for t in toks_b.values():
         t.close()
-    res["per_request_launches"] = {"tokens_per_s": toks2 / wall_b,
-                                   "p50_ms": float(np.percentile(lat_b, 50)),
-                                   "p99_ms": float(np.percentile(lat_b, 99)), "wall_s": wall_b,
-                                   "tokens": toks2}
+    return {"tokens_per_s": toks2 / wall_b, "p50_ms": float(np.percentile(lat_b, 50)),
+            "p99_ms": float(np.percentile(lat_b, 99)), "wall_s": wall_b, "tokens": toks2}
+
+
+def _serving(torch, P, dev, seconds: float):
+    """Config-5 request trace (Poisson 2000/s, 200 B-1 MB, 30% single-
+    nucleotide / 50% 6-mer / 20% BPE with the 4096-merge table) replayed in
+    real time through the serving loop, and through per-request plain
+    launches (host copy + encode + wait, one request at a time); then both
+    at three times the arrival rate (3 s of trace)."""
+    import numpy as np
+    import synth
+    tr = synth.request_trace(duration_s=seconds)
+    n = len(tr.sizes)
+    m = np.loadtxt(os.path.join(ROOT, "tests", "golden", "bpe_merges_markov45_seed45_4096.txt"),
+                   dtype=np.int32)
+    res = {"requests": n, "offered_bytes_per_s": float(tr.sizes.sum() / seconds),
+           "budget_bytes": 4 << 30,
+           "latency": "both arms: completion seen by the submitting host thread minus the "
+                      "request's arrival time in the trace (queueing and refused submits "
+                      "included)"}
+    res["served"] = _served(P, tr, m, seconds)
+    res["per_request_launches"] = _per_request(torch, P, dev, tr, m)
     over_s = min(3.0, seconds)
     tr3 = synth.request_trace(rate=6000.0, duration_s=over_s)
     res["served_x3_rate"] = dict(_served(P, tr3, m, over_s), requests=len(tr3.sizes),
                                  rate_per_s=6000.0)
+    res["per_request_x3_rate"] = dict(_per_request(torch, P, dev, tr3, m), requests=len(tr3.sizes),
+                                      rate_per_s=6000.0)
     return res
 
 
@@ -1007,6 +1014,14 @@ def run_gpu(args):
         tok.set_launch(*[int(x) for x in args.shape.split(",")])
     tok.reserve(n_bytes, n_seq)
     ids, o_out, totals = tok.alloc_outputs(n_bytes, n_seq, device=dev)
+    # the direct kernel's shape (slots per step, ring depth, CTAs per SM),
+    # timed on this batch by the library's autotuner and kept in its cache
+    import tempfile
+    tune_cache = os.path.join(tempfile.gettempdir(), "dnatok_autotune_cache.txt")
+    _, tune_ms = binding.dnatok_autotune(tok.h, d_bytes.data_ptr(), n_bytes, d_offs.data_ptr(),
+                                         n_seq, ids.data_ptr(), ids.numel(), o_out.data_ptr(),
+                                         o_out.numel(), 3, tune_cache)
+    dshape = binding.dnatok_get_direct_launch(tok.h)
     # one non-default stream for everything (graph capture needs one)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
@@ -1119,7 +1134,10 @@ def run_gpu(args):
                        "launch_form": "CUDA graph replay of one dnatok_encode (value, "
                                       "roofline); plain_launch below is the same call "
                                       "launched directly",
-                       "launch": list(tok.get_launch()),
+                       "launch": {"kernel": "direct k-mer", "slots_per_step": dshape[0],
+                                  "ring_steps": dshape[1], "ctas_per_sm": dshape[2],
+                                  "chosen_by": "dnatok_autotune (cache %s; %s)" % (
+                                      tune_cache, "timed now" if tune_ms > 0 else "cache hit")},
                        "parallelism": ("record shards x%d (dnatok_shard_records over %d "
                                        "copies of the batch)" % (ws, ws)) if ws > 1
                        else "one GPU"},
@@ -1144,10 +1162,10 @@ def run_gpu(args):
             line["sharding"] = sharding
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(data, offs)
-        if ws == 1 and not args.no_extras:
-            _extras(line, torch, P, dev, data, offs, d_bytes, d_offs, flush_l2, args)
         if ws == 1 and args.stream_gib > 0:
             line["host_streamed"] = _streamed(torch, P, dev, int(args.stream_gib * 2**30))
+        if ws == 1 and not args.no_extras:
+            _extras(line, torch, P, dev, data, offs, d_bytes, d_offs, flush_l2, args)
         print(json.dumps(line), flush=True)
     tok.close()
     if ws > 1:

@@ -538,13 +538,18 @@ DNATOK_API void dnatok_graph_destroy(dnatok_graph *g);
 /*
  * Autotuner: time every supported launch shape (tile bytes, threads, tiles
  * per chunk, resident CTAs per SM; for BPE handles the merge pass's segment
- * size) on this input -- `reps` timed runs each after one warm-up, L2
- * flushed before each -- and keep the fastest on the handle.  Arguments as
+ * size; for k-mer handles whose RAW encodes take the direct path -- k >= 2,
+ * dnatok_set_direct on, n_seq <= 65536 -- the direct kernel's slots per
+ * step, ring depth and CTAs per SM) on this input -- `reps` timed runs each
+ * after one warm-up, L2 flushed before each -- and keep the fastest on the
+ * handle.  Arguments as
  * for dnatok_encode (device pointers; outputs are overwritten).  cache_path:
  * NULL or a text file; a line for this GPU, mode, k, format and input size
  * class (power of two) is reused without timing, and a new result is
  * appended.  best / best_ms (either may be NULL) receive the choice (for
- * BPE: {segment, halo, 0, 0}) and its mean time (-1 on a cache hit).
+ * BPE: {segment, halo, 0, 0}; for the direct path: {512 x slots per step,
+ * 256 threads, CTAs per SM, ring steps}) and its mean time (-1 on a cache
+ * hit).
  * Synchronizes; allocates a 192 MB scratch buffer while it runs.
  */
 DNATOK_API dnatok_status dnatok_autotune(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_bytes,
@@ -577,6 +582,19 @@ DNATOK_API dnatok_status dnatok_set_wait_limit(dnatok_handle *h, int64_t polls);
  * outputs of that launch are undefined).  -1 cancels.  Affects one launch.
  * (No counterpart in the paper.) */
 DNATOK_API dnatok_status dnatok_inject_lookback_stall(dnatok_handle *h, int64_t chunk);
+
+/* Shape of the direct k-mer kernel (RAW input without separators, k >= 2):
+ * 512-byte slots per warp step ("bytes per thread": 16 per slot), warp
+ * steps in its shared-memory ring ("pipeline depth": ring_steps - 1 steps in
+ * flight per warp), and resident CTAs per SM the grid is sized for (0 = as
+ * many as fit).  Supported: (slots, ring) in {(2, 4), (1, 8), (4, 2)},
+ * ctas_per_sm 0..4; DNATOK_ERR_ARG otherwise.  Default (2, 4, 0).  Results
+ * do not depend on the shape.  dnatok_autotune chooses it for handles that
+ * take the direct path. */
+DNATOK_API dnatok_status dnatok_set_direct_launch(dnatok_handle *h, int32_t slots_per_step,
+                                                  int32_t ring_steps, int32_t ctas_per_sm);
+/* out3 = {slots_per_step, ring_steps, ctas_per_sm}. */
+DNATOK_API dnatok_status dnatok_get_direct_launch(const dnatok_handle *h, int32_t *out3);
 
 /* BPE handles: symbols per segment of the merge pass (64..65536, a multiple
  * of 16, at least twice the longest token) and the halo each segment's pass

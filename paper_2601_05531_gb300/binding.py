@@ -120,6 +120,8 @@ def lib():
                                             ctypes.POINTER(ctypes.c_int32)]),
             "dnatok_bpe_stats": (_ST, [_P, ctypes.POINTER(_I64), _P]),
             "dnatok_set_wait_limit": (_ST, [_P, _I64]),
+            "dnatok_set_direct_launch": (_ST, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+            "dnatok_get_direct_launch": (_ST, [_P, ctypes.POINTER(ctypes.c_int32)]),
             "dnatok_inject_lookback_stall": (_ST, [_P, _I64]),
             "dnatok_graph_begin": (_ST, [_P, _P]),
             "dnatok_graph_end": (_ST, [_P, _P, ctypes.POINTER(_P)]),
@@ -292,6 +294,16 @@ def dnatok_get_bpe_launch(h) -> tuple:
     a, b = ctypes.c_int32(), ctypes.c_int32()
     check(lib().dnatok_get_bpe_launch(h, ctypes.byref(a), ctypes.byref(b)), h)
     return (a.value, b.value)
+
+
+def dnatok_set_direct_launch(h, slots_per_step: int, ring_steps: int, ctas_per_sm: int = 0) -> None:
+    check(lib().dnatok_set_direct_launch(h, slots_per_step, ring_steps, ctas_per_sm), h)
+
+
+def dnatok_get_direct_launch(h) -> tuple:
+    v = (ctypes.c_int32 * 3)()
+    check(lib().dnatok_get_direct_launch(h, v), h)
+    return (v[0], v[1], v[2])
 
 
 def dnatok_set_wait_limit(h, polls: int) -> None:

@@ -140,7 +140,7 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
         // whose general kernel ran clears the switch and its descriptors at
         // its end (clear_gate), so the next replay starts clean
         e = launch_direct(mode, bytes, n_bytes, seq_offsets, n_bnd - 1, out, offsets_out,
-                          totals_out, h->d_gate, ep, k, h->d_lut, h->sm_count, s);
+                          totals_out, h->d_gate, ep, k, h->d_lut, h->sm_count, h->dshape, s);
         if (e != cudaSuccess) return fail_cuda(h, e, "direct kernel launch");
         p.gate = h->d_gate;
         p.gate_epoch = ep;
@@ -459,6 +459,23 @@ dnatok_status dnatok_get_launch(const dnatok_handle *h, dnatok_launch_cfg *cfg) 
     cfg->threads = h->shape.threads;
     cfg->ctas_per_sm = h->shape.ctas_per_sm;
     cfg->chunk_tiles = h->shape.chunk_tiles;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_set_direct_launch(dnatok_handle *h, int32_t slots_per_step, int32_t ring_steps,
+                                       int32_t ctas_per_sm) {
+    if (!h) return DNATOK_ERR_ARG;
+    const DirectShape sh{slots_per_step, ring_steps, ctas_per_sm};
+    if (!direct_shape_supported(sh)) return fail(h, DNATOK_ERR_ARG, "unsupported direct shape");
+    h->dshape = sh;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_get_direct_launch(const dnatok_handle *h, int32_t *out3) {
+    if (!h || !out3) return DNATOK_ERR_ARG;
+    out3[0] = h->dshape.slots;
+    out3[1] = h->dshape.ring;
+    out3[2] = h->dshape.ctas_per_sm;
     return DNATOK_OK;
 }
 

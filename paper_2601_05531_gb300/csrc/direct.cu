@@ -473,8 +473,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-constexpr int kRing = 4;  // warp steps in flight: a ring of 4 x 1 KiB per warp
-constexpr int kV = 2;     // 512-byte slots per warp step (one vector per lane each)
+// The kernel's shape is tunable (dnatok_set_direct_launch, dnatok_autotune):
+// kV 512-byte slots per warp step (one vector per lane each), and a ring of
+// kRing steps per warp (kRing - 1 in flight); the supported pairs are the
+// instantiations in launch_kmer_k.  Default: 2 slots, 4 steps.
 
 // Classification of one 16-byte vector: packed codes and N flags.
 struct KSlot {
@@ -499,7 +501,7 @@ __device__ __forceinline__ KSlot k_classify(const uint4 &w, bool real, long long
     return r;
 }
 
-template <int K>
+template <int K, int kV, int kRing>
 __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams q) {
     static_assert(K >= 2 && K <= 15, "k-mer length");
     using C = KC<K>;
@@ -794,15 +796,30 @@ __global__ void __launch_bounds__(kDThreads) direct_byte_kernel(DirectParams q) 
     if (__syncthreads_or(sep) && tid == 0) raise_gate(q);
 }
 
-cudaError_t launch_kmer_k(int k, const cudaLaunchConfig_t &cfg, const DirectParams &q) {
+template <int KV, int KR>
+cudaError_t launch_kmer_kv(int k, const cudaLaunchConfig_t &cfg, const DirectParams &q) {
     switch (k) {
 #define DNATOK_K(KK) \
-    case KK: return cudaLaunchKernelEx(&cfg, direct_kmer_kernel<KK>, q);
+    case KK: return cudaLaunchKernelEx(&cfg, direct_kmer_kernel<KK, KV, KR>, q);
         DNATOK_K(2) DNATOK_K(3) DNATOK_K(4) DNATOK_K(5) DNATOK_K(6) DNATOK_K(7) DNATOK_K(8)
         DNATOK_K(9) DNATOK_K(10) DNATOK_K(11) DNATOK_K(12) DNATOK_K(13) DNATOK_K(14) DNATOK_K(15)
 #undef DNATOK_K
         default: return cudaErrorInvalidValue;
     }
+}
+
+// resident CTAs per SM of one instantiation (the same for every k)
+template <int KV, int KR>
+int kmer_occupancy() {
+    static int occ = 0;
+    if (occ == 0) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, direct_kmer_kernel<6, KV, KR>, kSThreads,
+                                                          0) != cudaSuccess || o < 1)
+            o = 1;
+        occ = o;
+    }
+    return occ;
 }
 
 }  // namespace
@@ -816,10 +833,17 @@ bool direct_eligible(int mode, long long n_seq, const int32_t *lut_host) {
     return mode == MODE_CHAR || mode == MODE_KMER || mode == MODE_SYM;
 }
 
+bool direct_shape_supported(const DirectShape &sh) {
+    const bool pair = (sh.slots == 2 && sh.ring == 4) || (sh.slots == 1 && sh.ring == 8) ||
+                      (sh.slots == 4 && sh.ring == 2);
+    return pair && sh.ctas_per_sm >= 0 && sh.ctas_per_sm <= 4;
+}
+
 cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const long long *so,
                           long long n_seq, void *out, long long *offsets_out,
                           long long *totals_out, unsigned *gate, unsigned epoch, int k,
-                          const int *lut, int sm_count, cudaStream_t s) {
+                          const int *lut, int sm_count, const DirectShape &shape,
+                          cudaStream_t s) {
     DirectParams q;
     q.head_pad = (int)((uintptr_t)bytes & 15u);
     q.base = bytes - q.head_pad;
@@ -855,31 +879,27 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
     if (n > 0) {
         // programmatic dependent launch: it starts while the plan runs
         cudaLaunchConfig_t cfg = {};
-        cfg.blockDim = dim3(kDThreads);
+        cfg.blockDim = dim3(kSThreads);
         cfg.stream = s;
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr.val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
-        {
-            // one wave of resident CTAs, every warp with at least one step
-            static int occ = 0;
-            if (occ == 0) {
-                int o = 0;
-                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, direct_kmer_kernel<6>, kSThreads,
-                                                                  0) != cudaSuccess || o < 1)
-                    o = 1;
-                occ = o;
-            }
-            const long long steps = (q.head_pad + n + kV * kStep - 1) / (kV * kStep);
-            long long grid = (long long)sm_count * occ;
-            const long long need = (steps + kSWarps - 1) / kSWarps;
-            if (grid > need) grid = need;
-            cfg.blockDim = dim3(kSThreads);
-            cfg.gridDim = dim3((unsigned)grid);
-            return launch_kmer_k(k, cfg, q);
-        }
+        // one wave of resident CTAs (at most shape.ctas_per_sm per SM), every
+        // warp with at least one step
+        const int kv = shape.slots, kr = shape.ring;
+        int occ = kv == 1 ? kmer_occupancy<1, 8>() : kv == 4 ? kmer_occupancy<4, 2>()
+                                                            : kmer_occupancy<2, 4>();
+        if (shape.ctas_per_sm > 0 && shape.ctas_per_sm < occ) occ = shape.ctas_per_sm;
+        const long long steps = (q.head_pad + n + kv * kStep - 1) / (kv * kStep);
+        long long grid = (long long)sm_count * occ;
+        const long long need = (steps + kSWarps - 1) / kSWarps;
+        if (grid > need) grid = need;
+        cfg.gridDim = dim3((unsigned)grid);
+        if (kv == 1 && kr == 8) return launch_kmer_kv<1, 8>(k, cfg, q);
+        if (kv == 4 && kr == 2) return launch_kmer_kv<4, 2>(k, cfg, q);
+        return launch_kmer_kv<2, 4>(k, cfg, q);
     }
     return cudaGetLastError();
 }

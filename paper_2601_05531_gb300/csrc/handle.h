@@ -38,6 +38,7 @@ struct dnatok_handle {
     long long skip_chunk = -1;                  // next launch only (dnatok_inject_lookback_stall)
 
     dnatok::LaunchShape shape{16384, 256, 4, 8};
+    dnatok::DirectShape dshape{2, 4, 0};  // direct k-mer kernel (dnatok_set_direct_launch)
     bool direct = true;  // try the direct path on RAW input (dnatok_set_direct)  // tile, threads, CTAs per SM, tiles per chunk
 
     // device staging of dnatok_encode_host
@@ -103,7 +104,8 @@ bool direct_eligible(int mode, long long n_seq, const int32_t *lut_host);
 cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const long long *so,
                           long long n_seq, void *out, long long *offsets_out,
                           long long *totals_out, unsigned *gate, unsigned epoch, int k,
-                          const int *lut, int sm_count, cudaStream_t s);
+                          const int *lut, int sm_count, const DirectShape &shape,
+                          cudaStream_t s);
 
 // BPE path (bpe.cu)
 dnatok_status bpe_create(dnatok_handle *h, const int32_t *merges, int32_t n_merges);

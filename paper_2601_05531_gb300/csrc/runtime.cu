@@ -8,8 +8,10 @@
 // may allocate under capture.
 //
 // Autotuner: times every supported launch shape of the tokenization kernel
-// (tile bytes, threads, tiles per chunk, resident CTAs per SM) -- or, for BPE
-// handles, the segment size of the merge pass -- on the caller's own input,
+// (tile bytes, threads, tiles per chunk, resident CTAs per SM) -- for BPE
+// handles the segment size of the merge pass, and for k-mer handles whose RAW
+// encodes take the direct kernel its slots per step, ring depth and resident
+// CTAs per SM -- on the caller's own input,
 // keeps the fastest on the handle, and remembers it in an optional text
 // cache keyed by GPU name, mode, k, format and input size class.
 #include <cstdio>
@@ -32,7 +34,13 @@ struct Candidate {
     int a, b, c, d;  // tile, threads, ctas_per_sm, chunk_tiles  |  BPE: seg, halo(-1 = default)
 };
 
-std::string cache_key(const dnatok_handle *h, long long n_bytes) {
+// Does a RAW encode on this handle take the direct k-mer kernel?
+bool tunes_direct(const dnatok_handle *h, long long n_seq) {
+    return h->mode == DNATOK_KMER && h->k >= 2 && h->fmt == DNATOK_RAW && h->direct &&
+           direct_eligible(MODE_KMER, n_seq, h->lut_host);
+}
+
+std::string cache_key(const dnatok_handle *h, long long n_bytes, bool direct) {
     cudaDeviceProp prop;
     std::string gpu = "gpu";
     if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) gpu = prop.name;
@@ -41,8 +49,8 @@ std::string cache_key(const dnatok_handle *h, long long n_bytes) {
     int cls = 0;
     while ((1ll << (cls + 1)) <= n_bytes) ++cls;
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "%s mode=%d k=%d fmt=%d size=2^%d", gpu.c_str(), h->mode, h->k,
-                  h->fmt, cls);
+    std::snprintf(buf, sizeof(buf), "%s mode=%d k=%d fmt=%d size=2^%d%s", gpu.c_str(), h->mode,
+                  h->k, h->fmt, cls, direct ? " direct" : "");
     return buf;
 }
 
@@ -73,7 +81,8 @@ void cache_store(const char *path, const std::string &key, const Candidate &c, f
     std::fclose(f);
 }
 
-dnatok_status apply(dnatok_handle *h, const Candidate &c) {
+dnatok_status apply(dnatok_handle *h, const Candidate &c, bool direct) {
+    if (direct) return dnatok_set_direct_launch(h, c.a, c.b, c.c);  // slots, ring, CTAs per SM
     if (h->mode == DNATOK_BPE) {
         int seg = 0, halo = 0;
         bpe_get_launch(h, &seg, &halo);
@@ -139,15 +148,21 @@ dnatok_status dnatok_autotune(dnatok_handle *h, const uint8_t *bytes_d, int64_t 
                               int64_t offsets_capacity, int32_t reps, const char *cache_path,
                               dnatok_launch_cfg *best_out, float *best_ms_out) {
     if (!h || reps < 1) return DNATOK_ERR_ARG;
-    const std::string key = cache_key(h, n_bytes);
+    const bool direct = tunes_direct(h, n_seq);
+    const std::string key = cache_key(h, n_bytes, direct);
     Candidate best{};
     float best_ms = -1.f;
     if (cache_lookup(cache_path, key, &best)) {
-        dnatok_status st = apply(h, best);
+        dnatok_status st = apply(h, best, direct);
         if (st != DNATOK_OK) return st;
     } else {
         std::vector<Candidate> cands;
-        if (h->mode == DNATOK_BPE) {
+        if (direct) {
+            // slots per step, ring steps, resident CTAs per SM
+            const int pairs[3][2] = {{2, 4}, {1, 8}, {4, 2}};
+            for (auto &pr : pairs)
+                for (int c = 1; c <= 4; ++c) cands.push_back({pr[0], pr[1], c, 0});
+        } else if (h->mode == DNATOK_BPE) {
             for (int seg : {256, 512, 1024, 2048, 4096}) cands.push_back({seg, -1, 0, 0});
         } else {
             const int shapes[4][3] = {{8192, 256, 8}, {16384, 256, 4}, {16384, 256, 8}, {32768, 512, 4}};
@@ -166,7 +181,7 @@ dnatok_status dnatok_autotune(dnatok_handle *h, const uint8_t *bytes_d, int64_t 
         dnatok_status st = DNATOK_OK;
         if (e != cudaSuccess) st = fail_cuda(h, e, "autotune set-up");
         for (size_t i = 0; st == DNATOK_OK && i < cands.size(); ++i) {
-            st = apply(h, cands[i]);
+            st = apply(h, cands[i], direct);
             if (st != DNATOK_OK) break;
             float tot = 0.f;
             for (int r = 0; r <= reps && st == DNATOK_OK; ++r) {
@@ -193,12 +208,15 @@ dnatok_status dnatok_autotune(dnatok_handle *h, const uint8_t *bytes_d, int64_t 
         if (b) cudaEventDestroy(b);
         if (s) cudaStreamDestroy(s);
         if (st != DNATOK_OK) return st;
-        st = apply(h, best);
+        st = apply(h, best, direct);
         if (st != DNATOK_OK) return st;
         cache_store(cache_path, key, best, best_ms);
     }
     if (best_out) {
-        if (h->mode == DNATOK_BPE) {
+        if (direct) {
+            *best_out = dnatok_launch_cfg{512 * h->dshape.slots, 256, h->dshape.ctas_per_sm,
+                                          h->dshape.ring};
+        } else if (h->mode == DNATOK_BPE) {
             int seg = 0, halo = 0;
             bpe_get_launch(h, &seg, &halo);
             *best_out = dnatok_launch_cfg{seg, halo, 0, 0};

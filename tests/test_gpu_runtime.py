@@ -115,13 +115,19 @@ def test_graph_needs_reserved_workspace(env):
         B.dnatok_graph_destroy(g)
 
 
-@pytest.mark.parametrize("mode", ["kmer", "bpe"])
+@pytest.mark.parametrize("mode", ["kmer_direct", "kmer_general", "bpe"])
 def test_autotune_picks_and_caches(env, tmp_path, mode):
+    """The autotuner times the shapes of the kernel the encode takes (the
+    direct k-mer kernel's slots, ring depth and CTAs per SM; the general
+    kernel's tiles; the BPE segment), keeps the fastest, serves the second
+    call from its cache file, and the tuned encode stays bit-exact."""
     torch, P = env
     B = P.binding
     data, offs = _batch(77, n_seq=200, hi=60_000)
-    if mode == "kmer":
+    if mode.startswith("kmer"):
         tok = P.Tokenizer(P.KMER, k=6)
+        if mode == "kmer_general":
+            B.dnatok_set_direct(tok.h, 0)
         want = oracle.encode(data, oracle.KMER, k=6, seq_offsets=offs)
     else:
         m = np.loadtxt(TABLE, dtype=np.int32)
@@ -136,16 +142,49 @@ def test_autotune_picks_and_caches(env, tmp_path, mode):
     assert ms > 0
     text = open(cache).read()
     assert " -> " in text and text.count("\n") == 1
+    assert (" direct" in text) == (mode == "kmer_direct")
     best2, ms2 = B.dnatok_autotune(tok.h, d.data_ptr(), len(data), so.data_ptr(),
                                    len(offs) - 1, ids.data_ptr(), ids.numel(), o.data_ptr(),
                                    o.numel(), 2, cache)
     assert best2 == best and ms2 < 0  # served from the cache
-    if mode == "kmer":
+    if mode == "kmer_general":
         assert tok.get_launch() == best
+    if mode == "kmer_direct":
+        slots, ring, ctas = B.dnatok_get_direct_launch(tok.h)
+        assert best == (512 * slots, 256, ctas, ring)
     got = tok.encode_host(data, offs)
     assert got[1].tolist() == want[1].tolist()
     assert np.array_equal(got[0], want[0])
-    tok.close()
+
+
+@pytest.mark.parametrize("shape", [(2, 4, 0), (1, 8, 0), (4, 2, 0), (2, 4, 1), (4, 2, 3), (1, 8, 2)])
+@pytest.mark.parametrize("k", [3, 6, 11])
+def test_direct_shapes_are_exact(env, shape, k):
+    """Every supported shape of the direct k-mer kernel gives the oracle's ids
+    and offsets: record boundaries at every phase, tiny and empty records,
+    N runs and lowercase, a misaligned start."""
+    torch, P = env
+    B = P.binding
+    rng = np.random.default_rng(k * 100 + shape[0] * 10 + shape[2])
+    lens = np.concatenate([rng.integers(0, 40, size=300), rng.integers(1000, 30000, size=60)])
+    rng.shuffle(lens)
+    data, offs = synth.markov_batch(lens, 0.4, seed=int(lens.sum() % 1000))
+    want = oracle.encode(data, oracle.KMER, k=k, seq_offsets=offs)
+    with P.Tokenizer(P.KMER, k=k) as tok:
+        B.dnatok_set_direct_launch(tok.h, *shape)
+        assert B.dnatok_get_direct_launch(tok.h) == shape
+        raw = np.zeros(len(data) + 5, np.uint8)
+        raw[5:] = data
+        d = torch.from_numpy(raw).cuda()[5:]
+        so = torch.from_numpy(offs).cuda()
+        ids, o, tot = tok.encode(d, so)
+        tok.sync()
+        n = int(tot[0])
+        assert o[: len(offs)].cpu().tolist() == want[1].tolist()
+        assert np.array_equal(ids[:n].cpu().numpy(), want[0])
+    with P.Tokenizer(P.KMER, k=k) as tok:
+        with pytest.raises(P.DnatokError):
+            B.dnatok_set_direct_launch(tok.h, 3, 4, 0)
 
 
 @pytest.mark.parametrize("fmt", [0, 1])
