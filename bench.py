@@ -804,6 +804,11 @@ def _bpe_1gib(torch, P, dev, flush_l2, with_cpu: bool = True, steps: int = 5):
     return out
 
 
+_FASTA_PATHS = {1: "compacted on the device, then the direct k-mer kernels",
+                0: "general tile kernel (the compacted path declined)",
+                -1: "general tile kernel"}
+
+
 def _fasta_chunk(torch, P, dev, mib: int, steps: int = 10):
     """Device-resident 6-mer encode of one FASTA chunk (the first `mib` MiB
     of the seeded 8 GiB stream): the unit of work the host-streamed encode
@@ -820,9 +825,11 @@ def _fasta_chunk(torch, P, dev, mib: int, steps: int = 10):
         ms = _time_median(torch, lambda: tok.encode(d, None, ids, o, tot, stream=s),
                           lambda i: None, steps=steps)
         tok.sync()
+        path = P.binding.dnatok_direct_ran(tok.h)
         n_ids, n_rec = int(tot[0].item()), int(tot[1].item())
     alg = n + 4 * n_ids + 8 * (n_rec + 1)
     return {"workload": "6-mer ids of a %d MiB FASTA chunk (device-resident)" % mib,
+            "path": _FASTA_PATHS[path],
             "tokens": n_ids, "records": n_rec, "ms": ms, "gb_per_s": n / (ms / 1e3) / 1e9,
             "roofline": _hbm(alg, ms, "CUDA events around one encode (the chunk is "
                                       "%d MiB; L2 not flushed)" % mib)}
@@ -1160,10 +1167,12 @@ def run_gpu(args):
         }
         if sharding:
             line["sharding"] = sharding
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = _cpu_baseline(data, offs)
+        # the host-streamed measurement runs before the oracle's worker processes
+        # start, so that nothing else on the host competes with its pinned copies
         if ws == 1 and args.stream_gib > 0:
             line["host_streamed"] = _streamed(torch, P, dev, int(args.stream_gib * 2**30))
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = _cpu_baseline(data, offs)
         if ws == 1 and not args.no_extras:
             _extras(line, torch, P, dev, data, offs, d_bytes, d_offs, flush_l2, args)
         print(json.dumps(line), flush=True)
@@ -1206,12 +1215,51 @@ def run_fasta_chunk(args):
             evs.append((a, b))
         torch.cuda.synchronize()
         tok.sync()
+        path = P.binding.dnatok_direct_ran(tok.h)
         us = sorted(1e3 * a.elapsed_time(b) for a, b in evs)
         med = us[len(us) // 2]
         print(json.dumps({"workload": "6-mer ids of a %d MiB FASTA chunk (device-resident)"
-                                      % args.fasta_chunk_mib,
+                                      % args.fasta_chunk_mib, "path": _FASTA_PATHS[path],
                           "median_us": med, "gb_per_s": n / (med * 1e-6) / 1e9,
                           "tokens": int(tot[0])}), flush=True)
+    return 0
+
+
+def run_bpe_only(args):
+    """BPE encode (4096 merges) of the first `--bpe-records` records of the
+    1 GiB corpus (each 2,097,152 bases), device-resident, inputs larger than L2
+    from 32 records up: prints one JSON line with the median CUDA-event time of
+    --steps encodes and the merge pass's repair statistics."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    import paper_2601_05531_gb300 as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    data, offs = synth.bpe_apply_corpus()
+    nrec = max(1, min(int(args.bpe_records), len(offs) - 1))
+    data, offs = data[: offs[nrec]], offs[: nrec + 1]
+    merges = np.loadtxt(os.path.join(ROOT, "tests", "golden",
+                                     "bpe_merges_markov45_seed45_4096.txt"), dtype=np.int32)
+    d = torch.from_numpy(data).to(dev)
+    so = torch.from_numpy(offs).to(dev)
+    s = torch.cuda.current_stream()
+    with P.Tokenizer(P.BPE, merges=merges) as tok:
+        tok.reserve(len(data), nrec)
+        ids, o, tot = tok.alloc_outputs(len(data), nrec, device=dev)
+        ms = _time_median(torch, lambda: tok.encode(d, so, ids, o, tot, stream=s),
+                          lambda i: None, steps=args.steps, warm=max(args.warmup, 3))
+        tok.sync()
+        n_ids = int(tot[0].item())
+        stats = P.binding.dnatok_bpe_stats(tok.h, s.cuda_stream)
+    alg = len(data) + 4 * n_ids + 16 * (nrec + 1)
+    print(json.dumps({"workload": "BPE (4096 merges) of %d x 2,097,152 bases" % nrec,
+                      "tokens": n_ids, "ms": ms, "tokens_per_s": n_ids / (ms / 1e3),
+                      "merge_pass": stats,
+                      "roofline": _hbm(alg, ms, "CUDA events around one encode")}), flush=True)
     return 0
 
 
@@ -1231,7 +1279,11 @@ def main():
                     help="size of the host-streamed FASTA measurement (0 = skip)")
     ap.add_argument("--fasta-chunk-mib", type=int, default=0,
                     help="time only the device-resident encode of one FASTA chunk of this size")
+    ap.add_argument("--bpe-records", type=int, default=0,
+                    help="time only the BPE encode of this many records of the 1 GiB corpus")
     args = ap.parse_args()
+    if args.bpe_records > 0:
+        return run_bpe_only(args)
     if args.fasta_chunk_mib > 0:
         return run_fasta_chunk(args)
     if args.impl == "reference":

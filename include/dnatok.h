@@ -566,6 +566,20 @@ DNATOK_API dnatok_status dnatok_autotune(dnatok_handle *h, const uint8_t *bytes_
  * enable = 0 sends every encode straight to the general kernel.  Default 1. */
 DNATOK_API dnatok_status dnatok_set_direct(dnatok_handle *h, int32_t enable);
 
+/* Which kernels finished the handle's last one-shot encode (dnatok_encode,
+ * also inside dnatok_encode_host or dnatok_autotune): waits for `stream`,
+ * then *out = 1 when the direct path produced every output, 0 when the
+ * general kernel ran behind it (the direct path declined the input: a byte
+ * below 0x21 in a record, a malformed seq_offsets, more FASTA records than
+ * the direct plan takes, too few id offsets for the FASTA records), -1 when
+ * the encode never tried the direct path (switched off, not eligible, or
+ * no encode yet).  FASTA handles take the direct path for k-mers (k >= 2) of
+ * 16-byte aligned text of 64 KiB up to 4 GiB: the text is first compacted on
+ * the device to its sequence bytes and record starts.  Not meaningful for
+ * an encode recorded in a graph (its replays reset the switch). */
+DNATOK_API dnatok_status dnatok_direct_ran(dnatok_handle *h, dnatok_cuda_stream stream,
+                                           int32_t *out);
+
 /* How long a look-back wait of the general kernel polls before it gives up
  * (each poll is followed by a sleep of up to about a microsecond): after
  * that many polls the kernel records a timeout and returns, and

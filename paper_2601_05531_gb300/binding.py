@@ -116,6 +116,7 @@ def lib():
             "dnatok_stream_close": (_ST, [_P]),
             "dnatok_set_bpe_launch": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
             "dnatok_set_direct": (_ST, [_P, ctypes.c_int32]),
+            "dnatok_direct_ran": (_ST, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
             "dnatok_get_bpe_launch": (_ST, [_P, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
             "dnatok_bpe_stats": (_ST, [_P, ctypes.POINTER(_I64), _P]),
@@ -284,6 +285,12 @@ def dnatok_stream_close(h) -> None:
 
 def dnatok_set_direct(h, enable: bool) -> None:
     check(lib().dnatok_set_direct(h, int(bool(enable))), h)
+
+
+def dnatok_direct_ran(h, stream=0) -> int:
+    out = ctypes.c_int32(0)
+    check(lib().dnatok_direct_ran(h, stream, ctypes.byref(out)), h)
+    return out.value
 
 
 def dnatok_set_bpe_launch(h, seg_symbols: int, halo: int) -> None:

@@ -65,6 +65,8 @@ dnatok_status ensure_workspace(dnatok_handle *h, long long n_bytes, long long n_
         h->d_tile_rec = r;
         h->desc_cap = cap;
         h->rec_cap = cap;
+        e = cudaMemset(h->d_gate, 0, sizeof(unsigned));  // no old epoch left in the switch
+        if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemset(gate)");
         h->epoch = 0;  // fresh zeroed descriptors: epoch 0 is never used
     }
     (void)n_bnd;
@@ -120,6 +122,7 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
     for (const char *c = "ACGTacgt"; *c; ++c)
         if (h->lut_host[(unsigned char)*c] < 0) p.lut_keeps_bases = 0;
     cudaError_t e;
+    h->direct_epoch = 0;
     if (n_bytes == 0) {
         e = launch_empty_chunk(p, bsrc == BSRC_LIST, s);
         if (e != cudaSuccess) return fail_cuda(h, e, "empty-chunk launch");
@@ -144,6 +147,20 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
         if (e != cudaSuccess) return fail_cuda(h, e, "direct kernel launch");
         p.gate = h->d_gate;
         p.gate_epoch = ep;
+        h->direct_epoch = ep;
+        if (capturing) p.clear_gate = h->d_gate;
+    } else if (bsrc == BSRC_FASTA && !carry_in && !carry_out &&
+               fasta_direct_eligible(h, mode, k, bytes, n_bytes)) {
+        // FASTA text: compacted to sequence bytes and record starts, then the
+        // direct path over them; the general kernel behind it reads the text
+        unsigned ep = 0;
+        st = next_epoch(h, s, &ep);
+        if (st != DNATOK_OK) return st;
+        st = fasta_direct(h, bytes, n_bytes, out, offsets_out, offsets_cap, totals_out, ep, k, s);
+        if (st != DNATOK_OK) return st;
+        p.gate = h->d_gate;
+        p.gate_epoch = ep;
+        h->direct_epoch = ep;
         if (capturing) p.clear_gate = h->d_gate;
     }
     st = next_epoch(h, s, &p.epoch);
@@ -272,6 +289,7 @@ void dnatok_destroy(dnatok_handle *h) {
     stream_destroy(h);
     bpe_destroy(h);
     ovl_destroy(h);
+    fasta_destroy(h);
     dec_destroy(h);
     cudaFree(h->d_klut);
     cudaFree(h->d_klut16);
@@ -307,6 +325,8 @@ dnatok_status dnatok_reserve(dnatok_handle *h, int64_t max_bytes, int64_t max_se
     if (h->mode == DNATOK_BPE) return bpe_reserve(h, max_bytes);
     if (h->mode == DNATOK_KMER_OVERLAP || h->mode == DNATOK_KMER_TABLE)
         return ovl_reserve(h, max_bytes, h->fmt == DNATOK_RAW ? max_seq + 1 : max_bytes + 2, 0);
+    if (h->fmt == DNATOK_FASTA && h->mode == DNATOK_KMER && h->k >= 2)
+        return fasta_reserve(h, max_bytes, 1ll << 40, 0);  // the record starts at full size
     return DNATOK_OK;
 }
 
@@ -482,6 +502,19 @@ dnatok_status dnatok_get_direct_launch(const dnatok_handle *h, int32_t *out3) {
 dnatok_status dnatok_set_direct(dnatok_handle *h, int32_t enable) {
     if (!h || (enable != 0 && enable != 1)) return DNATOK_ERR_ARG;
     h->direct = enable != 0;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_direct_ran(dnatok_handle *h, dnatok_cuda_stream stream, int32_t *out) {
+    if (!h || !out) return DNATOK_ERR_ARG;
+    *out = -1;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaStreamSynchronize");
+    if (h->direct_epoch == 0) return DNATOK_OK;
+    unsigned g = 0;
+    e = cudaMemcpy(&g, h->d_gate, sizeof(g), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemcpy(gate)");
+    *out = (g == h->direct_epoch) ? 0 : 1;
     return DNATOK_OK;
 }
 

@@ -43,7 +43,21 @@ struct DirectParams {
     unsigned long long kinv;   // ceil(2^64 / k) for k >= 2: floor(x / k) = umulhi(x, kinv)
     const int *lut;            // MODE_CHAR
     long long n_tiles;
+    // non-null (compacted FASTA): {n, n_seq} are read here on the device,
+    // written by kernels that finished before these start; n and n_seq
+    // above are then upper bounds (the grid is sized by n)
+    const long long *dyn;
 };
+
+// The parameters with the device-side counts in place, or null when an
+// earlier kernel of this encode already sent it to the general path.
+__device__ __forceinline__ bool resolve_counts(DirectParams &q) {
+    if (!q.dyn) return true;
+    if (*(volatile const unsigned *)q.gate == q.epoch) return false;
+    q.n = q.dyn[0];
+    q.n_seq = q.dyn[1];
+    return q.n_seq >= 1;
+}
 
 // tokens of a record of L kept symbols: ceil(L / k) (L when k = 1)
 __device__ __forceinline__ long long rec_tokens(const DirectParams &q, long long L) {
@@ -58,11 +72,13 @@ __device__ __forceinline__ void raise_gate(const DirectParams &q) {
 // to the general path (which reports it).  One block (the direct kernel's
 // CTAs start while it runs): passes of kPlanTile records, each loaded and
 // stored coalesced through shared memory, one pass for up to 4096 records.
-__global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams q) {
+__global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams q0) {
     constexpr int kPer = kPlanTile / kPlanThreads;
     __shared__ long long s_v[kPlanTile + 1];
     __shared__ long long wsum[kPlanThreads / 32];
     pdl_launch_dependents();  // the direct kernel may start loading its input now
+    DirectParams q = q0;
+    if (!resolve_counts(q)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = q.n_seq;
     bool bad = false;
@@ -502,7 +518,7 @@ __device__ __forceinline__ KSlot k_classify(const uint4 &w, bool real, long long
 }
 
 template <int K, int kV, int kRing>
-__global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams q) {
+__global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams q0) {
     static_assert(K >= 2 && K <= 15, "k-mer length");
     using C = KC<K>;
     constexpr int kSpan = kV * kStep;  // bytes per warp step
@@ -514,11 +530,18 @@ __global__ void __launch_bounds__(kSThreads, 4) direct_kmer_kernel(DirectParams 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RecWin &W = wins[warp];
     uint4 *const ring = &ring_s[warp][0][0][lane];  // this lane's slot 0 of stage 0
+    // the steps are dealt out by the bound on n (the grid's size), then cut
+    // at the data's end
+    const long long S = (q0.head_pad + q0.n + kSpan - 1) / kSpan;
+    DirectParams q = q0;
+    if (!resolve_counts(q)) return;
     const long long lo = q.head_pad, hi = q.head_pad + q.n;  // valid aligned range
-    const long long S = (hi + kSpan - 1) / kSpan;
+    const long long S_data = (hi + kSpan - 1) / kSpan;
     const long long nw = (long long)gridDim.x * kSWarps;
     const long long gw = (long long)blockIdx.x * kSWarps + warp;
-    const long long s_begin = gw * S / nw, s_end = (gw + 1) * S / nw;
+    const long long s_begin = gw * S / nw;
+    long long s_end = (gw + 1) * S / nw;
+    if (s_end > S_data) s_end = S_data;
     if (s_begin >= s_end) return;
     const int n_steps = (int)(s_end - s_begin);
 
@@ -843,8 +866,9 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                           long long n_seq, void *out, long long *offsets_out,
                           long long *totals_out, unsigned *gate, unsigned epoch, int k,
                           const int *lut, int sm_count, const DirectShape &shape,
-                          cudaStream_t s) {
+                          cudaStream_t s, const long long *dyn) {
     DirectParams q;
+    q.dyn = dyn;
     q.head_pad = (int)((uintptr_t)bytes & 15u);
     q.base = bytes - q.head_pad;
     q.n = n;
@@ -860,6 +884,7 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
     q.lut = lut;
     q.n_tiles = 0;
     const bool kmer = mode == MODE_KMER && k >= 2;
+    if (dyn && !kmer) return cudaErrorInvalidValue;  // device-side counts: k-mers only
     if (!kmer) {
         // single-nucleotide ids, symbols, and 1-mers (the default table maps
         // A/C/G/T to 0..3 and every other kept byte to 4 = UNK): one kernel,

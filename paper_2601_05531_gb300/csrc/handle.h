@@ -13,6 +13,7 @@
 struct StreamState;  // host-streamed pipeline (stream.cu)
 struct BpeState;     // BPE tables and workspace (bpe.cu)
 struct OvlState;     // overlapping k-mer workspace (ovl.cu)
+struct FastaState;   // compacted FASTA workspace (fasta.cu)
 
 struct dnatok_handle {
     int mode = 0;
@@ -39,6 +40,7 @@ struct dnatok_handle {
 
     dnatok::LaunchShape shape{16384, 256, 4, 8};
     dnatok::DirectShape dshape{2, 4, 0};  // direct k-mer kernel (dnatok_set_direct_launch)
+    unsigned direct_epoch = 0;  // the epoch of the last encode that tried the direct path, or 0
     bool direct = true;  // try the direct path on RAW input (dnatok_set_direct)  // tile, threads, CTAs per SM, tiles per chunk
 
     // device staging of dnatok_encode_host
@@ -53,6 +55,7 @@ struct dnatok_handle {
     StreamState *stream = nullptr;
     BpeState *bpe = nullptr;
     OvlState *ovl = nullptr;
+    FastaState *fasta = nullptr;
 
     // table-driven k-mers: kmer_lut (5^k ids) on the device, the single-symbol ids
     int32_t *d_klut = nullptr;
@@ -105,7 +108,16 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                           long long n_seq, void *out, long long *offsets_out,
                           long long *totals_out, unsigned *gate, unsigned epoch, int k,
                           const int *lut, int sm_count, const DirectShape &shape,
-                          cudaStream_t s);
+                          cudaStream_t s, const long long *dyn = nullptr);
+
+void fasta_destroy(dnatok_handle *h);
+dnatok_status fasta_reserve(dnatok_handle *h, long long n_bytes, long long offsets_cap,
+                            cudaStream_t s);
+bool fasta_direct_eligible(const dnatok_handle *h, int mode, int k, const uint8_t *bytes,
+                           long long n);
+dnatok_status fasta_direct(dnatok_handle *h, const uint8_t *bytes, long long n, void *out,
+                           long long *offsets_out, long long offsets_cap, long long *totals_out,
+                           unsigned epoch, int k, cudaStream_t s);
 
 // BPE path (bpe.cu)
 dnatok_status bpe_create(dnatok_handle *h, const int32_t *merges, int32_t n_merges);
