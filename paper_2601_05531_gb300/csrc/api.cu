@@ -149,14 +149,16 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
         p.gate_epoch = ep;
         h->direct_epoch = ep;
         if (capturing) p.clear_gate = h->d_gate;
-    } else if (bsrc == BSRC_FASTA && !carry_in && !carry_out &&
-               fasta_direct_eligible(h, mode, k, bytes, n_bytes)) {
-        // FASTA text: compacted to sequence bytes and record starts, then the
-        // direct path over them; the general kernel behind it reads the text
+    } else if (bsrc == BSRC_FASTA && fasta_direct_eligible(h, mode, k, bytes, n_bytes) &&
+               (start_boundary ? !carry_in : carry_in != nullptr)) {
+        // FASTA text (one-shot, or a chunk of a stream): compacted to sequence
+        // bytes and record starts, then the direct path over them; the
+        // general kernel behind it reads the text
         unsigned ep = 0;
         st = next_epoch(h, s, &ep);
         if (st != DNATOK_OK) return st;
-        st = fasta_direct(h, bytes, n_bytes, out, offsets_out, offsets_cap, totals_out, ep, k, s);
+        st = fasta_direct(h, bytes, n_bytes, out, out_cap, offsets_out, offsets_cap, totals_out,
+                          carry_in, carry_out, start_boundary, end_boundary, ep, k, s);
         if (st != DNATOK_OK) return st;
         p.gate = h->d_gate;
         p.gate_epoch = ep;

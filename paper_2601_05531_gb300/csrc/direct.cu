@@ -43,10 +43,13 @@ struct DirectParams {
     unsigned long long kinv;   // ceil(2^64 / k) for k >= 2: floor(x / k) = umulhi(x, kinv)
     const int *lut;            // MODE_CHAR
     long long n_tiles;
-    // non-null (compacted FASTA): {n, n_seq} are read here on the device,
-    // written by kernels that finished before these start; n and n_seq
-    // above are then upper bounds (the grid is sized by n)
+    // non-null (compacted FASTA): {n, n_seq, start, id base} are read here
+    // on the device, written by kernels that finished before these start;
+    // the input then begins `start` bytes after `base` (16-byte aligned) and
+    // n and n_seq above are upper bounds (the grid is sized by n)
     const long long *dyn;
+    long long d_base;          // output index of the first record's first id
+    long long out_cap;         // ids capacity (the plan sends a larger encode to the general path)
 };
 
 // The parameters with the device-side counts in place, or null when an
@@ -56,6 +59,10 @@ __device__ __forceinline__ bool resolve_counts(DirectParams &q) {
     if (*(volatile const unsigned *)q.gate == q.epoch) return false;
     q.n = q.dyn[0];
     q.n_seq = q.dyn[1];
+    const long long start = q.dyn[2];
+    q.base += start & ~15ll;
+    q.head_pad = (int)(start & 15);
+    q.d_base = q.dyn[3];
     return q.n_seq >= 1;
 }
 
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = q.n_seq;
     bool bad = false;
-    long long carry = 0;  // tokens of the records before this pass
+    long long carry = q.d_base;  // output index of the first id of this pass
     for (long long r0 = 0; r0 < n; r0 += kPlanTile) {
         const int cnt = (n - r0 < kPlanTile) ? (int)(n - r0) : kPlanTile;
         {
@@ -137,7 +144,7 @@ __global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams 
         carry += tot;
         __syncthreads();  // s_v and wsum are reused by the next pass
     }
-    if (tid == 0 && (__ldg(q.so) != 0 || __ldg(q.so + n) != q.n)) bad = true;
+    if (tid == 0 && (__ldg(q.so) != 0 || __ldg(q.so + n) != q.n || carry > q.out_cap)) bad = true;
     if (__syncthreads_or(bad)) {
         if (tid == 0) raise_gate(q);
         return;
@@ -866,9 +873,11 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                           long long n_seq, void *out, long long *offsets_out,
                           long long *totals_out, unsigned *gate, unsigned epoch, int k,
                           const int *lut, int sm_count, const DirectShape &shape,
-                          cudaStream_t s, const long long *dyn) {
+                          cudaStream_t s, const long long *dyn, long long out_cap) {
     DirectParams q;
     q.dyn = dyn;
+    q.d_base = 0;
+    q.out_cap = out_cap;
     q.head_pad = (int)((uintptr_t)bytes & 15u);
     q.base = bytes - q.head_pad;
     q.n = n;

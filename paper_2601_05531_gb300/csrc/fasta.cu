@@ -46,7 +46,8 @@ struct FastaState {
     uint4 *csum = nullptr;      // per CTA (8 spans): the same
     longlong2 *sin = nullptr;   // per CTA: {kept offset, 2 * headers before + in header}
     long long ctas_cap = 0;
-    long long *tot = nullptr;   // {kept bytes, records}
+    long long *info = nullptr;  // kInfo words: counts for the direct kernels and the finish
+    long long *plan = nullptr;  // per record (and the end): first id (stream chunks)
 };
 
 namespace dnatok {
@@ -62,6 +63,22 @@ constexpr int kScanT = 1024;                  // threads of the scan kernel
 constexpr long long kMaxRecords = 65536;      // records the direct kernel's plan takes
 constexpr long long kFastaMin = 64 << 10;     // smallest input the compacted path takes
 constexpr unsigned kFull = 0xffffffffu;
+
+// The info words (device): the first four are the direct kernels' counts.
+enum : int {
+    I_N = 0,      // input bytes of the direct kernels (the open last record cut to whole k-mers)
+    I_NREC = 1,   // records of the chunk (the continued one first)
+    I_START = 2,  // where that input begins after the kept bytes' buffer: 16 - I_M
+    I_DBASE = 3,  // output index of the first record's next id
+    I_M = 4,      // symbols carried in front of the kept bytes (the continued record's partial k-mer)
+    I_G0 = 5,     // global boundary index of the first record that starts here
+    I_CONT = 6,   // 1 when the first record continues one from an earlier chunk
+    I_END = 7,    // I_M + kept bytes
+    I_HSTATE = 8, // line state after the chunk (HS_*)
+    I_REC0 = 9,   // record index of the first header
+    kInfo = 16
+};
+constexpr long long kHead = 16;  // kept bytes start this far into the buffer
 
 // kinds of a line start (the scan's value; 0 = none)
 enum : unsigned { LS_NONE = 0, LS_SEQ = 2, LS_HDR = 3 };
@@ -182,7 +199,10 @@ struct FastaParams {
     uint4 *ssum;           // per span: {kept, kept if entered in a header, headers, kind}
     uint4 *csum;           // per CTA: the same over its spans
     longlong2 *sin;        // per CTA: {kept offset, 2 * headers before + in header}
-    long long *tot;        // {kept bytes, records}: the direct kernel's n and n_seq
+    long long *info;       // the I_* words
+    const Carry *cin;      // the scan state before the chunk (stream chunks), or null
+    int k;
+    int end_boundary;      // the text ends with the chunk (the last record closes)
     unsigned *gate;        // set to `epoch` when the general path must run
     unsigned epoch;
 };
@@ -225,9 +245,11 @@ __device__ __forceinline__ TextAt text_then(const TextAt &t, const Run2 &a) {
     return TextAt{hd_after(a, t.hd), t.kept + (t.hd ? a.k_hd : a.k_sq), t.heads + a.heads};
 }
 
-// Whether byte s0 starts a line (s0 = 0, or byte s0 - 1 is '\n').
+// Whether byte s0 starts a line: byte s0 - 1 is '\n', or s0 = 0 and the text
+// starts here or the chunk before ended at a line start.
 __device__ __forceinline__ unsigned line_start_at(const FastaParams &p, long long s0) {
-    return (s0 == 0 || p.bytes[s0 - 1] == '\n') ? 1u : 0u;
+    if (s0 == 0) return (!p.cin || p.cin->hstate == HS_LS) ? 1u : 0u;
+    return p.bytes[s0 - 1] == '\n' ? 1u : 0u;
 }
 
 // Per span, entered outside a header: its kept bytes, the kept bytes a span
@@ -296,6 +318,74 @@ __global__ void __launch_bounds__(kFT, 4) fasta_sum_kernel(FastaParams p) {
     }
 }
 
+// Symbol code (as the general kernel's carry holds them: 0-3 for A C G T in
+// either case, 4 for any other kept byte) and back to a letter.
+__device__ __forceinline__ unsigned sym_code(unsigned b) {
+    switch (b | 0x20u) {
+    case 'a': return 0u;
+    case 'c': return 1u;
+    case 'g': return 2u;
+    case 't': return 3u;
+    default: return 4u;
+    }
+}
+__device__ __forceinline__ uint8_t sym_letter(unsigned c) {
+    return (c & 4u) ? (uint8_t)'N' : (uint8_t)"ACGT"[c & 3u];
+}
+
+__device__ __forceinline__ void decline(const FastaParams &p) {
+    p.info[I_N] = 0;
+    p.info[I_NREC] = 0;
+    *(volatile unsigned *)p.gate = p.epoch;
+}
+
+// After the scan (one thread): the chunk's records -- the one continued from
+// the chunk before (or an implicit first one when the text starts here and
+// byte 0 is not '>'), then one per header -- the symbols of the continued
+// record's partial k-mer, written as letters in front of the kept bytes, the
+// end of the direct kernels' input (the open last record cut to whole k-mers
+// unless the text ends with this chunk; when that record starts at a header
+// the emit kernel cuts it), and the line state after the chunk.  The gate is
+// raised instead when the direct path cannot take the chunk.
+__device__ void scan_totals(const FastaParams &p, const TextAt &at) {
+    long long m = 0, d_base = 0, g0 = 0, rec0;
+    unsigned long long codes = 0ull;
+    if (p.cin) {
+        m = p.cin->a.t % p.k;
+        d_base = p.cin->a.d;
+        g0 = p.cin->a.nb;
+        codes = p.cin->a.codes;
+        rec0 = 1;
+    } else {
+        rec0 = (p.bytes[0] != '>') ? 1 : 0;
+    }
+    const long long n_rec = rec0 + at.heads;
+    const long long end = m + at.kept;
+    long long n_direct = end;
+    if (!p.end_boundary) n_direct = at.heads == 0 ? end / p.k * p.k : -1;
+    if (n_rec < 1 || n_rec + 1 > p.cso_cap || n_rec > kMaxRecords || n_direct == 0 ||
+        (p.end_boundary && end == 0)) {
+        decline(p);
+        return;
+    }
+    p.info[I_NREC] = n_rec;
+    p.info[I_START] = kHead - m;
+    p.info[I_DBASE] = d_base;
+    p.info[I_M] = m;
+    p.info[I_G0] = g0;
+    p.info[I_CONT] = p.cin ? 1 : 0;
+    p.info[I_END] = end;
+    p.info[I_HSTATE] = (p.bytes[p.n - 1] == '\n') ? HS_LS : (at.hd ? HS_HD : HS_SQ);
+    p.info[I_REC0] = rec0;
+    if (rec0) p.cso[0] = 0;
+    if (n_direct > 0) {
+        p.info[I_N] = n_direct;
+        p.cso[n_rec] = n_direct;
+    }
+    for (long long i = 0; i < m; ++i)  // the carried symbols, oldest first
+        p.cbytes[kHead - m + i] = sym_letter((unsigned)(codes >> (3 * (m - 1 - i))) & 7u);
+}
+
 // One block: every CTA's incoming (inside a header, kept offset, headers
 // before); the totals.  The CTA summaries go through shared memory in tiles
 // of kScanTile, loaded and stored coalesced: thread i composes entries
@@ -309,7 +399,8 @@ __global__ void __launch_bounds__(kScanT) fasta_scan_kernel(FastaParams p) {
     __shared__ Run2 wsum[kScanT / 32];
     __shared__ Run2 s_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    TextAt at{false, 0, 0};  // the text starts at a line start: the entry state does not matter
+    // entered inside a header only when the chunk before ended inside one
+    TextAt at{p.cin != nullptr && p.cin->hstate == HS_HD, 0, 0};
     for (long long base = 0; base < p.n_ctas; base += kScanTile) {
 #pragma unroll
         for (int j = 0; j < kScanPer; ++j) {
@@ -364,24 +455,7 @@ __global__ void __launch_bounds__(kScanT) fasta_scan_kernel(FastaParams p) {
         at = text_then(at, s_total);
         __syncthreads();  // tile_s, wsum and s_total are reused by the next tile
     }
-    if (tid == 0) {
-        // totals: the kept bytes and the records (an implicit first record
-        // when byte 0 is not '>')
-        const long long implicit = (p.bytes[0] != '>') ? 1 : 0;
-        const long long n_rec = at.heads + implicit;
-        if (n_rec + 1 > p.cso_cap || n_rec > kMaxRecords) {
-            // more records than the direct path takes: the general kernel
-            // runs on the FASTA text instead
-            p.tot[0] = 0;
-            p.tot[1] = 0;
-            *(volatile unsigned *)p.gate = p.epoch;
-        } else {
-            p.tot[0] = at.kept;
-            p.tot[1] = n_rec;
-            if (implicit) p.cso[0] = 0;
-            p.cso[n_rec] = at.kept;
-        }
-    }
+    if (tid == 0) scan_totals(p, at);
 }
 
 // The 16 bytes of w with the bytes of `keep` packed to the front (the bytes
@@ -436,14 +510,14 @@ __global__ void __launch_bounds__(kFT, 4) fasta_emit_kernel(FastaParams p) {
     const long long span = (long long)blockIdx.x * kFWarps + warp;
     if (span >= p.n_spans) return;  // warp-level work only: no block barrier below
     const long long s0 = span * kFSpan;
-    // four rounds in flight: a ring of registers shifted by one each round
+    // three rounds in flight: a ring of registers shifted by one each round
     auto load = [&](int r) {
         const long long ab = s0 + r * 512 + 16 * lane;
         uint4 x = make_uint4(0u, 0u, 0u, 0u);
         if (r < kFRounds && ab < p.n) x = __ldg(reinterpret_cast<const uint4 *>(p.bytes + ab));
         return x;
     };
-    uint4 w0 = load(0), w1 = load(1), w2 = load(2), w3 = load(3);
+    uint4 w0 = load(0), w1 = load(1), w2 = load(2);
     unsigned *const wb = win[warp];
     for (int i = lane; i < kWinWords; i += 32) wb[i] = 0u;
     // this span's incoming state: the CTA's, then the CTA's spans before it
@@ -465,9 +539,7 @@ __global__ void __launch_bounds__(kFT, 4) fasta_emit_kernel(FastaParams p) {
     const long long o_begin = at.kept;  // the span's first kept byte
     long long o_cur = at.kept;          // kept offset at the round's start
     bool hd = at.hd;
-    const long long n_rec = p.tot[1];
-    const long long implicit = (p.bytes[0] != '>') ? 1 : 0;
-    long long rec = implicit + at.heads;
+    long long rec = p.info[I_REC0] + at.heads;
     unsigned carry_nl = line_start_at(p, s0);
     __syncwarp();
 #pragma unroll 1
@@ -475,8 +547,7 @@ __global__ void __launch_bounds__(kFT, 4) fasta_emit_kernel(FastaParams p) {
         const uint4 wr = w0;
         w0 = w1;
         w1 = w2;
-        w2 = w3;
-        w3 = load(r + 4);
+        w2 = load(r + 3);
         const long long ab = s0 + r * 512 + 16 * lane;
         const unsigned valid = f_valid(ab, p.n);
         Vec v;
@@ -493,13 +564,26 @@ __global__ void __launch_bounds__(kFT, 4) fasta_emit_kernel(FastaParams p) {
         const long long o_end = o_cur + __shfl_sync(kFull, cinc, 31);
         if (__ballot_sync(kFull, v.H != 0u)) {
             // record starts: each header's position among the kept bytes
+            // (after the carried symbols); the counts are read here, in this
+            // rare branch, to keep them out of the loop's registers
+            const long long n_rec = p.info[I_NREC], m = p.info[I_M];
             const unsigned nh = __popc(v.H);
             const unsigned hinc = warp_sum_incl(nh, lane);
             long long ri = rec + (hinc - nh);
             for (unsigned hh = v.H; hh; hh &= hh - 1u, ++ri) {
                 const int h = __ffs(hh) - 1;
-                if (ri < p.cso_cap && ri < n_rec)
-                    p.cso[ri] = o_lane + __popc(keep & ((1u << h) - 1u));
+                const long long pos = m + o_lane + __popc(keep & ((1u << h) - 1u));
+                if (ri < n_rec) p.cso[ri] = pos;
+                if (ri == n_rec - 1 && !p.end_boundary) {
+                    // the open last record: its whole k-mers only
+                    const long long cut = pos + (p.info[I_END] - pos) / p.k * p.k;
+                    if (cut == 0) {
+                        *(volatile unsigned *)p.gate = p.epoch;
+                    } else {
+                        p.info[I_N] = cut;
+                        p.cso[n_rec] = cut;
+                    }
+                }
             }
             rec += __shfl_sync(kFull, hinc, 31);
         }
@@ -524,12 +608,12 @@ __global__ void __launch_bounds__(kFT, 4) fasta_emit_kernel(FastaParams p) {
             const long long ga = wbase + 16 * i;
             const uint4 val = reinterpret_cast<const uint4 *>(wb)[i];
             if (ga >= o_begin) {
-                *reinterpret_cast<uint4 *>(p.cbytes + ga) = val;
+                *reinterpret_cast<uint4 *>(p.cbytes + kHead + ga) = val;
             } else {
                 const unsigned long long lo = ((unsigned long long)val.y << 32) | val.x;
                 const unsigned long long hi = ((unsigned long long)val.w << 32) | val.z;
                 for (int j = (int)(o_begin - ga); j < 16; ++j)
-                    p.cbytes[ga + j] = (uint8_t)((j < 8) ? (lo >> (8 * j)) : (hi >> (8 * (j - 8))));
+                    p.cbytes[kHead + ga + j] = (uint8_t)((j < 8) ? (lo >> (8 * j)) : (hi >> (8 * (j - 8))));
             }
         }
         // the partial piece to the front, the rest cleared
@@ -547,8 +631,56 @@ __global__ void __launch_bounds__(kFT, 4) fasta_emit_kernel(FastaParams p) {
     if (lane < 16) {
         const long long ga = wbase + lane;
         if (ga < o_cur && ga >= o_begin)
-            p.cbytes[ga] = (uint8_t)(wb[lane >> 2] >> (8 * (lane & 3)));
+            p.cbytes[kHead + ga] = (uint8_t)(wb[lane >> 2] >> (8 * (lane & 3)));
     }
+}
+
+// Stream chunks, after the direct kernels (one block): each record that
+// starts in the chunk gets its first id written at its global boundary index
+// (and the end boundary its total when the text ends here); the running
+// totals; and the scan state after the chunk in the general kernel's form
+// (boundaries, ids, the open record's symbols and their last k - 1 codes,
+// the line state), so that either path can take the next chunk.  Nothing
+// when the direct path declined the chunk: the general kernel behind writes
+// all of it.
+__global__ void __launch_bounds__(256) fasta_finish_kernel(FastaParams p, const long long *plan,
+                                                           long long *offsets, long long offsets_cap,
+                                                           long long *totals, Carry *cout) {
+    if (*(volatile const unsigned *)p.gate == p.epoch) return;
+    const long long n_rec = p.info[I_NREC], cont = p.info[I_CONT], g0 = p.info[I_G0];
+    for (long long r = cont + threadIdx.x; r < n_rec; r += blockDim.x) {
+        const long long g = g0 + r - cont;
+        if (g < offsets_cap) offsets[g] = plan[r];
+    }
+    if (threadIdx.x != 0) return;
+    const long long d_total = plan[n_rec];
+    const long long nb = g0 + (n_rec - cont) + (p.end_boundary ? 1 : 0);
+    if (p.end_boundary && nb - 1 < offsets_cap) offsets[nb - 1] = d_total;
+    if (totals) {
+        totals[0] = d_total;
+        totals[1] = nb > 0 ? nb - 1 : 0;
+    }
+    if (!cout) return;
+    const long long end = p.info[I_END], m = p.info[I_M];
+    const bool cont_last = cont && n_rec == 1;  // the last record is the continued one
+    const long long s_last = p.cso[n_rec - 1];
+    Carry c;
+    c.a.nb = nb;
+    c.a.h = 0;
+    c.a.d = d_total;
+    c.a.t = cont_last ? p.cin->a.t + (end - m) : end - s_last;
+    // the last k - 1 symbols: this chunk's (for the continued record, its
+    // new ones only), after the earlier ones when the record continues
+    const uint8_t *sym = p.cbytes + kHead - m;
+    long long from = cont_last ? m : s_last;
+    if (end - from > p.k - 1) from = end - (p.k - 1);
+    unsigned long long bits = 0ull;
+    for (long long i = from; i < end; ++i) bits = (bits << 3) | sym_code(sym[i]);
+    const unsigned long long mine = ((unsigned long long)(end - from) << 58) | bits;
+    c.a.codes = cont_last ? codes_concat(p.cin->a.codes, mine, p.k) : mine;
+    c.hstate = (unsigned)p.info[I_HSTATE];
+    c.pad = 0u;
+    *cout = c;
 }
 
 }  // namespace
@@ -560,7 +692,8 @@ void fasta_destroy(dnatok_handle *h) {
     cudaFree(h->fasta->ssum);
     cudaFree(h->fasta->csum);
     cudaFree(h->fasta->sin);
-    cudaFree(h->fasta->tot);
+    cudaFree(h->fasta->info);
+    cudaFree(h->fasta->plan);
     delete h->fasta;
     h->fasta = nullptr;
 }
@@ -576,7 +709,7 @@ dnatok_status fasta_reserve(dnatok_handle *h, long long n_bytes, long long offse
     long long cso_need = offsets_cap < kMaxRecords + 1 ? offsets_cap : kMaxRecords + 1;
     if (cso_need < 1) cso_need = 1;
     const bool grow = n_bytes + 64 > f.cbytes_cap || spans > f.spans_cap ||
-                      cso_need > f.cso_cap || !f.tot;
+                      cso_need > f.cso_cap || !f.info;
     if (!grow) return DNATOK_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
@@ -618,9 +751,10 @@ dnatok_status fasta_reserve(dnatok_handle *h, long long n_bytes, long long offse
         if (e != cudaSuccess) return fail_cuda(h, e, "cudaMalloc(FASTA record starts)");
         f.cso_cap = cso_need;
     }
-    if (!f.tot) {
-        e = cudaMalloc(&f.tot, 2 * sizeof(long long));
-        if (e != cudaSuccess) return fail_cuda(h, e, "cudaMalloc(FASTA totals)");
+    if (!f.info) {
+        e = cudaMalloc(&f.info, kInfo * sizeof(long long));
+        if (e == cudaSuccess) e = cudaMalloc(&f.plan, (kMaxRecords + 2) * sizeof(long long));
+        if (e != cudaSuccess) return fail_cuda(h, e, "cudaMalloc(FASTA counts)");
     }
     return DNATOK_OK;
 }
@@ -636,13 +770,22 @@ bool fasta_direct_eligible(const dnatok_handle *h, int mode, int k, const uint8_
 
 // FASTA text -> kept bytes and record starts (three kernels), then the direct
 // k-mer kernels over them with their byte and record counts read on the
-// device.  When the records do not fit (the id offsets' capacity, or more
-// than the plan takes) the scan raises the gate instead and every later
-// kernel of the direct path returns at once.
+// device.  A one-shot encode (no carries) has its id offsets and totals
+// written by the direct plan; a stream chunk (a carry in, or the stream's
+// first chunk with a carry out) continues the open record of the chunk
+// before and has them written by the finish kernel, which also writes the
+// carry out.  When the direct path cannot take the text (the id offsets'
+// capacity, more records than the plan takes, nothing to encode) the scan
+// raises the gate instead and every later kernel of the direct path returns
+// at once.
 dnatok_status fasta_direct(dnatok_handle *h, const uint8_t *bytes, long long n, void *out,
-                           long long *offsets_out, long long offsets_cap, long long *totals_out,
-                           unsigned epoch, int k, cudaStream_t s) {
-    dnatok_status st = fasta_reserve(h, n, offsets_cap, s);
+                           long long out_cap, long long *offsets_out, long long offsets_cap,
+                           long long *totals_out, const Carry *carry_in, Carry *carry_out,
+                           int start_boundary, int end_boundary, unsigned epoch, int k,
+                           cudaStream_t s) {
+    (void)start_boundary;  // implied: a stream's first chunk has no carry in
+    const bool stream = carry_in || carry_out;
+    dnatok_status st = fasta_reserve(h, n, stream ? kMaxRecords + 1 : offsets_cap, s);
     if (st != DNATOK_OK) return st;
     FastaState &f = *h->fasta;
     FastaParams p;
@@ -651,12 +794,15 @@ dnatok_status fasta_direct(dnatok_handle *h, const uint8_t *bytes, long long n, 
     p.n_spans = (n + kFSpan - 1) / kFSpan;
     p.cbytes = f.cbytes;
     p.cso = f.cso;
-    p.cso_cap = offsets_cap < f.cso_cap ? offsets_cap : f.cso_cap;
+    p.cso_cap = (stream || offsets_cap > f.cso_cap) ? f.cso_cap : offsets_cap;
     p.n_ctas = (p.n_spans + kFWarps - 1) / kFWarps;
     p.ssum = f.ssum;
     p.csum = f.csum;
     p.sin = f.sin;
-    p.tot = f.tot;
+    p.info = f.info;
+    p.cin = carry_in;
+    p.k = k;
+    p.end_boundary = end_boundary;
     p.gate = h->d_gate;
     p.epoch = epoch;
     const unsigned grid = (unsigned)p.n_ctas;
@@ -665,10 +811,18 @@ dnatok_status fasta_direct(dnatok_handle *h, const uint8_t *bytes, long long n, 
     fasta_emit_kernel<<<grid, kFT, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "FASTA compaction launch");
-    // n bytes and kMaxRecords records bound the device-side counts
-    e = launch_direct(MODE_KMER, f.cbytes, n, f.cso, kMaxRecords, out, offsets_out, totals_out,
-                      h->d_gate, epoch, k, h->d_lut, h->sm_count, h->dshape, s, f.tot);
+    // the kept bytes begin kHead - I_M bytes into the buffer: n + 32 bytes
+    // and kMaxRecords records bound the device-side counts
+    e = launch_direct(MODE_KMER, f.cbytes, n + 2 * kHead, f.cso, kMaxRecords, out,
+                      stream ? f.plan : offsets_out, stream ? nullptr : totals_out, h->d_gate,
+                      epoch, k, h->d_lut, h->sm_count, h->dshape, s, f.info, out_cap);
     if (e != cudaSuccess) return fail_cuda(h, e, "direct kernel launch");
+    if (stream) {
+        fasta_finish_kernel<<<1, 256, 0, s>>>(p, f.plan, offsets_out, offsets_cap, totals_out,
+                                              carry_out);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail_cuda(h, e, "FASTA finish launch");
+    }
     return DNATOK_OK;
 }
 

@@ -108,7 +108,8 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                           long long n_seq, void *out, long long *offsets_out,
                           long long *totals_out, unsigned *gate, unsigned epoch, int k,
                           const int *lut, int sm_count, const DirectShape &shape,
-                          cudaStream_t s, const long long *dyn = nullptr);
+                          cudaStream_t s, const long long *dyn = nullptr,
+                          long long out_cap = 0x7fffffffffffffffll);
 
 void fasta_destroy(dnatok_handle *h);
 dnatok_status fasta_reserve(dnatok_handle *h, long long n_bytes, long long offsets_cap,
@@ -116,8 +117,10 @@ dnatok_status fasta_reserve(dnatok_handle *h, long long n_bytes, long long offse
 bool fasta_direct_eligible(const dnatok_handle *h, int mode, int k, const uint8_t *bytes,
                            long long n);
 dnatok_status fasta_direct(dnatok_handle *h, const uint8_t *bytes, long long n, void *out,
-                           long long *offsets_out, long long offsets_cap, long long *totals_out,
-                           unsigned epoch, int k, cudaStream_t s);
+                           long long out_cap, long long *offsets_out, long long offsets_cap,
+                           long long *totals_out, const Carry *carry_in, Carry *carry_out,
+                           int start_boundary, int end_boundary, unsigned epoch, int k,
+                           cudaStream_t s);
 
 // BPE path (bpe.cu)
 dnatok_status bpe_create(dnatok_handle *h, const int32_t *merges, int32_t n_merges);

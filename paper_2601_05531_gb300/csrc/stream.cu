@@ -6,6 +6,8 @@
 // Each submitted piece is cut into chunks.  Chunk i goes to device slot
 // i % n_slots: its H2D copy waits (on the copy stream) for the kernel that
 // last read the slot; its kernel waits (on the compute stream) for the copy.
+// FASTA k-mer chunks of 64 KiB and more take the compacted path (fasta.cu),
+// the others the general kernel; both read and write the same carry.
 // Kernels run in stream order and pass the scan state through a two-entry
 // device carry (chunk i reads carry[i & 1] and writes carry[(i + 1) & 1]), so
 // the ids and offsets land at their global positions exactly as one
@@ -189,6 +191,8 @@ dnatok_status dnatok_stream_open(dnatok_handle *h, const dnatok_stream_cfg *cfg,
     st->n_slots = slots;
     st->overlap = overlap;
     dnatok_status r = ensure_workspace(h, chunk, 0, h->shape, 0);
+    if (r == DNATOK_OK && h->fmt == DNATOK_FASTA && h->mode == DNATOK_KMER && h->k >= 2)
+        r = fasta_reserve(h, chunk, 1ll << 40, 0);  // the compacted path's workspace, up front
     if (r != DNATOK_OK) {
         stream_destroy(h);
         return r;
