@@ -1101,6 +1101,20 @@ def run_gpu(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     assert int(h_tot[0]) == n_ids
 
+    # the dominant kernel's own duration: the same plain step with CUDA events
+    # recorded by the library right before and after the direct k-mer kernel
+    # (its launch then waits for the record plan instead of starting under it)
+    binding.dnatok_set_kernel_timing(tok.h, True)
+    kern_ms = []
+    for i in range(args.steps + 2):
+        flush_l2(i)
+        plain_step()
+        ms = binding.dnatok_kernel_time_ms(tok.h, stream.cuda_stream)
+        if i >= 2:
+            kern_ms.append(ms)
+    binding.dnatok_set_kernel_timing(tok.h, False)
+    tok.sync()
+
     sharding = None
     if ws > 1:
         # the one exchange of the sharded path: global id offsets
@@ -1123,6 +1137,8 @@ def run_gpu(args):
         achieved = alg_bytes / mean_s / 1e9
         plain_mean = statistics.mean(plain_ms) / 1e3
         traffic = _traffic(n_bytes)
+        kern_mean = statistics.mean(kern_ms)
+        kern_achieved = alg_bytes / (kern_mean / 1e3) / 1e9
         line = {
             "metric": METRIC,
             "value": job_ids * args.steps / (total_ms / 1e3),
@@ -1148,12 +1164,21 @@ def run_gpu(args):
                        "parallelism": ("record shards x%d (dnatok_shard_records over %d "
                                        "copies of the batch)" % (ws, ws)) if ws > 1
                        else "one GPU"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
+            "roofline": {"bound": "hbm", "achieved": kern_achieved, "peak": peak,
+                         "unit": "GB/s", "frac": kern_achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": KERNEL,
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "duration": "CUDA events around the whole graph replay (every "
-                                     "launch of the step)"},
+                         "duration_ms": kern_mean,
+                         "duration": "mean over %d steps of CUDA events recorded on the "
+                                     "launching stream right before and after the direct "
+                                     "k-mer kernel, L2 flushed before each step" % len(kern_ms)},
+            "roofline_step": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                              "unit": "GB/s", "frac": achieved / peak,
+                              "peak_kind": peak_kind,
+                              "algorithmic_bytes_per_step": alg_bytes,
+                              "duration": "CUDA events around the whole graph replay (every "
+                                          "launch of the step: plan, direct kernel, gated "
+                                          "general kernel)"},
             "plain_launch": {"ms_per_step": 1e3 * plain_mean,
                              "p50_ms": statistics.median(plain_ms),
                              "tokens_per_s": n_ids / plain_mean,

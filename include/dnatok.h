@@ -588,6 +588,19 @@ DNATOK_API dnatok_status dnatok_direct_ran(dnatok_handle *h, dnatok_cuda_stream 
  * hold the GPU; tests lower it to see the timeout come back quickly. */
 DNATOK_API dnatok_status dnatok_set_wait_limit(dnatok_handle *h, int64_t polls);
 
+/* Kernel timing, for measurement: with enable != 0, every later one-shot
+ * encode that runs the direct k-mer kernel (RAW input without separators,
+ * k >= 2, not under stream capture) records two CUDA events on its stream,
+ * right before and right after that kernel's launch; the kernel then waits
+ * for the record plan to finish instead of starting under it.
+ * dnatok_kernel_time_ms waits for `stream` and sets *ms to the time between
+ * the two events of the last such encode on this handle, or to -1 when there
+ * was none since timing was switched on.  0 switches it off (the default).
+ * (No counterpart in the paper: a measurement aid.) */
+DNATOK_API dnatok_status dnatok_set_kernel_timing(dnatok_handle *h, int32_t enable);
+DNATOK_API dnatok_status dnatok_kernel_time_ms(dnatok_handle *h, dnatok_cuda_stream stream,
+                                               float *ms);
+
 /* Fault injection, for testing the bounded waits: the next launch of the
  * general kernel on this handle leaves look-back chunk `chunk` (chunks of
  * tiles_per_chunk x tile_bytes input bytes, counted from 0) unprocessed, so

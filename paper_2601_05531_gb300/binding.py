@@ -117,6 +117,8 @@ def lib():
             "dnatok_set_bpe_launch": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
             "dnatok_set_direct": (_ST, [_P, ctypes.c_int32]),
             "dnatok_direct_ran": (_ST, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
+            "dnatok_set_kernel_timing": (_ST, [_P, ctypes.c_int32]),
+            "dnatok_kernel_time_ms": (_ST, [_P, _P, ctypes.POINTER(ctypes.c_float)]),
             "dnatok_get_bpe_launch": (_ST, [_P, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
             "dnatok_bpe_stats": (_ST, [_P, ctypes.POINTER(_I64), _P]),
@@ -290,6 +292,16 @@ def dnatok_set_direct(h, enable: bool) -> None:
 def dnatok_direct_ran(h, stream=0) -> int:
     out = ctypes.c_int32(0)
     check(lib().dnatok_direct_ran(h, stream, ctypes.byref(out)), h)
+    return out.value
+
+
+def dnatok_set_kernel_timing(h, enable: bool) -> None:
+    check(lib().dnatok_set_kernel_timing(h, int(bool(enable))), h)
+
+
+def dnatok_kernel_time_ms(h, stream=0) -> float:
+    out = ctypes.c_float(0.0)
+    check(lib().dnatok_kernel_time_ms(h, stream, ctypes.byref(out)), h)
     return out.value
 
 

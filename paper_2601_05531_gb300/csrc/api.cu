@@ -142,8 +142,12 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
         // under stream capture the epochs are baked into the graph: a replay
         // whose general kernel ran clears the switch and its descriptors at
         // its end (clear_gate), so the next replay starts clean
+        const bool timed = h->ktime_on && mode == MODE_KMER && k >= 2 && !capturing;
         e = launch_direct(mode, bytes, n_bytes, seq_offsets, n_bnd - 1, out, offsets_out,
-                          totals_out, h->d_gate, ep, k, h->d_lut, h->sm_count, h->dshape, s);
+                          totals_out, h->d_gate, ep, k, h->d_lut, h->sm_count, h->dshape, s,
+                          nullptr, 0x7fffffffffffffffll, timed ? h->ktime[0] : nullptr,
+                          timed ? h->ktime[1] : nullptr);
+        if (timed && e == cudaSuccess) h->ktime_valid = true;
         if (e != cudaSuccess) return fail_cuda(h, e, "direct kernel launch");
         p.gate = h->d_gate;
         p.gate_epoch = ep;
@@ -292,6 +296,8 @@ void dnatok_destroy(dnatok_handle *h) {
     bpe_destroy(h);
     ovl_destroy(h);
     fasta_destroy(h);
+    for (cudaEvent_t ev : h->ktime)
+        if (ev) cudaEventDestroy(ev);
     dec_destroy(h);
     cudaFree(h->d_klut);
     cudaFree(h->d_klut16);
@@ -517,6 +523,29 @@ dnatok_status dnatok_direct_ran(dnatok_handle *h, dnatok_cuda_stream stream, int
     e = cudaMemcpy(&g, h->d_gate, sizeof(g), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemcpy(gate)");
     *out = (g == h->direct_epoch) ? 0 : 1;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_set_kernel_timing(dnatok_handle *h, int32_t enable) {
+    if (!h) return DNATOK_ERR_ARG;
+    if (enable && !h->ktime[0]) {
+        cudaError_t e = cudaEventCreate(&h->ktime[0]);
+        if (e == cudaSuccess) e = cudaEventCreate(&h->ktime[1]);
+        if (e != cudaSuccess) return fail_cuda(h, e, "cudaEventCreate");
+    }
+    h->ktime_on = enable != 0;
+    h->ktime_valid = false;
+    return DNATOK_OK;
+}
+
+dnatok_status dnatok_kernel_time_ms(dnatok_handle *h, dnatok_cuda_stream stream, float *ms) {
+    if (!h || !ms) return DNATOK_ERR_ARG;
+    *ms = -1.0f;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaStreamSynchronize");
+    if (!h->ktime_valid) return DNATOK_OK;
+    e = cudaEventElapsedTime(ms, h->ktime[0], h->ktime[1]);
+    if (e != cudaSuccess) return fail_cuda(h, e, "cudaEventElapsedTime");
     return DNATOK_OK;
 }
 

@@ -873,7 +873,8 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                           long long n_seq, void *out, long long *offsets_out,
                           long long *totals_out, unsigned *gate, unsigned epoch, int k,
                           const int *lut, int sm_count, const DirectShape &shape,
-                          cudaStream_t s, const long long *dyn, long long out_cap) {
+                          cudaStream_t s, const long long *dyn, long long out_cap,
+                          cudaEvent_t ev0, cudaEvent_t ev1) {
     DirectParams q;
     q.dyn = dyn;
     q.d_base = 0;
@@ -931,9 +932,14 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
         const long long need = (steps + kSWarps - 1) / kSWarps;
         if (grid > need) grid = need;
         cfg.gridDim = dim3((unsigned)grid);
-        if (kv == 1 && kr == 8) return launch_kmer_kv<1, 8>(k, cfg, q);
-        if (kv == 4 && kr == 2) return launch_kmer_kv<4, 2>(k, cfg, q);
-        return launch_kmer_kv<2, 4>(k, cfg, q);
+        cudaError_t e = cudaSuccess;
+        if (ev0) e = cudaEventRecord(ev0, s);  // timing: the kernel then waits for the plan
+        if (e != cudaSuccess) return e;
+        if (kv == 1 && kr == 8) e = launch_kmer_kv<1, 8>(k, cfg, q);
+        else if (kv == 4 && kr == 2) e = launch_kmer_kv<4, 2>(k, cfg, q);
+        else e = launch_kmer_kv<2, 4>(k, cfg, q);
+        if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+        return e;
     }
     return cudaGetLastError();
 }

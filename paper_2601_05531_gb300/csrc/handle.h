@@ -41,6 +41,10 @@ struct dnatok_handle {
     dnatok::LaunchShape shape{16384, 256, 4, 8};
     dnatok::DirectShape dshape{2, 4, 0};  // direct k-mer kernel (dnatok_set_direct_launch)
     unsigned direct_epoch = 0;  // the epoch of the last encode that tried the direct path, or 0
+    // dnatok_set_kernel_timing: events around the direct k-mer kernel
+    cudaEvent_t ktime[2] = {nullptr, nullptr};
+    bool ktime_on = false;
+    bool ktime_valid = false;  // the events hold the last such launch
     bool direct = true;  // try the direct path on RAW input (dnatok_set_direct)  // tile, threads, CTAs per SM, tiles per chunk
 
     // device staging of dnatok_encode_host
@@ -109,7 +113,8 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                           long long *totals_out, unsigned *gate, unsigned epoch, int k,
                           const int *lut, int sm_count, const DirectShape &shape,
                           cudaStream_t s, const long long *dyn = nullptr,
-                          long long out_cap = 0x7fffffffffffffffll);
+                          long long out_cap = 0x7fffffffffffffffll,
+                          cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 
 void fasta_destroy(dnatok_handle *h);
 dnatok_status fasta_reserve(dnatok_handle *h, long long n_bytes, long long offsets_cap,
