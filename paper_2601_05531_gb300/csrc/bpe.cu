@@ -97,8 +97,9 @@ struct BpeWork {
 
 // ---------------------------------------------------------------- helpers
 
+// (token ids are below 0xFFFF, so a * V + b fits in 32 bits)
 __device__ __forceinline__ bool compat_bit(const unsigned *compat, int V, unsigned a, unsigned b) {
-    const unsigned long long bit = (unsigned long long)a * (unsigned)V + b;
+    const unsigned bit = a * (unsigned)V + b;
     return (__ldg(compat + (bit >> 5)) >> (bit & 31)) & 1u;
 }
 
@@ -142,7 +143,7 @@ struct DpPass {
 // token before it.  The single base at the end of every list is taken
 // without a check (no other candidate fits).  Returns (length << 16) | token.
 template <int R, int NT, bool SM>
-__device__ __forceinline__ unsigned dp_step(const BpeTables &T, DpPass &P, long long j, unsigned c) {
+__device__ __forceinline__ unsigned dp_step(const BpeTables &T, DpPass &P, unsigned j, unsigned c) {
     P.state = node_next(P.nd, c);
     P.nd = node_at<SM>(T, P.state);
     if (P.wd < 63) ++P.wd;
@@ -306,48 +307,52 @@ __device__ void seg_pass(const BpeTables &T, const BpeWork &W, long long seg, lo
     const unsigned N_ID = (unsigned)T.V;
     for (long long j0 = j_begin & ~15ll; j0 < e; j0 += 16) {
         const uint4 sv = *reinterpret_cast<const uint4 *>(W.sym + j0);
-        const unsigned long long s_lo = ((unsigned long long)sv.y << 32) | sv.x;
-        const unsigned long long s_hi = ((unsigned long long)sv.w << 32) | sv.z;
         // four values per 64-bit word; 0xFFFF: no value
         unsigned long long o0 = ~0ull, o1 = ~0ull, o2 = ~0ull, o3 = ~0ull;
         const int q0 = (j0 < j_begin) ? (int)(j_begin - j0) : 0;
         const int q1 = (e - j0 < 16) ? (int)(e - j0) : 16;
+        // groups of four symbols: inside a group the shifts are constants
 #pragma unroll 1
-        for (int q = q0; q < q1; ++q) {
-            const long long j = j0 + q;
-            while (j == next_b) {
-                dp_reset<SM>(T, P);
-                ++r;
-                next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
-                if (j < s) exact = true;  // a record starts in the halo
+        for (int g = q0 >> 2; g < 4 && 4 * g < q1; ++g) {
+            const unsigned wg = g == 0 ? sv.x : g == 1 ? sv.y : g == 2 ? sv.z : sv.w;
+            unsigned long long grp = ~0ull;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const int q = 4 * g + qq;
+                if (q < q0 || q >= q1) continue;
+                const long long j = j0 + q;
+                while (j == next_b) {
+                    dp_reset<SM>(T, P);
+                    ++r;
+                    next_b = (r + 1 < nb) ? W.rec_off[r + 1] : (1ll << 62);
+                    if (j < s) exact = true;  // a record starts in the halo
+                }
+                const unsigned c = (wg >> (8 * qq)) & 0xFFu;
+                const unsigned ju = (unsigned)j;  // ring slots: the low bits of j
+                unsigned L, t;
+                if (c >= 4) {
+                    L = 1;
+                    t = N_ID;
+                    dp_reset<SM>(T, P);
+                    if (j < s) exact = true;  // a word starts after it, before the segment
+                } else {
+                    const unsigned pk = dp_step<R, NT, SM>(T, P, ju, c);
+                    L = pk >> 16;
+                    t = pk & 0xFFFFu;
+                }
+                P.ring[(ju & (R - 1)) * NT] = (unsigned short)t;
+                if (j >= s) {
+                    const long long back = j - (long long)L;
+                    const unsigned F = back < s ? ((unsigned)(s - 1 - back) << 24) | 1u
+                                                : ringf[((unsigned)back & (R - 1)) * NT] + 1u;
+                    ringf[(ju & (R - 1)) * NT] = F;
+                }
+                grp = (grp & ~(0xFFFFull << (16 * qq))) | ((unsigned long long)t << (16 * qq));
             }
-            const unsigned c =
-                (unsigned)((q < 8 ? s_lo >> (8 * q) : s_hi >> (8 * (q - 8))) & 0xFFu);
-            unsigned L, t;
-            if (c >= 4) {
-                L = 1;
-                t = N_ID;
-                dp_reset<SM>(T, P);
-                if (j < s) exact = true;  // a word starts after it, before the segment
-            } else {
-                const unsigned pk = dp_step<R, NT, SM>(T, P, j, c);
-                L = pk >> 16;
-                t = pk & 0xFFFFu;
-            }
-            P.ring[(j & (R - 1)) * NT] = (unsigned short)t;
-            if (j >= s) {
-                const long long back = j - (long long)L;
-                const unsigned F = back < s ? ((unsigned)(s - 1 - back) << 24) | 1u
-                                            : ringf[(back & (R - 1)) * NT] + 1u;
-                ringf[(j & (R - 1)) * NT] = F;
-            }
-            const int sh = 16 * (q & 3);
-            const unsigned long long keep = ~(0xFFFFull << sh), v = (unsigned long long)t << sh;
-            const int g = q >> 2;
-            if (g == 0) o0 = (o0 & keep) | v;
-            if (g == 1) o1 = (o1 & keep) | v;
-            if (g == 2) o2 = (o2 & keep) | v;
-            if (g == 3) o3 = (o3 & keep) | v;
+            if (g == 0) o0 = grp;
+            else if (g == 1) o1 = grp;
+            else if (g == 2) o2 = grp;
+            else o3 = grp;
         }
         const uint4 v0 = make_uint4((unsigned)o0, (unsigned)(o0 >> 32), (unsigned)o1,
                                     (unsigned)(o1 >> 32));
