@@ -108,6 +108,9 @@ __global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams 
             }
         }
         __syncthreads();
+        // the list's two ends, from the staged offsets (no second round trip)
+        if (tid == 0 && r0 == 0 && s_v[0] != 0) bad = true;
+        if (tid == 0 && r0 + cnt == n && s_v[cnt] != q.n) bad = true;
         long long t[kPer], sum = 0;
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams 
         carry += tot;
         __syncthreads();  // s_v and wsum are reused by the next pass
     }
-    if (tid == 0 && (__ldg(q.so) != 0 || __ldg(q.so + n) != q.n || carry > q.out_cap)) bad = true;
+    if (tid == 0 && (n == 0 || carry > q.out_cap)) bad = true;
     if (__syncthreads_or(bad)) {
         if (tid == 0) raise_gate(q);
         return;

@@ -180,107 +180,106 @@ __global__ void __launch_bounds__(kOPlanThreads) offsets_kernel(long long *offs,
     }
 }
 
-// Ids of overlapping k-mers, one tile of 4096 symbols at a time (a
-// contiguous run of tiles per CTA).  Phase 1: each thread slides a 2-bit
-// register window over 16 consecutive staged symbols (plus k - 1 of
-// lookahead), remembering where the last N-class symbol was, and writes the
-// 16 ids to shared memory (rows of 17 ints, so neighbouring threads hit
-// different banks).  Phase 2 walks the records overlapping the tile; the
-// starts of each that have a token (j + k <= record end) are a contiguous
-// run with contiguous output slots, which consecutive threads copy.
+// Overlapping k-mer ids, warp by warp (no block barrier): each warp takes a
+// contiguous run of 512-symbol tiles.  Per tile a lane loads its 16 symbols
+// (and the next lane's by shuffle, for the k - 1 symbols a window reaches
+// past them), slides a 2-bit window over them remembering the last N-class
+// symbol, and writes its 16 ids to the warp's rows in shared memory (17 ints
+// per row, so neighbouring lanes hit different banks).  The starts of a record
+// that have a token (j + k <= record end) are contiguous with contiguous
+// output slots: when the whole tile is such a run the warp writes it as 16
+// rows of 32 consecutive ids (every store a full 128-byte line whatever the
+// alignment), otherwise record by record.  A register cursor follows the
+// records from tile to tile.
+constexpr int kOWT = 512;  // symbols per warp tile
+
 template <int K>
 __global__ void __launch_bounds__(kOThreads) ovl_emit_kernel(const uint8_t *sym, const long long *srec,
                                                              const long long *offs, const long long *tot,
                                                              int *out, long long ids_cap) {
     constexpr unsigned UNK = 1u << (2 * K);
     constexpr unsigned MASK = UNK - 1u;
-    constexpr int kPer = kOT / kOThreads;  // 16 starts per thread in phase 1
-    __shared__ __align__(16) uint8_t s_sym[kOT + 32];
-    __shared__ int s_id[kOThreads * (kPer + 1)];
-    __shared__ long long s_rs[kORW + 1], s_ob[kORW];
-    __shared__ long long s_rb;
-    __shared__ int s_nw;
-    const int tid = threadIdx.x;
+    constexpr int kW = kOThreads / 32;
+    __shared__ int s_id[kW][32 * 17];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long n_sym = tot[0], n_rec = tot[1];
     if (n_rec < 1 || n_sym < 1) return;
-    const long long n_tiles = (n_sym + kOT - 1) / kOT;
-    const long long t_begin = (long long)blockIdx.x * n_tiles / gridDim.x;
-    const long long t_end = (long long)(blockIdx.x + 1) * n_tiles / gridDim.x;
-    for (long long tile = t_begin; tile < t_end; ++tile) {
-        const long long j0 = tile * kOT;
-        const long long j1 = (j0 + kOT < n_sym) ? j0 + kOT : n_sym;
-        const long long jh = (j1 + K - 1 < n_sym) ? j1 + K - 1 : n_sym;
-        stage_symbols(s_sym, sym, j0, jh - j0, tid, kOThreads);  // (j0 is a multiple of 4096)
-        if (tid == 0) {
-            // the record holding j0: from the last tile's window when it is there
-            long long rb;
-            if (tile > t_begin && s_rs[0] <= j0 && (s_rb + s_nw >= n_rec || s_rs[s_nw] > j0)) {
-                int i = 0;
-                while (i + 1 < s_nw && s_rs[i + 1] <= j0) ++i;
-                rb = s_rb + i;
-            } else {
-                rb = ovl_find(srec, n_rec, j0);
-            }
-            s_rb = rb;
-            s_nw = (n_rec - rb < kORW) ? (int)(n_rec - rb) : kORW;
-        }
-        __syncthreads();
-        const long long rb = s_rb;
-        const int nw = s_nw;
-        for (int l = tid; l <= nw; l += kOThreads) {
-            s_rs[l] = srec[rb + l];
-            if (l < nw) s_ob[l] = offs[rb + l];
-        }
-        // phase 1: ids of starts j0 + 16 tid .. + 15 (bytes past the staged
-        // symbols only reach starts that phase 2 never writes)
+    const long long n_wt = (n_sym + kOWT - 1) / kOWT;
+    const long long nw = (long long)gridDim.x * kW, gw = (long long)blockIdx.x * kW + warp;
+    const long long t_begin = gw * n_wt / nw, t_end = (gw + 1) * n_wt / nw;
+    if (t_begin >= t_end) return;
+    int *const rows = s_id[warp];
+    // the record cursor: r holds symbol rs .. re - 1, its first id at ob
+    long long r = ovl_find(srec, n_rec, t_begin * kOWT);
+    long long rs = srec[r], re = srec[r + 1], ob = offs[r];
+    // the symbol buffer has spare bytes past the last tile: every load below
+    // stays inside it; the next tile's vector is loaded one tile ahead, and its
+    // lane 0 gives lane 31 the symbols past this tile
+    uint4 vn = *reinterpret_cast<const uint4 *>(sym + t_begin * kOWT + 16 * lane);
+    for (long long t = t_begin; t < t_end; ++t) {
+        const long long j0 = t * kOWT;
+        const uint4 v = vn;
+        vn = *reinterpret_cast<const uint4 *>(sym + j0 + kOWT + 16 * lane);
+        uint4 nx, n0;
+        nx.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+        nx.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+        nx.z = __shfl_down_sync(0xffffffffu, v.z, 1);
+        nx.w = __shfl_down_sync(0xffffffffu, v.w, 1);
+        n0.x = __shfl_sync(0xffffffffu, vn.x, 0);
+        n0.y = __shfl_sync(0xffffffffu, vn.y, 0);
+        n0.z = __shfl_sync(0xffffffffu, vn.z, 0);
+        n0.w = __shfl_sync(0xffffffffu, vn.w, 0);
+        if (lane == 31) nx = n0;
         {
-            const uint4 a = *reinterpret_cast<const uint4 *>(s_sym + kPer * tid);
-            const uint4 b = *reinterpret_cast<const uint4 *>(s_sym + kPer * tid + 16);
-            const unsigned wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            const unsigned wd[8] = {v.x, v.y, v.z, v.w, nx.x, nx.y, nx.z, nx.w};
             unsigned id = 0;
             int last_n = -1000;  // position of the last N-class symbol
-            int *row = s_id + tid * (kPer + 1);
+            int *row = rows + lane * 17;
 #pragma unroll
-            for (int p = 0; p < kPer + K - 1; ++p) {
+            for (int p = 0; p < 16 + K - 1; ++p) {
                 const unsigned c = (wd[p >> 2] >> (8 * (p & 3))) & 0xFFu;
                 id = ((id << 2) | (c & 3u)) & MASK;
                 if (c >= 4u) last_n = p;
                 if (p >= K - 1) row[p - (K - 1)] = (last_n > p - K) ? (int)UNK : (int)id;
             }
         }
-        __syncthreads();
-        // phase 2: record by record over the tile; the starts of record r
-        // that have a token are [max(rs, j0), min(re - K + 1, j1)), and they
-        // go to consecutive slots from ob + (start - rs)
-        for (int l = 0;; ++l) {
-            long long rs, re, ob;
-            if (l < nw) {
-                rs = s_rs[l];
-                re = s_rs[l + 1];
-                ob = s_ob[l];
-            } else if (rb + l < n_rec) {  // more records start in this tile than the window holds
-                rs = srec[rb + l];
-                re = srec[rb + l + 1];
-                ob = offs[rb + l];
-            } else {
-                break;
+        __syncwarp();
+        while (re <= j0 && r + 1 < n_rec) {  // (warp-uniform)
+            ++r;
+            rs = re;
+            re = srec[r + 1];
+            ob = offs[r];
+        }
+        if (rs <= j0 && j0 + kOWT + K - 1 <= re && ob + (j0 - rs) + kOWT <= ids_cap) {
+            // the whole tile is one run of starts with tokens
+            int *dst = out + ob + (j0 - rs);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int x = 32 * i + lane;
+                dst[x] = rows[(x >> 4) * 17 + (x & 15)];
             }
-            if (rs >= j1) break;
-            const long long a = rs > j0 ? rs : j0;
-            const long long b = (re - K + 1 < j1) ? re - K + 1 : j1;
-            if (b > a) {
-                const int xa = (int)(a - j0), n = (int)(b - a);
-                const long long oa = ob + (a - rs);  // slot of start a
-                if (oa >= 0 && oa + n <= ids_cap) {
-                    int *dst = out + oa;
-                    for (int y = tid; y < n; y += kOThreads) {
-                        const int x = xa + y;
-                        dst[y] = s_id[(x >> 4) * (kPer + 1) + (x & 15)];
+        } else {
+            // record by record: the starts of record q with a token in this
+            // tile are [max(qs, j0), min(qe - K + 1, j0 + kOWT))
+            long long q = r, qs = rs, qe = re, qb = ob;
+            while (true) {
+                const long long a = qs > j0 ? qs : j0;
+                const long long b = (qe - K + 1 < j0 + kOWT) ? qe - K + 1 : j0 + kOWT;
+                if (b > a) {
+                    const long long oa = qb + (a - qs);
+                    for (long long y = lane; y < b - a; y += 32) {
+                        const int x = (int)(a - j0 + y);
+                        if (oa + y < ids_cap) out[oa + y] = rows[(x >> 4) * 17 + (x & 15)];
                     }
                 }
+                if (qe >= j0 + kOWT || q + 1 >= n_rec) break;
+                ++q;
+                qs = qe;
+                qe = srec[q + 1];
+                qb = offs[q];
             }
         }
-        __syncthreads();  // the tile's shared memory is reused by the next
+        __syncwarp();  // the rows are rewritten by the next tile
     }
 }
 
