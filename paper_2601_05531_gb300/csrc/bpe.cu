@@ -712,26 +712,47 @@ __global__ void __launch_bounds__(kScanThreads) bpe_scan_down(BpeWork W) {
 // loads of tok and stores of ids are coalesced.  Segments longer than
 // kEmitMaxS use emit_walk_kernel, which writes each id as it walks.
 constexpr int kEmitT = 128;
-constexpr int kEmitMaxS = 2048;
+constexpr int kEmitMaxS = 1024;  // the default segment; longer ones take bpe_emit_walk_kernel
 
 __device__ __forceinline__ unsigned pick4(const uint4 &v, int i) {
     return i < 2 ? (i == 0 ? v.x : v.y) : (i == 2 ? v.z : v.w);
 }
 
 // Walk a segment's chain: f(e, t) for every token (end e, id t), last first.
+// Tokens are at most 32 symbols long, so the walk goes through the 32-position
+// windows of tok strictly one after another, downwards: the window below the
+// current one is loaded one window ahead, and its round trip overlaps the
+// tokens of the current one.
 template <class F>
 __device__ __forceinline__ void walk_chain(const BpeTables &T, const BpeWork &W, long long s,
                                            long long e, F &&f) {
-    long long wb = 1ll << 62;  // first position of the window held
-    uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+    if (e < s) return;
+    const long long floor_w = s & ~31ll;  // the lowest window the walk can reach
+    long long wb = e & ~31ll;             // first position of the window held
+    const uint4 *src = reinterpret_cast<const uint4 *>(W.tok + wb);
+    uint4 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
+    uint4 p0 = make_uint4(0, 0, 0, 0), p1 = p0, p2 = p0, p3 = p0;
+    if (wb - 32 >= floor_w) {
+        const uint4 *q = src - 4;
+        p0 = q[0];
+        p1 = q[1];
+        p2 = q[2];
+        p3 = q[3];
+    }
     while (e >= s) {
-        if (e < wb) {
-            wb = e & ~31ll;
-            const uint4 *src = reinterpret_cast<const uint4 *>(W.tok + wb);
-            v0 = src[0];
-            v1 = src[1];
-            v2 = src[2];
-            v3 = src[3];
+        if (e < wb) {  // the next window down, already loaded; load the one below it
+            wb -= 32;
+            v0 = p0;
+            v1 = p1;
+            v2 = p2;
+            v3 = p3;
+            if (wb - 32 >= floor_w) {
+                const uint4 *q = reinterpret_cast<const uint4 *>(W.tok + wb - 32);
+                p0 = q[0];
+                p1 = q[1];
+                p2 = q[2];
+                p3 = q[3];
+            }
         }
         const int wi = (int)((e - wb) >> 1);  // 32-bit word of the window, 0..15
         const unsigned w = wi < 8 ? (wi < 4 ? pick4(v0, wi) : pick4(v1, wi - 4))
