@@ -220,7 +220,7 @@ def _streamed(torch, P, dev, n_bytes: int, reps: int = 3):
 
 def _batched(torch, P, dev, data, offs, d_bytes, d_offs, reps: int = 5):
     """The batched form against per-request plain launches: the whole
-    config-2 batch as one launch (direct and replayed from a CUDA graph)
+    4096-sequence batch as one launch (direct and replayed from a CUDA graph)
     versus one dnatok_encode per sequence; and 64 independent 1 MB
     single-nucleotide calls as plain launches versus one graph replay."""
     import numpy as np
@@ -284,7 +284,7 @@ def _batched(torch, P, dev, data, offs, d_bytes, d_offs, reps: int = 5):
                                       "tokens_per_s": n_ids / seq_wall * 1e3},
             "note": "ids may be cut short in the per-sequence arm only where a sequence's "
                     "capacity bound exceeds the batched result; tokens counted from the batch"}
-    # config 1: 64 independent 1 MB single-nucleotide calls
+    # 64 independent 1 MB single-nucleotide calls
     one, _ = synth.single_sequence_1mb()
     m1 = len(one)
     calls = 64
@@ -570,7 +570,7 @@ def _per_request(torch, P, dev, tr, merges):
 
 
 def _serving(torch, P, dev, seconds: float):
-    """Config-5 request trace (Poisson 2000/s, 200 B-1 MB, 30% single-
+    """The serving request trace (Poisson 2000/s, 200 B-1 MB, 30% single-
     nucleotide / 50% 6-mer / 20% BPE with the 4096-merge table) replayed in
     real time through the serving loop, and through per-request plain
     launches (host copy + encode + wait, one request at a time); then both
@@ -661,7 +661,7 @@ def _graph_of(P, tok, stream, fn):
 
 
 def _char_1mb(torch, P, dev, flush_l2):
-    """Config 1: single-nucleotide ids of one 1 MB sequence.  One call with
+    """Single-nucleotide ids of one 1 MB sequence.  One call with
     L2 flushed before it (plain launch and graph replay), and 64 independent
     1 MB calls replayed back to back from one graph (64 MB in, 256 MB out,
     more than L2 holds)."""
@@ -716,7 +716,7 @@ def _char_1mb(torch, P, dev, flush_l2):
 
 
 def _kmer_uniform(torch, P, dev, flush_l2):
-    """Config 2u: the same 6-mer encode on 4096 sequences with lengths
+    """The same 6-mer encode on 4096 sequences with lengths
     uniform in [1 kb, 128 kb] (about 264 MB), graph replay and plain launch."""
     import synth
     B = P.binding
@@ -747,7 +747,7 @@ def _kmer_uniform(torch, P, dev, flush_l2):
 
 
 def _bpe_1gib(torch, P, dev, flush_l2, with_cpu: bool = True, steps: int = 5):
-    """Config 3: BPE with the 4096-merge table (trained by the oracle's
+    """BPE with the 4096-merge table (trained by the oracle's
     trainer on a 10 MB Markov corpus) on 512 x 2,097,152 fresh bases (1 GiB).
     Device-resident encode (L2 flushed; the input is 8x L2 anyway), the
     repair statistics of the merge pass, the end-to-end call from pinned
@@ -1210,7 +1210,7 @@ def run_gpu(args):
 
 def run_fasta_chunk(args):
     """Device-resident 6-mer encode of one FASTA chunk (the first
-    `--fasta-chunk-mib` MiB of the seeded config-4 stream), the unit of work
+    `--fasta-chunk-mib` MiB of the seeded 8 GiB FASTA stream), the unit of work
     the host-streamed encode gives the general kernel: prints one JSON line
     with the per-encode time (CUDA events, median of --steps)."""
     import numpy as np

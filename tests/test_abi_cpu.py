@@ -115,7 +115,7 @@ def test_shard_records_bounds(lib):
             for i in range(1, world):
                 p = n * i // world
                 assert b[i] == int(np.searchsorted(offs[:n_seq + 1], p, side="left")), (trial, world, i)
-    # the config-2 batch over 8 ranks: no shard more than one record over its share
+    # the 4096-sequence batch over 8 ranks: no shard more than one record over its share
     lens = synth.log_uniform_lengths(4096, 1000, 128000, seed=44)
     offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     b = binding.dnatok_shard_records(offs, 8)
