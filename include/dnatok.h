@@ -156,7 +156,10 @@ DNATOK_API dnatok_status dnatok_reserve(dnatok_handle *h, int64_t max_bytes, int
  *                  Checked on the device (DNATOK_ERR_DEVICE_DATA via
  *                  dnatok_sync).  FASTA: ignored (pass NULL, 0).
  *   ids_out_d      capacity ids_capacity >= dnatok_max_tokens(n_bytes, n_seq),
- *                  checked here (DNATOK_ERR_CAPACITY).
+ *                  checked here (DNATOK_ERR_CAPACITY).  Entries after the ids
+ *                  produced, up to the capacity, are scratch: a direct path
+ *                  that finds its premise broken may leave ids there before
+ *                  the general path rewrites the result.
  *   id_offsets_d   RAW: n_seq + 1 entries.  FASTA: offsets_capacity entries;
  *                  the records found may exceed it: entries past the capacity
  *                  are not written and totals tells how many there were.

@@ -76,8 +76,11 @@ dnatok_status ensure_workspace(dnatok_handle *h, long long n_bytes, long long n_
 dnatok_status next_epoch(dnatok_handle *h, cudaStream_t s, unsigned *epoch) {
     h->epoch++;
     if ((h->epoch & ((1u << kEpochBits) - 1)) == 0) {  // epoch wrap: forget every old descriptor
+        // The gate holds whole 32-bit epochs, so it needs clearing only when
+        // those wrap; clearing it here could drop a gate that a direct path
+        // raised for the general launch that takes this epoch.
         cudaError_t e = cudaMemsetAsync(h->d_desc, 0, sizeof(TileDesc) * h->desc_cap, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_gate, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess && h->epoch == 0) e = cudaMemsetAsync(h->d_gate, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(descriptors)");
         h->epoch++;
     }
@@ -90,7 +93,7 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
                               void *out, long long out_cap, long long *offsets_out,
                               long long offsets_cap, long long *totals_out, const Carry *carry_in,
                               Carry *carry_out, int start_boundary, int end_boundary,
-                              cudaStream_t s) {
+                              cudaStream_t s, unsigned gate_epoch) {
     const LaunchShape sh = h->shape;
     dnatok_status st = ensure_workspace(h, n_bytes, n_bnd, sh, s);
     if (st != DNATOK_OK) return st;
@@ -133,8 +136,14 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
     const bool capturing = cudaStreamIsCapturing(s, &capst) == cudaSuccess &&
                            capst != cudaStreamCaptureStatusNone;
-    if (bsrc == BSRC_LIST && !carry_in && !carry_out && h->direct &&
-        direct_eligible(mode, n_bnd - 1, h->lut_host)) {
+    if (gate_epoch != 0) {
+        // behind a direct path of the caller's (launched before this call
+        // on the same stream, never under capture): run only if it raised
+        // the gate
+        p.gate = h->d_gate;
+        p.gate_epoch = gate_epoch;
+    } else if (bsrc == BSRC_LIST && !carry_in && !carry_out && h->direct &&
+               direct_eligible(mode, n_bnd - 1, h->lut_host)) {
         // RAW input: the direct path, with the general kernel behind it
         unsigned ep = 0;
         st = next_epoch(h, s, &ep);
@@ -258,6 +267,10 @@ dnatok_status dnatok_create(dnatok_handle **out, dnatok_mode mode, int k,
         // a u16 copy that fits shared memory (31 KB for k = 6), padded to 16 bytes
         bool small = k <= 6;
         for (long long i = 0; small && i < n_index; ++i) small = h->klut_host[i] < 0xFFFF;
+        // 2-byte window entries for the direct path: ids below 0x8000, and a
+        // window's base-5 index (5^k values) in 14 bits
+        h->kent16 = k <= 6;
+        for (long long i = 0; h->kent16 && i < n_index; ++i) h->kent16 = h->klut_host[i] < 0x8000;
         if (e == cudaSuccess && small) {
             std::vector<uint16_t> t16((size_t)((n_index + 7) / 8 * 8), 0xFFFF);
             for (long long i = 0; i < n_index; ++i)

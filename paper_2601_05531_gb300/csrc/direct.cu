@@ -17,6 +17,8 @@
 //      failed, and exits at once otherwise.
 // Paper: Algorithm 2's byte -> id gather and MapKmer, with the k-mer id in
 // closed form sum_i 4^(k-1-i) * code(b_i) (Sec. 2.2).
+#include <cstring>
+
 #include "handle.h"
 #include "tile_kernel.cuh"
 
@@ -50,6 +52,11 @@ struct DirectParams {
     const long long *dyn;
     long long d_base;          // output index of the first record's first id
     long long out_cap;         // ids capacity (the plan sends a larger encode to the general path)
+    // table-driven k-mers (non-null only there): the plan also maps every
+    // tile of 2^tile_shift windows to the record holding its first window
+    long long *tile_rec;
+    long long tile_cap;        // entries of tile_rec
+    int tile_shift;
 };
 
 // The parameters with the device-side counts in place, or null when an
@@ -143,6 +150,23 @@ __global__ void __launch_bounds__(kPlanThreads) direct_plan_kernel(DirectParams 
             run += t[j];
         }
         __syncthreads();
+        if (q.tile_rec) {
+            // the tiles whose first window lies in this pass's records, one
+            // thread per tile: its record by a search of the staged window
+            // offsets (at most tile_cap tiles, whatever the offsets hold)
+            const int sh = q.tile_shift;
+            const long long a = carry - q.d_base, b = a + tot;
+            for (long long tt = ((a + (1ll << sh) - 1) >> sh) + tid; tt < q.tile_cap && (tt << sh) < b;
+                 tt += kPlanThreads) {
+                const long long w = (tt << sh) + q.d_base;
+                int lo = 0, hi = cnt - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_v[mid] <= w) lo = mid; else hi = mid - 1;
+                }
+                q.tile_rec[tt] = r0 + lo;
+            }
+        }
         for (int i = tid; i < cnt; i += kPlanThreads) q.offsets_out[r0 + i] = s_v[i];
         carry += tot;
         __syncthreads();  // s_v and wsum are reused by the next pass
@@ -879,6 +903,9 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                           cudaStream_t s, const long long *dyn, long long out_cap,
                           cudaEvent_t ev0, cudaEvent_t ev1) {
     DirectParams q;
+    q.tile_rec = nullptr;
+    q.tile_cap = 0;
+    q.tile_shift = 0;
     q.dyn = dyn;
     q.d_base = 0;
     q.out_cap = out_cap;
@@ -944,6 +971,27 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
         if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
         return e;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_plan(const long long *so, long long n_seq, long long n, int k,
+                               long long *wpre, long long *tile_rec, long long tile_cap,
+                               int tile_shift, unsigned *gate, unsigned epoch, cudaStream_t s) {
+    DirectParams q;
+    std::memset(&q, 0, sizeof(q));
+    q.n = n;
+    q.so = so;
+    q.n_seq = n_seq;
+    q.offsets_out = wpre;
+    q.gate = gate;
+    q.epoch = epoch;
+    q.k = k;
+    q.kinv = k > 1 ? ~0ull / (unsigned long long)k + 1ull : 0ull;
+    q.out_cap = 0x7fffffffffffffffll;
+    q.tile_rec = tile_rec;
+    q.tile_cap = tile_cap;
+    q.tile_shift = tile_shift;
+    direct_plan_kernel<<<1, kPlanThreads, 0, s>>>(q);
     return cudaGetLastError();
 }
 

@@ -64,6 +64,7 @@ struct dnatok_handle {
     // table-driven k-mers: kmer_lut (5^k ids) on the device, the single-symbol ids
     int32_t *d_klut = nullptr;
     uint16_t *d_klut16 = nullptr;  // the same as u16 (0xFFFF = none) when k <= 6 and ids < 0xFFFF
+    bool kent16 = false;           // k <= 6, every kmer_lut id below 0x8000 (2-byte window entries)
     std::vector<int32_t> klut_host;
     int32_t base_ids[5] = {0, 1, 2, 3, 4};
     std::vector<int32_t> merges_host;  // BPE table, kept for the decode table
@@ -93,7 +94,8 @@ dnatok_status fail_cuda(dnatok_handle *h, cudaError_t e, const char *what);
 dnatok_status ensure_workspace(dnatok_handle *h, long long n_bytes, long long n_bnd,
                                const LaunchShape &sh, cudaStream_t s);
 
-// Next launch epoch (descriptors are reset when the 24-bit epoch wraps).
+// Next launch epoch (descriptors are reset when the 18-bit descriptor epoch
+// wraps, the gate when the 32-bit epoch does).
 dnatok_status next_epoch(dnatok_handle *h, cudaStream_t s, unsigned *epoch);
 
 long long tiles_for(long long n_bytes, int head_pad, int tile);
@@ -104,7 +106,7 @@ dnatok_status run_tile_encode(dnatok_handle *h, int mode, int k, int bsrc, const
                               void *out, long long out_cap, long long *offsets_out,
                               long long offsets_cap, long long *totals_out, const Carry *carry_in,
                               Carry *carry_out, int start_boundary, int end_boundary,
-                              cudaStream_t s);
+                              cudaStream_t s, unsigned gate_epoch = 0);
 
 // Direct path for RAW input without separators (direct.cu)
 bool direct_eligible(int mode, long long n_seq, const int32_t *lut_host);
@@ -115,6 +117,27 @@ cudaError_t launch_direct(int mode, const uint8_t *bytes, long long n, const lon
                           cudaStream_t s, const long long *dyn = nullptr,
                           long long out_cap = 0x7fffffffffffffffll,
                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+// The direct plan alone for table-driven k-mers: window offsets ceil(L / k)
+// into wpre (n_seq + 1), and for every tile of 2^tile_shift windows the
+// record of its first window (tile_cap entries at most).  Malformed offsets
+// raise the gate instead.
+cudaError_t launch_window_plan(const long long *so, long long n_seq, long long n, int k,
+                               long long *wpre, long long *tile_rec, long long tile_cap,
+                               int tile_shift, unsigned *gate, unsigned epoch, cudaStream_t s);
+
+// Table-driven k-mers straight from RAW bytes without separators
+// (ktab_direct.cu): the window plan, count, scan and expand; the count
+// raises the gate (epoch) when the input holds a byte below 0x21.
+// ktab_direct_tiles(n) entries for tile_rec and tsum;
+// ktab_direct_entries(n, n_seq, k) window entries of 2 bytes (kent16) or 4.
+long long ktab_direct_tiles(long long n_bytes);
+long long ktab_direct_entries(long long n_bytes, long long n_seq, int k);
+cudaError_t ktab_direct_setup(dnatok_handle *h);
+cudaError_t ktab_direct_launch(dnatok_handle *h, const uint8_t *bytes, long long n,
+                               const long long *so, long long n_seq, long long *wpre,
+                               long long *tile_rec, long long *tsum, void *went, int32_t *out,
+                               long long ids_cap, long long *id_offsets, long long *totals,
+                               unsigned epoch, cudaStream_t s);
 
 void fasta_destroy(dnatok_handle *h);
 dnatok_status fasta_reserve(dnatok_handle *h, long long n_bytes, long long offsets_cap,
@@ -161,12 +184,13 @@ dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_by
 // totals_out (NULL or 2): {total, sum of tinv (NULL: n_rec)}.  n_rec comes
 // from n_rec_dev when not NULL; n_items from n_items_dev when not NULL, else
 // n_items_host when >= 0, else keys[n_rec].  Does nothing once the device
-// status word holds an error.
+// status word holds an error, nor when gate is not NULL and *gate differs
+// from gate_epoch (the direct path behind which it runs did the work).
 __global__ void tile_scan_kernel(long long *tsum, const long long *tinv, const long long *keys,
                                  const long long *n_rec_dev, long long n_rec_host,
                                  const long long *n_items_dev, long long n_items_host,
                                  int items_per_tile, long long *rec_out, long long *totals_out,
-                                 const int *status);
+                                 const int *status, const unsigned *gate, unsigned gate_epoch);
 constexpr int kTileScanThreads = 1024;
 
 // decode tables (decode.cu)

@@ -40,6 +40,7 @@
 #include "handle.h"
 #include "search.cuh"
 #include "tile_kernel.cuh"
+#include "ktab.cuh"
 
 struct OvlState {
     uint8_t *d_sym = nullptr;   // one symbol per kept base
@@ -50,6 +51,11 @@ struct OvlState {
     long long *d_tot = nullptr;   // {symbols, records} of the symbol pass
     long long *d_tsum = nullptr;  // table-driven k-mers: per-tile token counts
     long long cap_tsum = 0;
+    // table-driven k-mers straight from RAW bytes: per tile of windows its
+    // first window's record, and per window its entry (sized for cap_sym
+    // input bytes and cap_srec records; the tile counts go to d_tsum)
+    long long *d_trec = nullptr;
+    void *d_went = nullptr;
 };
 
 namespace {
@@ -58,22 +64,10 @@ using namespace dnatok;
 
 constexpr int kOT = 4096;          // symbols per emit tile
 constexpr int kOThreads = 256;
-constexpr int kORW = 64;           // records of a tile kept in shared memory
 constexpr int kOPlanThreads = 1024;
 constexpr int kOPlanTile = 4096;   // records per pass of the offsets kernel
 
 __device__ __forceinline__ long long ovl_tokens(long long L, int k) { return L >= k ? L - k + 1 : 0; }
-
-// Largest r in [0, n_rec - 1] with srec[r] <= j (srec sorted, srec[0] = 0),
-// by one thread.
-__device__ long long ovl_find(const long long *srec, long long n_rec, long long j) {
-    long long lo = 0, hi = n_rec - 1;
-    while (lo < hi) {
-        const long long mid = (lo + hi + 1) >> 1;
-        if (srec[mid] <= j) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
 
 // Stage sym[j0 .. j0 + n) in shared memory as the 16-byte aligned span
 // around it, s[x] = sym[(j0 & ~15) + x] for x < (j0 & 15) + n rounded up to
@@ -104,11 +98,14 @@ template <int KIND>
 __global__ void __launch_bounds__(kOPlanThreads) offsets_kernel(long long *offs, long long *srec,
                                                                 long long *wpre, long long *tot,
                                                                 int k, long long offs_cap,
-                                                                long long *totals_out, int *status) {
+                                                                long long *totals_out, int *status,
+                                                                const unsigned *gate,
+                                                                unsigned gate_epoch) {
     constexpr int kPer = kOPlanTile / kOPlanThreads;
     __shared__ long long s_v[kOPlanTile + 1];
     __shared__ long long wsum[kOPlanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (gate && *(volatile const unsigned *)gate != gate_epoch) return;  // the direct path did it
     const long long n = tot[1];  // records
     if (n + 1 > offs_cap) {
         __syncthreads();  // every thread has read tot[1]
@@ -298,200 +295,6 @@ cudaError_t launch_emit(int k, unsigned grid, const uint8_t *sym, const long lon
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------ table-driven k-mers
-
-constexpr int kKW = 2048;       // windows per tile
-constexpr int kKThreads = 256;
-constexpr int kKPer = kKW / kKThreads;  // consecutive windows per thread
-constexpr int kKRW = 64;        // records of a tile kept in shared memory
-constexpr int kKTok = 2560;     // ids of a tile staged in shared memory by the emit
-
-struct KtabIds {
-    int b[5];  // ids of the single symbols A C G T N
-};
-
-__host__ __device__ constexpr int pow5(int k) { return k == 0 ? 1 : 5 * pow5(k - 1); }
-
-// Dynamic shared memory of a ktab_tile_kernel: [u16 table (T16)] [symbols]
-// [staged ids (EMIT)], each part 16-byte aligned.
-__host__ __device__ constexpr int ktab_tab_bytes(int K, bool T16) {
-    return T16 ? ((pow5(K) * 2 + 15) / 16) * 16 : 0;
-}
-__host__ __device__ constexpr int ktab_sym_bytes(int K) { return ((kKW * K + 32 + 15) / 16) * 16; }
-__host__ __device__ constexpr int ktab_smem(int K, bool EMIT, bool T16) {
-    return ktab_tab_bytes(K, T16) + ktab_sym_bytes(K) + (EMIT ? kKTok * 4 + 16 : 0);
-}
-
-// One window: its record (r, its first window wp, its symbol range [sr, sr1))
-// from the tile's shared record window (advancing the caller's index i, as
-// windows only grow), else by a search of wpre.
-struct KWin {
-    long long r, t, j;  // record, window within the record, first symbol in s_sym
-    int cnt, ent;       // tokens; the table entry of a whole window (-1: none)
-};
-
-template <int K, bool T16>
-__device__ __forceinline__ KWin ktab_window(long long w, int &i, int nw, long long rb, long long n_rec,
-                                            const long long *s_wp, const long long *s_sr,
-                                            const long long *wpre, const long long *srec,
-                                            const uint8_t *s_sym, long long jlo, long long nsym,
-                                            const int *klut, const uint16_t *s_tab) {
-    KWin q;
-    q.r = -1;
-    q.cnt = 0;
-    q.ent = -1;
-    long long wp, sr, sr1;
-    if (w >= s_wp[nw] && rb + nw < n_rec) {
-        // more records start in this tile than the window holds
-        const long long r = ovl_find(wpre, n_rec, w);
-        q.r = r;
-        wp = wpre[r];
-        sr = srec[r];
-        sr1 = srec[r + 1];
-    } else {
-        while (i + 1 < nw && s_wp[i + 1] <= w) ++i;
-        q.r = rb + i;
-        wp = s_wp[i];
-        sr = s_sr[i];
-        sr1 = s_sr[i + 1];
-    }
-    q.t = w - wp;
-    q.j = sr + q.t * K - jlo;
-    const long long rem = (sr1 - sr) - q.t * K;
-    const int n_s = rem >= K ? K : (int)rem;
-    if (q.j < 0 || n_s < 1 || q.j + n_s > nsym) {  // (malformed input)
-        q.r = -1;
-        return q;
-    }
-    if (n_s == K) {
-        int index = 0;
-#pragma unroll
-        for (int x = 0; x < K; ++x) {
-            const int d = s_sym[q.j + x];
-            index = index * 5 + (d < 5 ? d : 4);
-        }
-        if (T16) {
-            const unsigned v = s_tab[index];
-            q.ent = v == 0xFFFFu ? -1 : (int)v;
-        } else {
-            q.ent = __ldg(klut + index);
-        }
-        q.cnt = q.ent >= 0 ? 1 : K;
-    } else {
-        q.cnt = n_s;
-    }
-    return q;
-}
-
-// A thread's walk over its consecutive windows in 32-bit tile-local terms:
-// record i of the tile's shared window, j = the window's first symbol in the
-// staged symbols, rem = symbols of the record from j on (clamped).  Set up
-// once per thread; each window then costs a few int operations.
-struct KCursor {
-    int i, j, rem;
-    bool first;  // the window is its record's first
-};
-
-template <int K>
-__device__ __forceinline__ KCursor kc_init(long long w, int nw, const long long *s_wp,
-                                           const long long *s_sr, long long jlo) {
-    KCursor c;
-    int i = 0;
-    while (i + 1 < nw && s_wp[i + 1] <= w) ++i;
-    const long long t = w - s_wp[i];
-    const long long rem = (s_sr[i + 1] - s_sr[i]) - t * K;
-    c.i = i;
-    c.j = (int)(s_sr[i] + t * K - jlo);
-    c.rem = (int)(rem < (1ll << 30) ? rem : (1ll << 30));
-    c.first = (t == 0);
-    return c;
-}
-
-// The window at the cursor (then advanced by one window), or cnt = 0 with
-// r = -1 past the shared window's records or on malformed input.
-template <int K, bool T16>
-__device__ __forceinline__ KWin kc_window(KCursor &c, int nw, long long rb, const long long *s_sr,
-                                          long long jlo, const uint8_t *s_sym, long long nsym,
-                                          const int *klut, const uint16_t *s_tab) {
-    KWin q;
-    q.r = -1;
-    q.cnt = 0;
-    q.ent = -1;
-    while (c.rem <= 0 && c.i + 1 < nw) {  // the record's windows are used up: the next record's
-        ++c.i;
-        const long long len = s_sr[c.i + 1] - s_sr[c.i];
-        c.j = (int)(s_sr[c.i] - jlo);
-        c.rem = (int)(len < (1ll << 30) ? len : (1ll << 30));
-        c.first = true;
-    }
-    const int n_s = c.rem >= K ? K : c.rem;
-    if (n_s < 1 || c.j < 0 || c.j + n_s > nsym) return q;  // (malformed input)
-    q.r = rb + c.i;
-    q.t = c.first ? 0 : 1;
-    q.j = c.j;
-    if (n_s == K) {
-        int index = 0;
-#pragma unroll
-        for (int x = 0; x < K; ++x) {
-            const int d = s_sym[c.j + x];
-            index = index * 5 + (d < 5 ? d : 4);
-        }
-        if (T16) {
-            const unsigned v = s_tab[index];
-            q.ent = v == 0xFFFFu ? -1 : (int)v;
-        } else {
-            q.ent = __ldg(klut + index);
-        }
-        q.cnt = q.ent >= 0 ? 1 : K;
-    } else {
-        q.cnt = n_s;
-    }
-    c.j += K;
-    c.rem -= K;
-    c.first = false;
-    return q;
-}
-
-// The kKPer whole windows of one record starting at staged symbol A (all in
-// shared memory): the span is read as 32-bit words and shifted into place
-// once, and each window's digits are then taken from registers at
-// compile-time positions (instead of k single-byte shared-memory loads per
-// window).  ent[q] = the table entry (-1: none), cnt[q] = 1 or K.
-template <int K, bool T16>
-__device__ __forceinline__ void ktab_fast_windows(const uint8_t *s_base, int A, const int *klut,
-                                                  const uint16_t *s_tab, int (&ent)[kKPer],
-                                                  int (&cnt)[kKPer]) {
-    constexpr int NB = kKPer * K;          // bytes of the span
-    constexpr int NW = (NB + 3) / 4 + 1;   // words read (one more for the shift)
-    const uint32_t *w32 = reinterpret_cast<const uint32_t *>(s_base + (A & ~3));
-    const unsigned sh = 8u * (unsigned)(A & 3);
-    uint32_t W[NW];
-#pragma unroll
-    for (int i = 0; i < NW; ++i) W[i] = w32[i];
-    uint32_t X[NW - 1];
-#pragma unroll
-    for (int i = 0; i < NW - 1; ++i) X[i] = __funnelshift_r(W[i], W[i + 1], sh);
-#pragma unroll
-    for (int q = 0; q < kKPer; ++q) {
-        int index = 0;
-#pragma unroll
-        for (int x = 0; x < K; ++x) {
-            const int b = q * K + x;
-            const int d = (int)((X[b >> 2] >> (8 * (b & 3))) & 0xFFu);
-            index = index * 5 + (d < 5 ? d : 4);
-        }
-        int e;
-        if (T16) {
-            const unsigned v = s_tab[index];
-            e = v == 0xFFFFu ? -1 : (int)v;
-        } else {
-            e = __ldg(klut + index);
-        }
-        ent[q] = e;
-        cnt[q] = e >= 0 ? 1 : K;
-    }
-}
-
 // One tile of windows [w0, w1): count (EMIT = false: the tile's token count
 // to tsum[tile]) or emit (EMIT = true: ids from tsum[tile], by then the
 // tile's exclusive token offset, and the record offsets of records whose
@@ -506,7 +309,7 @@ template <int K, bool EMIT, bool T16>
 __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
     const uint8_t *sym, const long long *srec, const long long *wpre, const long long *tot,
     const int *klut, const uint16_t *klut16, KtabIds base, long long *tsum, int *out,
-    long long ids_cap, long long *id_offsets) {
+    long long ids_cap, long long *id_offsets, const unsigned *gate, unsigned gate_epoch) {
     extern __shared__ __align__(16) uint8_t dyn[];
     uint16_t *s_tab = reinterpret_cast<uint16_t *>(dyn);
     uint8_t *s_sym = dyn + ktab_tab_bytes(K, T16);
@@ -516,6 +319,7 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
     __shared__ int s_nw;
     __shared__ int s_wsum[kKThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (gate && *(volatile const unsigned *)gate != gate_epoch) return;  // the direct path did it
     const long long n_rec = tot[1];
     if (n_rec < 1) return;
     if (T16) {
@@ -598,8 +402,8 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
                 const int nq = (int)((w1 - wt < kKPer) ? w1 - wt : kKPer);
                 if (nq == kKPer && c.rem >= kKPer * K && c.j >= 0 && c.j + kKPer * K <= nsym) {
                     // all eight windows whole and in one record
-                    int ent[kKPer], cn[kKPer];
-                    ktab_fast_windows<K, T16>(s_sym, lead + c.j, klut, s_tab, ent, cn);
+                    int ent[kKPer], cn[kKPer], ix[kKPer];
+                    ktab_fast_windows<K, T16>(s_sym, lead + c.j, klut, s_tab, ent, cn, ix);
 #pragma unroll
                     for (int q = 0; q < kKPer; ++q) sum += cn[q];
                 } else {
@@ -648,8 +452,8 @@ __global__ void __launch_bounds__(kKThreads) ktab_tile_kernel(
                               c.j + kKPer * K <= nsym;
             if (fast) {
                 // all eight windows whole and in one record (as in the count)
-                int ent[kKPer], cn[kKPer];
-                ktab_fast_windows<K, T16>(s_sym, lead + c.j, klut, s_tab, ent, cn);
+                int ent[kKPer], cn[kKPer], ix[kKPer];
+                ktab_fast_windows<K, T16>(s_sym, lead + c.j, klut, s_tab, ent, cn, ix);
                 if (c.first) {
                     long long r = rb + c.i;
                     const long long pos = tbase + loc;
@@ -761,7 +565,8 @@ template <int K, bool EMIT, bool T16>
 cudaError_t launch_ktab_k(int sm_count, long long max_tiles, const uint8_t *sym,
                           const long long *srec, const long long *wpre, const long long *tot,
                           const int *klut, const uint16_t *klut16, KtabIds base, long long *tsum,
-                          int *out, long long cap, long long *id_offsets, cudaStream_t s) {
+                          int *out, long long cap, long long *id_offsets, const unsigned *gate,
+                          unsigned gate_epoch, cudaStream_t s) {
     constexpr int smem = ktab_smem(K, EMIT, T16);
     int per_sm = 1;
     cudaError_t e = ktab_init<K, EMIT, T16>(&per_sm);
@@ -771,7 +576,7 @@ cudaError_t launch_ktab_k(int sm_count, long long max_tiles, const uint8_t *sym,
     if (grid > max_tiles) grid = max_tiles;
     if (grid < 1) grid = 1;
     ktab_tile_kernel<K, EMIT, T16><<<(unsigned)grid, kKThreads, smem, s>>>(
-        sym, srec, wpre, tot, klut, klut16, base, tsum, out, cap, id_offsets);
+        sym, srec, wpre, tot, klut, klut16, base, tsum, out, cap, id_offsets, gate, gate_epoch);
     return cudaGetLastError();
 }
 
@@ -779,10 +584,11 @@ cudaError_t launch_ktab(int k, bool emit, bool t16, int sm_count, long long max_
                         const uint8_t *sym, const long long *srec, const long long *wpre,
                         const long long *tot, const int *klut, const uint16_t *klut16,
                         KtabIds base, long long *tsum, int *out, long long cap,
-                        long long *id_offsets, cudaStream_t s) {
+                        long long *id_offsets, const unsigned *gate, unsigned gate_epoch,
+                        cudaStream_t s) {
 #define DNATOK_KT(KK, EM, TT)                                                                  \
     return launch_ktab_k<KK, EM, TT>(sm_count, max_tiles, sym, srec, wpre, tot, klut, klut16,  \
-                                     base, tsum, out, cap, id_offsets, s)
+                                     base, tsum, out, cap, id_offsets, gate, gate_epoch, s)
 #define DNATOK_KT_K(KK)                                                                        \
     case KK:                                                                                   \
         if (emit) {                                                                            \
@@ -807,6 +613,10 @@ void free_ovl(OvlState *o) {
     cudaFree(o->d_wpre);
     cudaFree(o->d_tot);
     cudaFree(o->d_tsum);
+    cudaFree(o->d_trec);
+    cudaFree(o->d_went);
+    o->d_trec = nullptr;
+    o->d_went = nullptr;
     o->d_sym = nullptr;
     o->d_srec = nullptr;
     o->d_wpre = nullptr;
@@ -839,8 +649,12 @@ dnatok_status ovl_reserve(dnatok_handle *h, long long max_bytes, long long max_o
         for (int emit = 0; emit < 2; ++emit) {
             cudaError_t e = launch_ktab(h->k, emit != 0, h->d_klut16 != nullptr, 1, 1, nullptr,
                                         nullptr, nullptr, nullptr, nullptr, nullptr, none, nullptr,
-                                        nullptr, 0, nullptr, s);
+                                        nullptr, 0, nullptr, nullptr, 0u, s);
             if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer kernel setup");
+        }
+        if (h->fmt == DNATOK_RAW) {
+            cudaError_t e = ktab_direct_setup(h);
+            if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer kernel setup (RAW bytes)");
         }
     }
     if (max_bytes <= o->cap_sym && max_offsets <= o->cap_srec && o->d_tot) return DNATOK_OK;
@@ -860,6 +674,12 @@ dnatok_status ovl_reserve(dnatok_handle *h, long long max_bytes, long long max_o
         e = cudaMalloc(&o->d_wpre, sizeof(long long) * (size_t)(cr + 1));
     if (e == cudaSuccess && h->mode == DNATOK_KMER_TABLE)
         e = cudaMalloc(&o->d_tsum, sizeof(long long) * (size_t)ct);
+    if (e == cudaSuccess && h->mode == DNATOK_KMER_TABLE && h->fmt == DNATOK_RAW) {
+        const long long nt = ktab_direct_tiles(cs_);
+        e = cudaMalloc(&o->d_trec, sizeof(long long) * (size_t)nt);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&o->d_went, (h->kent16 ? 2 : 4) * (size_t)ktab_direct_entries(cs_, cr, h->k));
+    }
     if (e == cudaSuccess) e = cudaMalloc(&o->d_tot, 2 * sizeof(long long));
     if (e != cudaSuccess) {
         free_ovl(o);
@@ -888,7 +708,7 @@ dnatok_status ovl_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
     // 2. token offsets
     offsets_kernel<kOffsetsTokens><<<1, kOPlanThreads, 0, s>>>(
         reinterpret_cast<long long *>(id_offsets_d), o->d_srec, nullptr, o->d_tot, h->k,
-        offsets_capacity, reinterpret_cast<long long *>(totals_d), h->d_status);
+        offsets_capacity, reinterpret_cast<long long *>(totals_d), h->d_status, nullptr, 0u);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "overlap offsets launch");
     // 3. ids
@@ -906,11 +726,13 @@ dnatok_status ovl_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_byt
 __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     long long *tsum, const long long *tinv, const long long *keys, const long long *n_rec_dev,
     long long n_rec_host, const long long *n_items_dev, long long n_items_host, int items_per_tile,
-    long long *rec_out, long long *totals_out, const int *status) {
+    long long *rec_out, long long *totals_out, const int *status, const unsigned *gate,
+    unsigned gate_epoch) {
     constexpr int kPer = 4;
     __shared__ long long wsum[kTileScanThreads / 32], winv[kTileScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (dev_failed(status)) return;  // an earlier pass failed: its counts are not valid
+    if (gate && *(volatile const unsigned *)gate != gate_epoch) return;  // the direct path did it
     const long long n_rec = n_rec_dev ? *n_rec_dev : n_rec_host;
     if (n_rec < 0) return;
     const long long n_items = n_items_dev ? *n_items_dev : (n_items_host >= 0 ? n_items_host : keys[n_rec]);
@@ -980,17 +802,42 @@ dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_by
     OvlState *o = h->ovl;
     const bool raw = (h->fmt == DNATOK_RAW);
     long long *offs = reinterpret_cast<long long *>(id_offsets_d);
+    const long long *so = reinterpret_cast<const long long *>(seq_offsets_d);
+    cudaError_t e = cudaSuccess;
+    // 0. RAW input: straight from the bytes (window plan, count, scan,
+    // emit), with the general path below gated behind it.  Not under stream
+    // capture: a replay would find the gate raised with the epoch baked into
+    // the graph.
+    unsigned gate_ep = 0;
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(s, &capst) == cudaSuccess &&
+                           capst != cudaStreamCaptureStatusNone;
+    if (raw && h->direct && n_bytes > 0 && !capturing && o->d_trec &&
+        direct_eligible(MODE_SYM, n_seq, h->lut_host)) {
+        // the general path's workspace first: growing it clears the gate
+        // and restarts the epochs, which must not happen behind the gate
+        st = ensure_workspace(h, n_bytes, n_seq + 1, h->shape, s);
+        if (st != DNATOK_OK) return st;
+        st = next_epoch(h, s, &gate_ep);
+        if (st != DNATOK_OK) return st;
+        e = ktab_direct_launch(h, bytes_d, n_bytes, so, n_seq, o->d_wpre, o->d_trec, o->d_tsum,
+                               o->d_went, ids_out_d, ids_capacity, offs,
+                               reinterpret_cast<long long *>(totals_d), gate_ep, s);
+        if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer launch (RAW bytes)");
+    }
+    const unsigned *gate = gate_ep ? h->d_gate : nullptr;
     // 1. symbols and record starts (in symbols)
     st = run_tile_encode(h, MODE_SYM, 1, raw ? BSRC_LIST : BSRC_FASTA, bytes_d, n_bytes,
-                         reinterpret_cast<const long long *>(seq_offsets_d), raw ? n_seq + 1 : 0,
-                         o->d_sym, o->cap_sym, offs, offsets_capacity, o->d_tot, nullptr, nullptr,
-                         raw ? 0 : 1, raw ? 0 : 1, s);
+                         raw ? so : nullptr, raw ? n_seq + 1 : 0, o->d_sym, o->cap_sym, offs,
+                         offsets_capacity, o->d_tot, nullptr, nullptr, raw ? 0 : 1, raw ? 0 : 1, s,
+                         gate_ep);
     if (st != DNATOK_OK) return st;
+    if (gate_ep) h->direct_epoch = gate_ep;
     // 2. window offsets
     offsets_kernel<kOffsetsWindows><<<1, kOPlanThreads, 0, s>>>(
         offs, o->d_srec, o->d_wpre, o->d_tot, h->k, offsets_capacity,
-        reinterpret_cast<long long *>(totals_d), h->d_status);
-    cudaError_t e = cudaGetLastError();
+        reinterpret_cast<long long *>(totals_d), h->d_status, gate, gate_ep);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "window offsets launch");
     // 3-5. count, scan, emit
     const long long tiles = n_bytes / kKW + 1;
@@ -998,16 +845,18 @@ dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_by
     KtabIds base;
     for (int d = 0; d < 5; ++d) base.b[d] = h->base_ids[d];
     e = launch_ktab(h->k, false, t16, h->sm_count, tiles, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,
-                    h->d_klut, h->d_klut16, base, o->d_tsum, ids_out_d, ids_capacity, offs, s);
+                    h->d_klut, h->d_klut16, base, o->d_tsum, ids_out_d, ids_capacity, offs, gate,
+                    gate_ep, s);
     if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer count launch");
     tile_scan_kernel<<<1, kTileScanThreads, 0, s>>>(o->d_tsum, nullptr, o->d_wpre, o->d_tot + 1, 0,
                                                 nullptr, -1, kKW, offs,
                                                 reinterpret_cast<long long *>(totals_d),
-                                                h->d_status);
+                                                h->d_status, gate, gate_ep);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer scan launch");
     e = launch_ktab(h->k, true, t16, h->sm_count, tiles, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,
-                    h->d_klut, h->d_klut16, base, o->d_tsum, ids_out_d, ids_capacity, offs, s);
+                    h->d_klut, h->d_klut16, base, o->d_tsum, ids_out_d, ids_capacity, offs, gate,
+                    gate_ep, s);
     if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer emit launch");
     return DNATOK_OK;
 }
