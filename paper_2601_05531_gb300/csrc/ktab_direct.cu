@@ -141,10 +141,11 @@ __device__ __forceinline__ void kd_issue(const KdParams &p, const KdMeta &m, uin
 }
 
 // A bounded wait for a bulk copy: false when it has not landed after
-// kSpinLimit polls.
+// kSpinLimit polls.  Each poll lets the thread sleep up to 20 us while the
+// copy is in flight, so waiting warps take no issue slots from the others.
 __device__ __forceinline__ bool kd_wait(uint64_t *bar, unsigned parity) {
     int spins = 0;
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait_hint(bar, parity, 20000u))
         if (++spins > kSpinLimit) return false;
     return true;
 }
@@ -175,6 +176,13 @@ struct KdEnt<uint16_t, K> {
         return (uint16_t)(0x8000 + kd_off(c) + index);
     }
     static __device__ __forceinline__ bool is_id(uint16_t e) { return e < 0x8000u; }
+    // ids the entry stands for (the tail's length found only for a tail)
+    static __device__ __forceinline__ int count(uint16_t e) {
+        if (e < 0x8000u) return 1;
+        if (e >= 0xC000u) return K;
+        int v;
+        return tail_decode((int)e - 0x8000, v);
+    }
     // ids the entry stands for; v = the id (is_id) or the digits' index
     static __device__ __forceinline__ int decode(uint16_t e, int &v, bool &is_id) {
         is_id = e < 0x8000u;
@@ -205,6 +213,13 @@ struct KdEnt<int, K> {
         return -1 - pow5(K) - (kd_off(c) + index);
     }
     static __device__ __forceinline__ bool is_id(int e) { return e >= 0; }
+    static __device__ __forceinline__ int count(int e) {
+        if (e >= 0) return 1;
+        const int u = -1 - e;
+        if (u < pow5(K)) return K;
+        int v;
+        return KdEnt<uint16_t, K>::tail_decode(u - pow5(K), v);
+    }
     static __device__ __forceinline__ int decode(int e, int &v, bool &is_id) {
         is_id = e >= 0;
         if (is_id) {
@@ -499,11 +514,7 @@ __global__ void __launch_bounds__(kKThreads) kd_expand_kernel(const KdParams p) 
         if (plain) {
             sum = kKPer;
         } else {
-            for (int q = 0; q < nq; ++q) {
-                int vq;
-                bool is_id;
-                sum += KdEnt<E, K>::decode(kd_pick(e, q), vq, is_id);
-            }
+            for (int q = 0; q < nq; ++q) sum += KdEnt<E, K>::count(kd_pick(e, q));
         }
         kd_store_ents(s_ent + q0, e);
         int x = sum;
@@ -531,10 +542,8 @@ __global__ void __launch_bounds__(kKThreads) kd_expand_kernel(const KdParams p) 
             *reinterpret_cast<uint4 *>(s_wpos + q0) = wp4;
         } else {
             for (int q = 0; q < nq; ++q) {
-                int vq;
-                bool is_id;
                 s_wpos[q0 + q] = (uint16_t)loc;
-                loc += KdEnt<E, K>::decode(kd_pick(e, q), vq, is_id);
+                loc += KdEnt<E, K>::count(kd_pick(e, q));
             }
         }
         // staged: ids go to s_tok[shift + pos], shift being the misalignment
@@ -545,9 +554,12 @@ __global__ void __launch_bounds__(kKThreads) kd_expand_kernel(const KdParams p) 
 #pragma unroll
         for (int q = 0; q < kKPer; ++q) {
             const int w = q * kKThreads + tid;
-            if (w < nwin)
-                kd_expand_one<E, K>(s_ent[w], s_wpos[w], staged, s_tok, shift, p.out, tb, p.ids_cap,
-                                    s_ids);
+            if (w < nwin) {
+                const E ew = s_ent[w];
+                const int pos = s_wpos[w];
+                if (KdEnt<E, K>::is_id(ew) && staged) s_tok[shift + pos] = (int)ew;
+                else kd_expand_one<E, K>(ew, pos, staged, s_tok, shift, p.out, tb, p.ids_cap, s_ids);
+            }
         }
         __syncthreads();
         if (staged) {
