@@ -385,7 +385,9 @@ def _hbm(alg, ms, what):
 def _ktab(torch, P, dev, d_bytes, d_offs, n, n_seq, flush_l2):
     """The 4096-sequence batch through a 5^6-entry k-mer table laid out like a
     blocked 6-mer model's vocabulary (windows with N fall back to single
-    symbols): symbol pass, window offsets, count, scan and emit."""
+    symbols), straight from the RAW bytes: window plan, count (window
+    entries), tile scan and expand, with the general path's five kernels
+    launched gated behind them (they exit at once)."""
     import synth
     lut, base = synth.kmer_vocab(6, seed=49)
     s = torch.cuda.current_stream()
@@ -394,12 +396,14 @@ def _ktab(torch, P, dev, d_bytes, d_offs, n, n_seq, flush_l2):
         ms = _time_median(torch, lambda: tok.encode(d_bytes, d_offs, ids, o, tot, stream=s), flush_l2)
         tok.sync()
         n_ids = int(tot[0].item())
+        direct = P.binding.dnatok_direct_ran(tok.h)
     alg = n + 4 * n_ids + 16 * (n_seq + 1)
     return {"workload": "table-driven 6-mers (5^6 table, single-symbol fallback) of the same "
                         "4096 sequences", "tokens": n_ids, "ms": ms,
-            "tokens_per_s": n_ids / (ms / 1e3),
-            "roofline": _hbm(alg, ms, "CUDA events around the whole encode (five launches)"),
-            "gpu_launches_per_step": 6}
+            "tokens_per_s": n_ids / (ms / 1e3), "path": "raw bytes" if direct == 1 else "general",
+            "roofline": _hbm(alg, ms, "CUDA events around the whole encode (plan, count, scan, "
+                                      "expand, and the general path's gated launches)"),
+            "gpu_launches_per_step": 9}
 
 
 def _decode_rc_feed(torch, P, dev, d_bytes, d_offs, n, n_seq, flush_l2):
