@@ -1,9 +1,8 @@
 // ktab.cuh -- the shared pieces of the table-driven k-mer kernels (the
-// two-pass kernels over the symbol plane and the single-pass kernel over
-// raw bytes): tile constants, shared-memory sizing, and the per-window
-// walk that turns k staged digits (A0 C1 G2 T3, 4 for N-class; or input
-// bytes, digitized on the way) into a base-5 table index and a token count
-// (Algorithm 2, MapKmer).
+// two-pass kernels over the symbol plane and the count pass over raw
+// bytes): tile constants, shared-memory sizing, and the per-window
+// walk that turns k staged digits (A0 C1 G2 T3, 4 for N-class) into a
+// base-5 table index and a token count (Algorithm 2, MapKmer).
 #pragma once
 #include <cstdint>
 
@@ -37,19 +36,6 @@ struct KtabIds {
 
 __host__ __device__ constexpr int pow5(int k) { return k == 0 ? 1 : 5 * pow5(k - 1); }
 
-// The digit of a staged byte: a symbol-plane byte (0..3, 4 for N-class) as
-// it is (clamped), or (RAW) an input byte: A0 C1 G2 T3 in either case, 4 for
-// any other byte.  A byte is one of ACGTacgt iff its bits 0, 3, 4, 6 and 7
-// match those of 'A', or those of 'T' (bit 2 set, bit 1 clear) for a T; the
-// code is bit1 ^ bit2 (low bit) and bit2 ^ bit3 (high bit).
-template <bool RAW>
-__device__ __forceinline__ int ktab_digit(unsigned b) {
-    if (!RAW) return b < 5u ? (int)b : 4;
-    const unsigned code = ((b >> 1) ^ (b >> 2)) & 3u;
-    const unsigned t = (b >> 2) & ~(b >> 1) & 1u;
-    return ((b & 0xD9u) ^ (0x41u + 0x0Fu * t)) == 0u ? (int)code : 4;
-}
-
 // Dynamic shared memory of a ktab_tile_kernel: [u16 table (T16)] [symbols]
 // [staged ids (EMIT)], each part 16-byte aligned.
 __host__ __device__ constexpr int ktab_tab_bytes(int K, bool T16) {
@@ -69,7 +55,7 @@ struct KWin {
     int idx;            // a whole window's base-5 index
 };
 
-template <int K, bool T16, bool RAW = false>
+template <int K, bool T16>
 __device__ __forceinline__ KWin ktab_window(long long w, int &i, int nw, long long rb, long long n_rec,
                                             const long long *s_wp, const long long *s_sr,
                                             const long long *wpre, const long long *srec,
@@ -107,7 +93,8 @@ __device__ __forceinline__ KWin ktab_window(long long w, int &i, int nw, long lo
         int index = 0;
 #pragma unroll
         for (int x = 0; x < K; ++x) {
-            index = index * 5 + ktab_digit<RAW>(s_sym[q.j + x]);
+            const int d = s_sym[q.j + x];
+            index = index * 5 + (d < 5 ? d : 4);
         }
         if (T16) {
             const unsigned v = s_tab[index];
@@ -149,7 +136,7 @@ __device__ __forceinline__ KCursor kc_init(long long w, int nw, const long long 
 
 // The window at the cursor (then advanced by one window), or cnt = 0 with
 // r = -1 past the shared window's records or on malformed input.
-template <int K, bool T16, bool RAW = false>
+template <int K, bool T16>
 __device__ __forceinline__ KWin kc_window(KCursor &c, int nw, long long rb, const long long *s_sr,
                                           long long jlo, const uint8_t *s_sym, long long nsym,
                                           const int *klut, const uint16_t *s_tab) {
@@ -174,7 +161,8 @@ __device__ __forceinline__ KWin kc_window(KCursor &c, int nw, long long rb, cons
         int index = 0;
 #pragma unroll
         for (int x = 0; x < K; ++x) {
-            index = index * 5 + ktab_digit<RAW>(s_sym[c.j + x]);
+            const int d = s_sym[c.j + x];
+            index = index * 5 + (d < 5 ? d : 4);
         }
         if (T16) {
             const unsigned v = s_tab[index];
@@ -199,7 +187,7 @@ __device__ __forceinline__ KWin kc_window(KCursor &c, int nw, long long rb, cons
 // compile-time positions (instead of k single-byte shared-memory loads per
 // window).  ent[q] = the table entry (-1: none), cnt[q] = 1 or K, idx[q] =
 // the window's base-5 index.
-template <int K, bool T16, bool RAW = false>
+template <int K, bool T16>
 __device__ __forceinline__ void ktab_fast_windows(const uint8_t *s_base, int A, const int *klut,
                                                   const uint16_t *s_tab, int (&ent)[kKPer],
                                                   int (&cnt)[kKPer], int (&idx)[kKPer]) {
@@ -219,7 +207,8 @@ __device__ __forceinline__ void ktab_fast_windows(const uint8_t *s_base, int A, 
 #pragma unroll
         for (int x = 0; x < K; ++x) {
             const int b = q * K + x;
-            index = index * 5 + ktab_digit<RAW>((X[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+            const int d = (int)((X[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+            index = index * 5 + (d < 5 ? d : 4);
         }
         int e;
         if (T16) {
