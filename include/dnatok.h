@@ -578,8 +578,10 @@ DNATOK_API dnatok_status dnatok_set_direct(dnatok_handle *h, int32_t enable);
  * the encode never tried the direct path (switched off, not eligible, or
  * no encode yet).  FASTA handles take the direct path for k-mers (k >= 2) of
  * 16-byte aligned text of 64 KiB up to 4 GiB: the text is first compacted on
- * the device to its sequence bytes and record starts.  Not meaningful for
- * an encode recorded in a graph (its replays reset the switch). */
+ * the device to its sequence bytes and record starts.  DNATOK_KMER_TABLE
+ * handles on RAW input take it straight from the bytes (window plan, count,
+ * scan, expand), except under stream capture.  Not meaningful for an encode
+ * recorded in a graph (its replays reset the switch). */
 DNATOK_API dnatok_status dnatok_direct_ran(dnatok_handle *h, dnatok_cuda_stream stream,
                                            int32_t *out);
 
