@@ -401,7 +401,7 @@ dnatok_status dnatok_decode(dnatok_handle *h, const int32_t *ids_d, int64_t n_id
         if (pass == 1) {
             tile_scan_kernel<<<1, kTileScanThreads, 0, s>>>(
                 h->d_dsum, h->d_dinv, a.keys, nullptr, n_seq, nullptr, n_ids, kDT, a.rec_out,
-                reinterpret_cast<long long *>(totals_d), nullptr, nullptr, 0u);
+                reinterpret_cast<long long *>(totals_d), nullptr, nullptr, 0u, false);
             e = cudaGetLastError();
             if (e != cudaSuccess) return fail_cuda(h, e, "decode scan launch");
         }

@@ -184,13 +184,17 @@ dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_by
 // totals_out (NULL or 2): {total, sum of tinv (NULL: n_rec)}.  n_rec comes
 // from n_rec_dev when not NULL; n_items from n_items_dev when not NULL, else
 // n_items_host when >= 0, else keys[n_rec].  Does nothing once the device
-// status word holds an error, nor when gate is not NULL and *gate differs
-// from gate_epoch (the direct path behind which it runs did the work).
+// status word holds an error.  With gate not NULL it runs only when the gate
+// is raised (*gate == gate_epoch) if run_if_raised, only when it is not
+// otherwise: behind a direct path it is the general path's scan, which runs
+// only when the direct path declined; inside a direct path it is that
+// path's own scan, which must not read what a declined plan left unwritten.
 __global__ void tile_scan_kernel(long long *tsum, const long long *tinv, const long long *keys,
                                  const long long *n_rec_dev, long long n_rec_host,
                                  const long long *n_items_dev, long long n_items_host,
                                  int items_per_tile, long long *rec_out, long long *totals_out,
-                                 const int *status, const unsigned *gate, unsigned gate_epoch);
+                                 const int *status, const unsigned *gate, unsigned gate_epoch,
+                                 bool run_if_raised);
 constexpr int kTileScanThreads = 1024;
 
 // decode tables (decode.cu)

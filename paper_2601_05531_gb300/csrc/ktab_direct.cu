@@ -748,9 +748,10 @@ cudaError_t ktab_direct_launch(dnatok_handle *h, const uint8_t *bytes, long long
     e = kd_dispatch(h->k, false, t16, h->kent16, p, h->sm_count, max_tiles, s);
     if (e != cudaSuccess) return e;
     // 3. tile offsets, totals, records with no window left
+    // (skipped when the gate is up: a plan that declined left wpre unwritten)
     tile_scan_kernel<<<1, kTileScanThreads, 0, s>>>(tsum, nullptr, wpre, nullptr, n_seq, nullptr,
                                                     -1, kKW, id_offsets, totals, h->d_status,
-                                                    nullptr, 0u);
+                                                    h->d_gate, epoch, false);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // 4. ids and record offsets

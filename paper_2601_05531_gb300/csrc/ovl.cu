@@ -727,12 +727,17 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(
     long long *tsum, const long long *tinv, const long long *keys, const long long *n_rec_dev,
     long long n_rec_host, const long long *n_items_dev, long long n_items_host, int items_per_tile,
     long long *rec_out, long long *totals_out, const int *status, const unsigned *gate,
-    unsigned gate_epoch) {
+    unsigned gate_epoch, bool run_if_raised) {
     constexpr int kPer = 4;
     __shared__ long long wsum[kTileScanThreads / 32], winv[kTileScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (dev_failed(status)) return;  // an earlier pass failed: its counts are not valid
-    if (gate && *(volatile const unsigned *)gate != gate_epoch) return;  // the direct path did it
+    if (gate) {
+        // behind a direct path (run_if_raised: only when it declined), or
+        // the direct path's own scan (only when it did not)
+        const bool raised = *(volatile const unsigned *)gate == gate_epoch;
+        if (raised != run_if_raised) return;
+    }
     const long long n_rec = n_rec_dev ? *n_rec_dev : n_rec_host;
     if (n_rec < 0) return;
     const long long n_items = n_items_dev ? *n_items_dev : (n_items_host >= 0 ? n_items_host : keys[n_rec]);
@@ -851,7 +856,7 @@ dnatok_status ktab_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n_by
     tile_scan_kernel<<<1, kTileScanThreads, 0, s>>>(o->d_tsum, nullptr, o->d_wpre, o->d_tot + 1, 0,
                                                 nullptr, -1, kKW, offs,
                                                 reinterpret_cast<long long *>(totals_d),
-                                                h->d_status, gate, gate_ep);
+                                                h->d_status, gate, gate_ep, true);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(h, e, "table k-mer scan launch");
     e = launch_ktab(h->k, true, t16, h->sm_count, tiles, o->d_sym, o->d_srec, o->d_wpre, o->d_tot,

@@ -141,13 +141,30 @@ def test_direct_off_and_malformed_offsets(P):
     wi, wo = oracle.encode_ktab(data, 5, lut, base, seq_offsets=offs)
     gi, go, tot, ran, guard = run(P, data, offs, 5, lut, base, direct=False)
     assert go.tolist() == wo.tolist() and np.array_equal(gi, wi) and guard
-    # offsets that decrease: the plan declines, the general path reports it
+    # offsets that decrease, between two good encodes on one handle: the plan
+    # declines, nothing behind it reads the window offsets it left unwritten,
+    # the general path reports the error, and the handle works again after
     bad = offs.copy()
-    bad[5], bad[6] = bad[6], bad[5]
-    if bad[5] != bad[6]:
-        with P.Tokenizer(P.KMER_TABLE, k=5, kmer_lut=lut, base_ids=base) as tok:
-            d = torch.from_numpy(data).cuda()
-            so = torch.from_numpy(bad).cuda()
-            tok.encode(d, so)
-            with pytest.raises(P.DnatokError):
-                tok.sync()
+    bad[5], bad[6] = offs[6] + 1, offs[5]
+    with P.Tokenizer(P.KMER_TABLE, k=5, kmer_lut=lut, base_ids=base) as tok:
+        d = torch.from_numpy(data).cuda()
+        so = torch.from_numpy(offs).cuda()
+        for good in (True, False, True):
+            ids, o, tot = tok.encode(d, so if good else torch.from_numpy(bad).cuda())
+            if not good:
+                with pytest.raises(P.DnatokError):
+                    tok.sync()
+                continue
+            tok.sync()
+            n_ids = int(tot[0])
+            assert o.cpu().numpy().tolist() == wo.tolist()
+            assert np.array_equal(ids[:n_ids].cpu().numpy(), wi)
+
+
+def test_more_records_than_the_plan_takes(P):
+    # 70000 short records: past the 65536 the direct plans take, so the
+    # general path encodes them on its own
+    rng = np.random.default_rng(12)
+    data, offs = synth.markov_batch(rng.integers(0, 60, size=70000), 0.4, seed=12)
+    lut, base = synth.kmer_vocab(4, seed=12)
+    check(P, data, offs, 4, lut, base, "70000 records", expect_direct=-1)
