@@ -649,6 +649,79 @@ DNATOK_API dnatok_status dnatok_get_bpe_launch(const dnatok_handle *h, int32_t *
 DNATOK_API dnatok_status dnatok_bpe_stats(dnatok_handle *h, int64_t *stats3,
                                           dnatok_cuda_stream stream);
 
+/* ---- One long stream split into parts, one process (GPU) per part ----
+ *
+ * A part is a contiguous byte range of the stream (FASTA text, or RAW bytes
+ * of one record), split anywhere: the streamed encode of Sec. 2.2 with its
+ * chunks on different GPUs.  Each part's encode needs only a small state
+ * from the bytes before it, the state that the host-streamed path
+ * (dnatok_stream_*) carries from chunk to chunk: the scan element of the
+ * encode at the part's start and the FASTA line state there.  The
+ * protocol, for ranks 0..N-1 holding parts in stream order:
+ *   1. every rank: dnatok_part_line_map of its part; exchange the maps; the
+ *      line state at rank r's start is the stream start's state (0) mapped
+ *      through the maps of ranks 0..r-1 in order;
+ *   2. rank 0: dnatok_part_encode(before = NULL, last = (N == 1)), its real
+ *      encode; ranks 1..N-2: dnatok_part_encode from an all-zero state in
+ *      that line state, which gives the part's own state; exchange the
+ *      states;
+ *   3. rank r >= 1: its start state is rank 0's state combined
+ *      (dnatok_part_combine, in order) with the states of ranks 1..r-1, with
+ *      the line state of step 1; dnatok_part_encode(before = that, last =
+ *      (r == N-1)).
+ * Ranks exchange their part lengths with the maps: the first rank whose
+ * part holds bytes plays rank 0 (ranks before it hold empty parts and write
+ * nothing), so that the stream start merges with a header at its first byte
+ * as in one encode.
+ * Each rank's ids then start at its ids_out[0]: the part's ids are ids
+ * [before.d, after.d) of the whole stream.  Its id_offsets[0 ..
+ * after.nb - before.nb) are the offsets of records before.nb .. after.nb - 1
+ * of the stream, as stream-wide id positions (the last part also writes the
+ * final one).  Concatenated, the ranks' ids equal one encode of the stream.
+ * Single-nucleotide and k-mer handles (not BPE, overlapping or table-driven
+ * k-mers).
+ */
+typedef struct {
+    int64_t nb;         /* record boundaries seen (the stream start counts) */
+    int64_t h;          /* kept symbols before the first boundary */
+    int64_t d;          /* ids completed */
+    int64_t t;          /* kept symbols of the record still open */
+    uint64_t codes;     /* its last min(t, k-1) symbols, 3 bits each, newest lowest;
+                           their number in bits 58..61 */
+    uint32_t line_state; /* FASTA: 0 at a line start, 1 in a header, 2 in sequence */
+    uint32_t pad;
+} dnatok_part_state;
+
+/* The part's line-state map: bits 2s..2s+1 hold the state at its end when
+ * it starts in state s (RAW handles: the identity, 0 | 1 << 2 | 2 << 4).
+ * Reads the part's bytes on `stream` (DEVICE memory, any alignment) and
+ * waits for the result. */
+DNATOK_API dnatok_status dnatok_part_line_map(dnatok_handle *h, const uint8_t *bytes_d, int64_t n,
+                                              int32_t *map_out, dnatok_cuda_stream stream);
+
+/* Encode one part (DEVICE bytes, any alignment) from the state `before`
+ * (host; NULL: the part starts the stream) and write the state at its end
+ * to *after (host).  last != 0: the part ends the stream (the open record
+ * is closed).  A `before` with nb = 0 (all zero but the line state) asks
+ * for the part's own state, the one that dnatok_part_combine appends to the
+ * state before it: the outputs are then scratch (two runs of the encode for
+ * k-mers, one for single nucleotides).  ids_out_d: ids_capacity >= n + 1;
+ * id_offsets_d: offsets_capacity >= 1 entries, those past it not written.
+ * Waits for `stream`; device errors come back as from dnatok_sync.
+ * DNATOK_ERR_STATE for BPE, overlapping or table-driven handles, or while a
+ * stream is open on h. */
+DNATOK_API dnatok_status dnatok_part_encode(dnatok_handle *h, const uint8_t *bytes_d, int64_t n,
+                                            const dnatok_part_state *before, int32_t last,
+                                            int32_t *ids_out_d, int64_t ids_capacity,
+                                            int64_t *id_offsets_d, int64_t offsets_capacity,
+                                            dnatok_part_state *after, dnatok_cuda_stream stream);
+
+/* out = the state after a part with state b that follows a stretch of the
+ * stream with state a, for k-mers of k (1 for single nucleotides).  Host
+ * only (no device work).  The line state is b's. */
+DNATOK_API dnatok_status dnatok_part_combine(int32_t k, const dnatok_part_state *a,
+                                             const dnatok_part_state *b, dnatok_part_state *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -248,3 +248,96 @@ def global_id_offsets(local_offsets, group=None):
     counts = torch.cat(counts).cpu()
     base = int(counts[:rank].sum())
     return local_offsets + base, int(counts.sum())
+
+
+class StreamPart:
+    """One rank's part of a long stream split over processes (one GPU each):
+    the protocol of dnatok_part_* in three steps with two exchanges between
+    them.  `part` is a CUDA uint8 tensor holding the rank's contiguous bytes
+    of the stream; `ids` / `offsets` receive its ids and its records'
+    offsets (stream-wide id positions).
+
+        p = StreamPart(tok, part, ids, offsets, rank, world)
+        maps = exchange(p.line_map())          # two ints per rank
+        states = exchange(p.summary(maps))     # six ints per rank
+        n_ids, n_offsets, first_id, first_record = p.finish(states)
+
+    The first rank whose part holds bytes starts the stream (ranks before it
+    hold empty parts and write nothing), so the stream start merges with a
+    header at its first byte exactly as in one encode.
+    """
+
+    def __init__(self, tok, part, ids, offsets, rank: int, world: int, stream=None):
+        self.tok, self.part, self.ids, self.offsets = tok, part, ids, offsets
+        self.rank, self.world = rank, world
+        self.sp = _stream_ptr(stream)
+        self.n = int(part.numel())
+        self.addr = part.data_ptr() if self.n else 0
+        self.line_state = 0
+        self.lead = 0
+        self.mine = None
+
+    def _encode(self, before, last):
+        return binding.dnatok_part_encode(self.tok.h, self.addr, self.n, before, last,
+                                          self.ids.data_ptr(), self.ids.numel(),
+                                          self.offsets.data_ptr(), self.offsets.numel(), self.sp)
+
+    def line_map(self):
+        """Step 1: this part's line-state map and length, to exchange."""
+        return [binding.dnatok_part_line_map(self.tok.h, self.addr, self.n, self.sp), self.n]
+
+    def summary(self, maps):
+        """Step 2 (maps: every rank's step-1 list): the line state at this
+        part's start, and this part's state to exchange (the stream's first
+        rank: its real encode; the last rank sends nothing anyone reads)."""
+        s = 0
+        for r in range(self.rank):
+            s = (int(maps[r][0]) >> (2 * s)) & 3
+        self.line_state = s
+        lead = next((r for r in range(self.world) if int(maps[r][1]) > 0), self.world - 1)
+        self.lead = lead
+        last = self.rank == self.world - 1
+        if self.rank == lead:
+            self.mine = self._encode(None, last)
+        elif lead < self.rank < self.world - 1:
+            self.mine = self._encode(binding.PartState.from_list([0, 0, 0, 0, 0, s]), False)
+        else:
+            self.mine = binding.PartState()
+        return self.mine.as_list()
+
+    def finish(self, states):
+        """Step 3 (states: every rank's step-2 list): encode the part from the
+        state of the stream before it.  Returns (ids written, offsets
+        written, stream index of its first id, of its first record)."""
+        if self.rank < self.lead:
+            return 0, 0, 0, 0
+        if self.rank == self.lead:
+            return self.mine.d, self.mine.nb, 0, 0
+        k = self.tok.k if self.tok.mode == binding.KMER else 1
+        before = binding.PartState.from_list(states[self.lead])
+        for r in range(self.lead + 1, self.rank):
+            before = binding.dnatok_part_combine(k, before, binding.PartState.from_list(states[r]))
+        before.line_state = self.line_state
+        after = self._encode(before, self.rank == self.world - 1)
+        return after.d - before.d, after.nb - before.nb, before.d, before.nb
+
+
+def encode_stream_part(tok, part, ids, offsets, group=None, stream=None):
+    """StreamPart's three steps with torch.distributed all_gathers (CPU
+    tensors for gloo, CUDA tensors for nccl) in the default or given group."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    dev = torch.device("cuda") if dist.get_backend(group) == "nccl" else torch.device("cpu")
+
+    def exchange(vals):
+        t = torch.tensor(vals, dtype=torch.int64, device=dev)
+        out = [torch.empty_like(t) for _ in range(ws)]
+        dist.all_gather(out, t, group=group)
+        return [o.cpu().tolist() for o in out]
+
+    p = StreamPart(tok, part, ids, offsets, rank, ws, stream)
+    maps = exchange(p.line_map())
+    states = exchange(p.summary(maps))
+    return p.finish(states)

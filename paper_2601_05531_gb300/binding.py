@@ -44,6 +44,21 @@ class StreamResult(ctypes.Structure):
                 ("bytes_in", ctypes.c_int64)]
 
 
+class PartState(ctypes.Structure):
+    """dnatok_part_state: the state at a part boundary of a split stream."""
+    _fields_ = [("nb", ctypes.c_int64), ("h", ctypes.c_int64), ("d", ctypes.c_int64),
+                ("t", ctypes.c_int64), ("codes", ctypes.c_uint64),
+                ("line_state", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+    def as_list(self):
+        return [self.nb, self.h, self.d, self.t, self.codes, self.line_state]
+
+    @classmethod
+    def from_list(cls, v):
+        return cls(int(v[0]), int(v[1]), int(v[2]), int(v[3]), int(v[4]) & ((1 << 64) - 1),
+                   int(v[5]), 0)
+
+
 class ServerCfg(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("host_arena_bytes", ctypes.c_int64),
                 ("max_batch_bytes", ctypes.c_int64), ("max_batch_requests", ctypes.c_int32),
@@ -152,6 +167,11 @@ def lib():
             "dnatok_shard_records": (_ST, [_P, _I64, ctypes.c_int32, _P]),
             "dnatok_feed_pipeline": (_ST, [_P, _P, _I64, _I64, _I64, ctypes.c_int32, _I64, _P, _P,
                                            _P, _P, FEED_CONSUMER, _P]),
+            "dnatok_part_line_map": (_ST, [_P, _P, _I64, ctypes.POINTER(ctypes.c_int32), _P]),
+            "dnatok_part_encode": (_ST, [_P, _P, _I64, ctypes.POINTER(PartState), ctypes.c_int32,
+                                         _P, _I64, _P, _I64, ctypes.POINTER(PartState), _P]),
+            "dnatok_part_combine": (_ST, [ctypes.c_int32, ctypes.POINTER(PartState),
+                                          ctypes.POINTER(PartState), ctypes.POINTER(PartState)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -516,4 +536,27 @@ def dnatok_shard_records(seq_offsets, world_size: int):
     so = np.ascontiguousarray(seq_offsets, dtype=np.int64)
     out = np.empty(world_size + 1, dtype=np.int64)
     check(lib().dnatok_shard_records(so.ctypes.data, so.size - 1, world_size, out.ctypes.data))
+    return out
+
+
+def dnatok_part_line_map(h, bytes_d: int, n: int, stream=0) -> int:
+    out = ctypes.c_int32(0)
+    check(lib().dnatok_part_line_map(h, bytes_d, n, ctypes.byref(out), stream), h)
+    return out.value
+
+
+def dnatok_part_encode(h, bytes_d: int, n: int, before, last: bool, ids_out_d: int,
+                       ids_capacity: int, id_offsets_d: int, offsets_capacity: int,
+                       stream=0) -> PartState:
+    """before: a PartState, or None when the part starts the stream."""
+    after = PartState()
+    check(lib().dnatok_part_encode(h, bytes_d, n, ctypes.byref(before) if before is not None else None,
+                                   int(bool(last)), ids_out_d, ids_capacity, id_offsets_d,
+                                   offsets_capacity, ctypes.byref(after), stream), h)
+    return after
+
+
+def dnatok_part_combine(k: int, a: PartState, b: PartState) -> PartState:
+    out = PartState()
+    check(lib().dnatok_part_combine(k, ctypes.byref(a), ctypes.byref(b), ctypes.byref(out)))
     return out

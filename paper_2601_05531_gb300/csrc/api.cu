@@ -306,6 +306,7 @@ void dnatok_destroy(dnatok_handle *h) {
     if (!h) return;
     cudaDeviceSynchronize();
     stream_destroy(h);
+    part_destroy(h);
     bpe_destroy(h);
     ovl_destroy(h);
     fasta_destroy(h);

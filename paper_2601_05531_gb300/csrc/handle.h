@@ -57,6 +57,7 @@ struct dnatok_handle {
     long long *d_stage_totals = nullptr;
 
     StreamState *stream = nullptr;
+    void *d_part = nullptr;  // parts of a split stream: carries, newline scan, map, totals (part.cu)
     BpeState *bpe = nullptr;
     OvlState *ovl = nullptr;
     FastaState *fasta = nullptr;
@@ -202,5 +203,8 @@ void dec_destroy(dnatok_handle *h);
 
 // host-streamed pipeline (stream.cu)
 void stream_destroy(dnatok_handle *h);
+
+// parts of a split stream (part.cu)
+void part_destroy(dnatok_handle *h);
 
 }  // namespace dnatok
