@@ -22,9 +22,13 @@ def build(force: bool = False) -> str:
 
 
 def _stream_ptr(stream) -> int:
+    """A cudaStream_t value: None -> torch's current stream, an int as it
+    is (0: the legacy default stream), else the stream's handle."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
     return int(stream.cuda_stream)
 
 

@@ -107,3 +107,102 @@ def test_three_ranks_with_an_empty_shard():
     assert np.array_equal(ids, want_ids)
     assert got_offs == want_offs.tolist()
     assert all(x[5] == len(want_ids) for x in res)
+
+
+# ---------------------------------------------------------------- split stream
+#
+# encode_stream_part's exchanges over gloo with 2 to 4 processes.  A CPU has
+# no GPU to encode the parts, so the two device calls are replaced by the
+# scan element written out from its definition (tests.test_part_cpu) over a
+# stream of symbols and record boundaries: what is tested is everything
+# around them -- the all_gathers, the rank that starts the stream, the order
+# of the host combines (the real dnatok_part_combine) -- and each rank must
+# receive as its start state exactly the state of the whole stream before it.
+
+def _stream_events(seed, world):
+    rng = np.random.default_rng(seed)
+    ev = [None if rng.random() < 0.03 else int(rng.integers(0, 5)) for _ in range(3000)]
+    cuts = sorted(int(c) for c in rng.integers(0, len(ev) + 1, size=world - 1))
+    if seed % 3 == 0:
+        cuts[0] = 0  # an empty first part: the next rank starts the stream
+    return ev, [0] + cuts + [len(ev)]
+
+
+def _stream_rank_main(rank, world, port, seed, k, out_q):
+    import torch
+    import torch.distributed as dist
+    import paper_2601_05531_gb300 as P
+    from paper_2601_05531_gb300 import binding as B
+    from tests.test_part_cpu import span_state
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ev, b = _stream_events(seed, world)
+        mine = ev[b[rank]:b[rank + 1]]
+        seen = {}
+
+        def fake_map(h, addr, n, stream=0):
+            return 0 | (1 << 2) | (2 << 4)  # every part keeps the line state
+
+        def fake_encode(h, addr, n, before, last, *args):
+            own = mine + ([None] if last else [])
+            if before is None:
+                st = span_state([None] + own, k) + [0]
+            elif before.nb == 0:
+                st = span_state(own, k) + [before.line_state]
+            else:
+                seen["before"] = before.as_list()
+                st = B.dnatok_part_combine(k, before,
+                                           B.PartState.from_list(span_state(own, k) + [0])).as_list()
+            return B.PartState.from_list(st)
+
+        B.dnatok_part_line_map = fake_map
+        B.dnatok_part_encode = fake_encode
+
+        class Tok:
+            h = None
+            mode = B.KMER
+
+        Tok.k = k
+        part = torch.zeros(len(mine), dtype=torch.uint8)  # only its length is read
+        res = P.encode_stream_part(Tok(), part, torch.zeros(1, dtype=torch.int32),
+                                   torch.zeros(1, dtype=torch.int64), stream=0)
+        out_q.put((rank, tuple(int(x) for x in res), seen.get("before")))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,seed,k", [(2, 1, 6), (3, 3, 13), (4, 4, 2), (4, 6, 1)])
+def test_split_stream_exchanges(world, seed, k):
+    import multiprocessing as mp
+    import __graft_entry__
+    from tests.test_part_cpu import span_state
+    __graft_entry__.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_stream_rank_main, args=(r, world, port, seed, k, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=60) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    ev, b = _stream_events(seed, world)
+    lead = next((r for r in range(world) if b[r + 1] > b[r]), world - 1)
+    total = span_state([None] + ev + [None], k)
+    n_ids = n_recs = 0
+    for rank, (ni, no, first_id, first_rec), before in got:
+        if rank < lead:
+            assert (ni, no, first_id, first_rec) == (0, 0, 0, 0)
+            continue
+        want_before = span_state([None] + ev[:b[rank]], k)
+        if rank > lead:
+            assert before == want_before + [0], rank  # the state of everything before it
+        assert (first_id, first_rec) == (n_ids, n_recs) == (
+            (want_before[2], want_before[0]) if rank > lead else (0, 0))
+        n_ids += ni
+        n_recs += no
+    assert (n_ids, n_recs) == (total[2], total[0])
