@@ -206,7 +206,10 @@ static dnatok_status part_run(dnatok_handle *h, int mode, int k, const uint8_t *
     const int sb = from_carry ? 0 : 1;
     dnatok_status st;
     if (n == 0) {
-        st = run_tile_encode(h, mode, k, BSRC_LIST, nullptr, 0, nullptr, sb + eb, out,
+        // boundaries only; a FASTA stream with no bytes at all has no record
+        // (its start is not one), as in a one-shot encode of no text
+        const long long nb = (h->fmt == DNATOK_FASTA && !from_carry) ? eb : sb + eb;
+        st = run_tile_encode(h, mode, k, BSRC_LIST, nullptr, 0, nullptr, nb, out,
                              ids_capacity + d0, offs, offsets_capacity + nb0, part_tot(h), cin, cout,
                              0, 0, s);
     } else {

@@ -142,6 +142,16 @@ def test_raw_one_record_stream(env):
             check(torch, P, data, cuts, mode, k, P.RAW, "raw world %d" % world)
 
 
+def test_every_part_empty(env):
+    # the last rank starts and ends the stream: FASTA text of no bytes has
+    # no record, a RAW stream one empty record
+    torch, P = env
+    e = np.zeros(0, np.uint8)
+    for fmt in (P.FASTA, P.RAW):
+        for cuts in ([], [0], [0, 0]):
+            check(torch, P, e, cuts, P.KMER, 6, fmt, "empty")
+
+
 def test_refused_for_other_modes(env):
     torch, P = env
     lut, base = synth.kmer_vocab(3, seed=1)
